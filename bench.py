@@ -1,0 +1,422 @@
+"""Benchmark: cell-updates/s of the explicit shallow-water step on GB300.
+
+Default workload: 10,001,406 triangles (3163 x 1581 jittered grid over
+100 km x 50 km), bed of 8 random sinusoids, per-cell Manning n, radial dam
+break, cells and edges in Morton order, FP32 state with compensated face
+sums and an FP64 mass integral; one step = one explicit Euler step of the
+whole mesh (all face fluxes, updates, friction and the CFL reduction).
+
+Prints ONE JSON line (rank 0). Under torchrun with N > 1 every rank runs an
+independent replica on its own GPU (the single-mesh step has no exchange on
+one GPU per rank here), and `value` is the sum over ranks divided by the
+slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s"
+UNIT = "cell-updates/s"
+HBM_FALLBACK_GBS = 6800.0
+L2_BYTES = 129 * 1024 * 1024
+
+# Algorithmic bytes per cell-update: each cell reads h, hu, hv, z, 1/area and
+# n, each edge's nx, ny, l and two int32 endpoints once (1.5 edges per cell),
+# and each cell writes h, hu, hv once: (12.5 + [n]) words + 12 bytes.
+def alg_bytes_per_cell(word: int, per_cell_n: bool) -> float:
+    return (12.5 + (1.0 if per_cell_n else 0.0)) * word + 12.0
+
+
+WORKLOADS = {
+    "sinusoid_10m": dict(fn="sinusoid_case", kw={}, per_cell_n=True, seed=3,
+                         desc="10,001,406 triangles, 8-sinusoid bed, per-cell n, radial dam break"),
+    "humps_1m": dict(fn="humps_case", kw={}, per_cell_n=False, seed=2,
+                     desc="1,000,000 triangles, 3 Gaussian humps, n=0.03, wet/dry"),
+}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", HBM_FALLBACK_GBS)), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k] == "Active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_case(name: str):
+    from paper_1807_00672_gb300 import inputs
+    w = WORKLOADS[name]
+    return getattr(inputs, w["fn"])(**w["kw"])
+
+
+def small_case(name: str, cells: int):
+    """The same workload recipe at a reduced size (bounded oracle samples)."""
+    from paper_1807_00672_gb300 import inputs
+    w = WORKLOADS[name]
+    full = getattr(inputs, w["fn"])
+    if name == "sinusoid_10m":
+        ny = max(4, int(round(math.sqrt(cells / 4.0))))
+        scale = (2 * ny) / 3163.0
+        return full(nx=2 * ny, ny=ny, lx=100_000.0 * scale, ly=50_000.0 * scale)
+    ny = max(4, int(round(math.sqrt(cells / 4.0))))
+    scale = (2 * ny) / 1000.0
+    return full(nx=2 * ny, ny=ny, lx=10_000.0 * scale, ly=5_000.0 * scale)
+
+
+def oracle_rate(case, steps: int, warmup: int):
+    """Cell-updates/s of the FP64 oracle (single thread) on `case`."""
+    import oracle
+    o = oracle.state_from_case(case)
+    if warmup:
+        o.run(warmup)
+    t0 = time.perf_counter()
+    o.run(steps)
+    dt = time.perf_counter() - t0
+    return o.mesh.T * steps / dt, dt
+
+
+def run_reference(args, ws, rank):
+    """The FP64 CPU oracle as it stands, timed on this host's cores."""
+    if rank != 0:
+        return
+    case = small_case(args.workload, args.ref_cells)
+    t_cells = case.mesh.n_tris
+    rate, secs = oracle_rate(case, args.steps, args.warmup)
+    sample = (f"same recipe as {args.workload} at {t_cells} triangles, {args.steps} steps "
+              f"after {args.warmup} warm-up steps, FP64 oracle, 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "triangles_sampled": t_cells},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sinusoid_10m")
+    ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--kernel", choices=["auto", "tiled", "edge"], default="auto")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="solver steps per e2e call (0 = --steps)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the fp64 and error legs")
+    ap.add_argument("--ref-cells", type=int, default=25_000)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    from paper_1807_00672_gb300 import build, swe
+
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    case = make_case(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=args.precision, kernel=args.kernel,
+                    tile=args.tile, stream=ctypes_stream(stream))
+    st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+    T = mesh.T
+    kernels_per_step = 2 if args.kernel == "edge" else 1
+
+    # warm-up: at least one full graph of steps, so the timed region replays
+    # an already captured graph
+    warm = max(args.warmup, 16)
+    st.run(warm)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st.run(args.steps, sync=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop() if sampler else None
+    st.sync()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * T * args.steps / (ms * 1e-3)
+
+    # Dominant kernel: per-launch CUDA events around single-step launches.
+    per_launch = []
+    for _ in range(min(args.steps, 200)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.run(1, sync=False)
+        b.record(stream)
+        per_launch.append((a, b))
+    torch.cuda.synchronize()
+    st.sync()
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in per_launch)
+    word = 4 if args.precision == "f32" else 8
+    balg = alg_bytes_per_cell(word, WORKLOADS[args.workload]["per_cell_n"])
+    peak, peak_kind = measured_peaks()
+    achieved = balg * T / (kern_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(args)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": warm, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {
+            "workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+            "triangles": T, "edges": mesh.E, "precision": args.precision,
+            "kernel": args.kernel, "order": "morton", "seed": WORKLOADS[args.workload]["seed"],
+            "l2": f"inputs larger than L2: {mesh.device_bytes() / 1e6:.0f} MB of mesh + "
+                  f"{6 * word * T / 1e6:.0f} MB of state vs 129 MB L2",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_tiled_step" if args.kernel != "edge" else "k_edge_flux+k_cell_update",
+                     "alg_bytes_per_cell": balg, "kernel_ms": kern_ms,
+                     "peak_source": f"{peak_kind} HBM copy bandwidth"},
+        "gpu_launches": args.steps * kernels_per_step,
+        "clocks": clocks,
+    }
+
+    # e2e through the C ABI with pinned host buffers: H2D of (h, hu, hv),
+    # the steps, D2H of (h, hu, hv).
+    e2e_steps = args.e2e_steps or args.steps
+    hp = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (case.h, case.hu, case.hv)]
+    ho = [torch.empty(T, dtype=torch.float64).pin_memory() for _ in range(3)]
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    swe_set_ptrs(st, hp)
+    st.run(e2e_steps, sync=False)
+    swe_copy_ptrs(st, ho)
+    t1 = time.perf_counter()
+    secs = t1 - t0
+    if dist is not None:
+        t = torch.tensor([secs], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    nbytes = 3 * 8 * T
+    out["e2e"] = {"value": ws * T * e2e_steps / secs, "unit": UNIT,
+                  "h2d_bytes_per_step": nbytes / e2e_steps, "d2h_bytes_per_step": nbytes / e2e_steps,
+                  "steps_per_call": e2e_steps, "h2d_bytes_per_call": nbytes,
+                  "d2h_bytes_per_call": nbytes,
+                  "path": "swe_state_set (pinned host) + swe_run + swe_copy_out (pinned host)"}
+
+    if rank == 0 and not args.no_extras:
+        out["fp64"] = fp64_leg(case, args, stream, ws)
+        out["error"] = error_leg(args)
+    st.close()
+    mesh.close()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        small = small_case(args.workload, args.ref_cells)
+        k = 40
+        rate, secs = oracle_rate(small, k, 2)
+        out["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, 1 thread, {k} steps of the same recipe at "
+                      f"{small.mesh.n_tris} triangles ({secs:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def ctypes_stream(stream):
+    import ctypes
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def swe_set_ptrs(st, tensors):
+    import ctypes
+    from paper_1807_00672_gb300 import swe
+    ptrs = [ctypes.c_void_p(t.data_ptr()) for t in tensors]
+    swe._check(swe.lib().swe_state_set(st._h, *ptrs), "swe_state_set")
+
+
+def swe_copy_ptrs(st, tensors):
+    import ctypes
+    from paper_1807_00672_gb300 import swe
+    ptrs = [ctypes.c_void_p(t.data_ptr()) for t in tensors]
+    swe._check(swe.lib().swe_copy_out(st._h, *ptrs, None, None), "swe_copy_out")
+
+
+def fp64_leg(case, args, stream, ws):
+    """The FP64 path on the same mesh: cell-updates/s and HBM fraction."""
+    import torch
+    from paper_1807_00672_gb300 import swe
+    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f64", kernel=args.kernel,
+                    tile=args.tile, stream=ctypes_stream(stream))
+    st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+    st.run(3)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    st.run(args.fp64_steps, sync=False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    st.sync()
+    ms = a.elapsed_time(b) / args.fp64_steps
+    balg = alg_bytes_per_cell(8, WORKLOADS[args.workload]["per_cell_n"])
+    peak, kind = measured_peaks()
+    achieved = balg * mesh.T / (ms * 1e-3) / 1e9
+    st.close()
+    mesh.close()
+    return {"value": mesh.T / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "steps": args.fp64_steps, "hbm_frac": achieved / peak, "achieved_gbs": achieved,
+            "alg_bytes_per_cell": balg}
+
+
+def error_leg(args, cells=50_000, steps=100):
+    """FP32 vs FP64-oracle error on the workload recipe at a reduced size."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from paper_1807_00672_gb300 import swe
+    case = small_case(args.workload, cells)
+    o = oracle.state_from_case(case)
+    o.run(steps)
+    area = o.mesh.cells()["area"]
+    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f32", kernel=args.kernel, tile=args.tile)
+    st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+    st.run(steps)
+    got = st.fields()
+    res = {"triangles": mesh.T, "steps": steps, "vs": "FP64 oracle"}
+    for name, g, r in zip(("h", "hu", "hv"), got, (o.h, o.hu, o.hv)):
+        den = float((area * np.abs(r)).sum())
+        res[f"l1_{name}"] = float((area * np.abs(g - r)).sum()) / den
+        res[f"linf_{name}"] = float(np.abs(g - r).max()) / float(np.abs(r).max())
+    st.close()
+    mesh.close()
+    return res
+
+
+def profiled_traffic(args):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the kernel source as it is now (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path) or args.precision != "f32" or args.kernel == "edge":
+        return None
+    src = os.path.join(ROOT, "paper_1807_00672_gb300", "csrc", "swe_kernels.cuh")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    scale_to = None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 4 and parts[0] == args.workload and parts[1] == digest:
+                return float(parts[2])
+    return scale_to
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * swe.h - C ABI of the GB300 shallow-water step library (libswe.so).
+ *
+ * One explicit Euler step of a cell-centred finite-volume solver for the 2D
+ * shallow-water equations on an unstructured triangle mesh (Zaoui, "A
+ * GPU-enabled finite volume solver for large shallow water simulations"):
+ *   Sec. 2.1, Eq. 1  state U = (h, hu, hv), physical fluxes G, H, bed slope
+ *                    and Manning friction sources;
+ *   Sec. 2.2, Eq. 2-4 finite volumes on triangles, the face sum
+ *                    sum_k F_k . n_k l_k, explicit Euler update;
+ *   Sec. 2.2         HLLC interface fluxes, hydrostatic reconstruction of the
+ *                    bed, semi-implicit friction, CFL time step (Courant 0.7);
+ *   Sec. 2.3         state and mesh stay on the device; the host only starts
+ *                    steps and copies results at the end.
+ *   Sec. 3           reflective (wall) boundaries on every boundary edge.
+ *
+ * Conventions for every call:
+ *   - Host pointers are plain host memory (pageable or pinned); the library
+ *     copies what it needs and never keeps a caller pointer.
+ *   - Cell arrays are indexed in the CALLER's cell order (the order of `tri`).
+ *     Any renumbering the library does for locality is internal.
+ *   - All work is queued on the CUDA stream given to swe_mesh_create (NULL =
+ *     a stream the library creates). Calls that return results to the host
+ *     synchronise that stream; swe_run does not.
+ *   - Errors are returned as negative swe_status codes, never by abort/trap.
+ *     Device-side conditions (NaN, all-dry) latch an error word that the next
+ *     synchronising call reports.
+ *   - Handles are owned by the caller and freed with the matching destroy.
+ *     A state must be destroyed before its mesh. Handles are not thread-safe.
+ */
+#ifndef SWE_H
+#define SWE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int swe_status;
+
+#define SWE_OK 0
+#define SWE_EINVAL (-1)     /* bad argument (null pointer, negative size, bad enum) */
+#define SWE_EMESH (-2)      /* bad mesh: node index out of range, zero-area triangle,
+                               an edge shared by more than two triangles, empty mesh */
+#define SWE_ENOMEM (-3)     /* device or host allocation failed */
+#define SWE_ECUDA (-4)      /* a CUDA runtime call failed (no device, launch error) */
+#define SWE_ENAN (-5)       /* a non-finite value appeared in the state */
+#define SWE_ETIMEOUT (-7)   /* a bounded device-side wait ran out */
+#define SWE_EDRY (-8)       /* no wet cell left: the CFL time step is undefined */
+#define SWE_ESTATE (-9)     /* call not valid for this handle (e.g. wrong precision) */
+
+/* Arithmetic of the state, the fluxes and the update. */
+typedef enum {
+  SWE_F64 = 0, /* everything in FP64 (the paper's precision, Sec. 3) */
+  SWE_F32 = 1  /* FP32 state and fluxes, compensated per-cell flux sums, FP64 mass
+                  integral and FP64 wet/dry depth tests */
+} swe_precision;
+
+/* Internal cell numbering (locality of the neighbour gathers). */
+typedef enum {
+  SWE_ORDER_NONE = 0,   /* keep the caller's order */
+  SWE_ORDER_MORTON = 1  /* Z-order of the cell centroids; edges follow their cells */
+} swe_order;
+
+/* Kernel structure of one step. */
+typedef enum {
+  SWE_KERNEL_AUTO = 0,  /* SWE_KERNEL_TILED */
+  SWE_KERNEL_EDGE = 1,  /* two launches: per-edge fluxes to HBM, then a per-cell gather
+                           and update (the paper's two parallel loops, Sec. 2.3) */
+  SWE_KERNEL_TILED = 2  /* one launch: each block stages a tile of cells in shared
+                           memory, computes every face flux of the tile once, then
+                           updates its cells */
+} swe_kernel;
+
+typedef struct {
+  double g;           /* gravity, m/s^2 (default 9.81) */
+  double courant;     /* Courant number (default 0.7, Sec. 2.2) */
+  double h_eps;       /* dry threshold in m (default 1e-6): cells at or below it carry
+                         no momentum, reconstructed sides at or below it are dry */
+  int32_t precision;  /* swe_precision (default SWE_F64) */
+  int32_t order;      /* swe_order (default SWE_ORDER_MORTON) */
+  int32_t kernel;     /* swe_kernel (default SWE_KERNEL_AUTO) */
+  int32_t tile;       /* cells per tile of SWE_KERNEL_TILED; 0 = library default */
+} swe_params;
+
+typedef struct swe_mesh swe_mesh;
+typedef struct swe_state swe_state;
+
+/* Fills *p with the defaults listed in swe_params. */
+void swe_params_default(swe_params* p);
+
+/* Builds a device-resident mesh from host arrays.
+ *   xy       [2*n_nodes] node coordinates (x0, y0, x1, y1, ...), metres.
+ *   tri      [3*n_tris]  node ids of each triangle, any orientation (clockwise
+ *            triangles are reoriented).
+ *   params   numerics and layout; NULL = defaults. Copied.
+ *   cuda_stream  a cudaStream_t, or NULL for a library-owned stream.
+ * Builds the edges (interior and wall), the geometry of Eq. 3 (areas, unit
+ * normals, edge lengths, perimeters) in FP64 on the host, renumbers cells and
+ * edges, and uploads everything. Returns SWE_EMESH for an invalid mesh,
+ * SWE_EINVAL for bad arguments. *out receives the handle. */
+swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tris,
+                           const swe_params* params, void* cuda_stream, swe_mesh** out);
+
+/* counts[0..3] = nodes, triangles, edges, wall edges. */
+swe_status swe_mesh_counts(const swe_mesh* mesh, int64_t* counts);
+
+/* Device bytes held by the mesh. */
+swe_status swe_mesh_device_bytes(const swe_mesh* mesh, int64_t* bytes);
+
+void swe_mesh_destroy(swe_mesh* mesh);
+
+/* Creates a state on a mesh from host arrays of n_tris values each, caller order:
+ * depth h (m), discharges hu, hv (m^2/s), bed z (m), per-cell Manning n
+ * (s/m^{1/3}) or NULL to use manning_const everywhere. Sets t = 0 and computes
+ * the first CFL time step. Returns SWE_EDRY if no cell is wet. */
+swe_status swe_state_init(swe_mesh* mesh, const double* h, const double* hu, const double* hv,
+                          const double* z, const double* manning, double manning_const,
+                          swe_state** out);
+
+/* Replaces (h, hu, hv) from host arrays (caller order) and resets t = 0 and
+ * the step count; bed and friction stay. */
+swe_status swe_state_set(swe_state* state, const double* h, const double* hu, const double* hv);
+
+/* One step with the current CFL time step (no end-time clamp). Synchronises;
+ * *dt_used (may be NULL) receives the step's dt. */
+swe_status swe_step(swe_state* state, double* dt_used);
+
+/* Queues n_steps CFL steps without an end time and returns without
+ * synchronising (device errors are reported by the next synchronising call).
+ * Steps are replayed from captured CUDA graphs. */
+swe_status swe_run(swe_state* state, int64_t n_steps);
+
+/* Steps until t == t_end exactly: each step uses min(CFL dt, t_end - t), and
+ * the step that reaches t_end sets t = t_end. Synchronises once per chunk of
+ * graph-replayed steps. *n_steps (may be NULL) receives the steps taken. */
+swe_status swe_advance(swe_state* state, double t_end, int64_t* n_steps);
+
+/* Waits for queued work and returns the latched device status. */
+swe_status swe_sync(swe_state* state);
+
+/* Copies the state to host arrays in caller order (any pointer may be NULL).
+ * *t = simulated time, *mass = sum of area * h in FP64. Synchronises. */
+swe_status swe_copy_out(const swe_state* state, double* h, double* hu, double* hv, double* t,
+                        double* mass);
+
+/* info[0] = steps taken, info[1] = cells whose depth went negative and was
+ * clipped to 0 (expected 0 under the CFL step), info[2] = latched error bits. */
+swe_status swe_state_info(const swe_state* state, int64_t* info);
+
+/* The CFL time step the next swe_step would use (before any end-time clamp). */
+swe_status swe_next_dt(const swe_state* state, double* dt);
+
+void swe_state_destroy(swe_state* state);
+
+/* Static description of a status code. */
+const char* swe_strerror(swe_status status);
+
+/* Message of the last CUDA runtime error seen by this thread ("" if none). */
+const char* swe_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWE_H */

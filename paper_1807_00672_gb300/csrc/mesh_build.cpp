@@ -1,0 +1,283 @@
+// Host-side mesh construction (see mesh_build.h).
+//
+// Geometry of the cell-centred scheme (Sec. 2.2, Eq. 3): for each triangle its
+// area Omega_i and perimeter; for each edge its length l_k and the unit normal
+// n_k pointing out of its left cell. Computed in FP64 from the node
+// coordinates and cast to the device precision at upload.
+//
+// Edge orientation: the left cell of an interior edge is the one with the
+// lower caller index and the normal is taken along that cell's
+// counter-clockwise traversal, so the library's faces are oriented the same
+// way whatever internal numbering it uses.
+//
+// Compiled with -ffp-contract=off so each geometric quantity is the plainly
+// rounded value of its formula.
+#include "mesh_build.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+namespace swe {
+
+namespace {
+
+// Spreads the low 32 bits of x to the even bit positions of a 64-bit word.
+inline uint64_t spread_bits(uint64_t x) {
+  x &= 0xffffffffull;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+}  // namespace
+
+int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t T, int order,
+                    int32_t tile, bool with_edges, HostMesh& m) {
+  if (!xy || !tri_in || V <= 0 || T <= 0) return T == 0 ? -2 : -1;
+  if (T >= (int64_t)INT32_MAX / 3 || V >= (int64_t)INT32_MAX) return -1;
+  m = HostMesh();
+  m.V = V;
+  m.T = T;
+
+  // 1. Validate, orient counter-clockwise, areas.
+  std::vector<int32_t> tri(tri_in, tri_in + 3 * T);
+  std::vector<double> area_c(T);
+  for (int64_t i = 0; i < T; ++i) {
+    int32_t a = tri[3 * i], b = tri[3 * i + 1], c = tri[3 * i + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= V || b >= V || c >= V) return -2;
+    if (a == b || b == c || a == c) return -2;
+    double ax = xy[2 * a], ay = xy[2 * a + 1];
+    double s = 0.5 * ((xy[2 * b] - ax) * (xy[2 * c + 1] - ay) - (xy[2 * c] - ax) * (xy[2 * b + 1] - ay));
+    if (!std::isfinite(s) || s == 0.0) return -2;
+    if (s < 0.0) {
+      tri[3 * i + 1] = c;
+      tri[3 * i + 2] = b;
+      s = -s;
+    }
+    area_c[i] = s;
+  }
+
+  // 2. Half-edges bucketed by their lower node (counting sort), then matched
+  //    within each bucket by their upper node.
+  std::vector<int64_t> start(V + 1, 0);
+  for (int64_t i = 0; i < 3 * T; ++i) {
+    int64_t cell = i / 3;
+    int k = (int)(i % 3);
+    int32_t a = tri[3 * cell + k], b = tri[3 * cell + (k + 1) % 3];
+    start[std::min(a, b) + 1]++;
+  }
+  for (int64_t v = 0; v < V; ++v) start[v + 1] += start[v];
+  std::vector<int64_t> fill(start.begin(), start.end() - 1);
+  std::vector<int64_t> bucket(3 * T);  // half-edge id = 3 * cell + k
+  for (int64_t i = 0; i < 3 * T; ++i) {
+    int64_t cell = i / 3;
+    int k = (int)(i % 3);
+    int32_t a = tri[3 * cell + k], b = tri[3 * cell + (k + 1) % 3];
+    bucket[fill[std::min(a, b)]++] = i;
+  }
+  // edge_of_half[h] = caller-side edge id; edges listed in bucket order.
+  std::vector<int32_t> edge_of_half(3 * T, -1);
+  std::vector<int32_t> cL, cR;  // caller cell ids; cR = -1 for walls
+  std::vector<int8_t> kL;      // face index of the edge within its left cell
+  cL.reserve(3 * T / 2 + 16);
+  cR.reserve(3 * T / 2 + 16);
+  kL.reserve(3 * T / 2 + 16);
+  auto upper = [&](int64_t h) {
+    int64_t cell = h / 3;
+    int k = (int)(h % 3);
+    return std::max(tri[3 * cell + k], tri[3 * cell + (k + 1) % 3]);
+  };
+  for (int64_t v = 0; v < V; ++v) {
+    int64_t b0 = start[v], b1 = start[v + 1];
+    // sort the (few) half-edges of this bucket by (upper node, cell)
+    std::sort(bucket.begin() + b0, bucket.begin() + b1, [&](int64_t p, int64_t q) {
+      int32_t up = upper(p), uq = upper(q);
+      if (up != uq) return up < uq;
+      return p < q;
+    });
+    int64_t j = b0;
+    while (j < b1) {
+      int64_t r = j + 1;
+      while (r < b1 && upper(bucket[r]) == upper(bucket[j])) ++r;
+      if (r - j > 2) return -2;  // non-manifold edge
+      int32_t e = (int32_t)cL.size();
+      int64_t h0 = bucket[j];
+      if (r - j == 2) {
+        int64_t h1 = bucket[j + 1];
+        if (h0 / 3 == h1 / 3) return -2;
+        // h0 < h1 and half-edge ids grow with the cell: h0 is the lower cell
+        cL.push_back((int32_t)(h0 / 3));
+        cR.push_back((int32_t)(h1 / 3));
+        kL.push_back((int8_t)(h0 % 3));
+        edge_of_half[h0] = e;
+        edge_of_half[h1] = e;
+      } else {
+        cL.push_back((int32_t)(h0 / 3));
+        cR.push_back(-1);
+        kL.push_back((int8_t)(h0 % 3));
+        edge_of_half[h0] = e;
+        m.Eb++;
+      }
+      j = r;
+    }
+  }
+  m.E = (int64_t)cL.size();
+
+  // 3. Edge geometry from the left cell's traversal.
+  std::vector<double> gnx(m.E), gny(m.E), glen(m.E);
+  for (int64_t e = 0; e < m.E; ++e) {
+    int32_t c = cL[e];
+    int k = kL[e];
+    int32_t a = tri[3 * (int64_t)c + k], b = tri[3 * (int64_t)c + (k + 1) % 3];
+    double dx = xy[2 * b] - xy[2 * a];
+    double dy = xy[2 * b + 1] - xy[2 * a + 1];
+    double l = std::sqrt(dx * dx + dy * dy);
+    gnx[e] = dy / l;
+    gny[e] = -dx / l;
+    glen[e] = l;
+  }
+
+  // 4. Cell order.
+  m.perm.resize(T);
+  std::iota(m.perm.begin(), m.perm.end(), 0);
+  if (order == 1) {
+    double x0 = xy[0], x1 = xy[0], y0 = xy[1], y1 = xy[1];
+    for (int64_t v = 0; v < V; ++v) {
+      x0 = std::min(x0, xy[2 * v]); x1 = std::max(x1, xy[2 * v]);
+      y0 = std::min(y0, xy[2 * v + 1]); y1 = std::max(y1, xy[2 * v + 1]);
+    }
+    double span = std::max(x1 - x0, y1 - y0);
+    if (!(span > 0.0)) span = 1.0;
+    const double q = 4194303.0;  // 22 bits per axis
+    std::vector<uint64_t> key(T);
+    for (int64_t i = 0; i < T; ++i) {
+      int32_t a = tri[3 * i], b = tri[3 * i + 1], c = tri[3 * i + 2];
+      double cx = (xy[2 * a] + xy[2 * b] + xy[2 * c]) / 3.0;
+      double cy = (xy[2 * a + 1] + xy[2 * b + 1] + xy[2 * c + 1]) / 3.0;
+      uint64_t ix = (uint64_t)std::min(q, std::max(0.0, (cx - x0) / span * q));
+      uint64_t iy = (uint64_t)std::min(q, std::max(0.0, (cy - y0) / span * q));
+      key[i] = spread_bits(ix) | (spread_bits(iy) << 1);
+    }
+    std::stable_sort(m.perm.begin(), m.perm.end(),
+                     [&](int32_t p, int32_t r) { return key[p] < key[r]; });
+  } else if (order != 0) {
+    return -1;
+  }
+  m.iperm.resize(T);
+  for (int64_t j = 0; j < T; ++j) m.iperm[m.perm[j]] = (int32_t)j;
+
+  // 5. Internal-order cell data: area and perimeter (faces k = 0, 1, 2).
+  m.area.resize(T);
+  m.perim.resize(T);
+  for (int64_t j = 0; j < T; ++j) {
+    int64_t i = m.perm[j];
+    double p = 0.0;
+    for (int k = 0; k < 3; ++k) p = p + glen[edge_of_half[3 * i + k]];
+    m.area[j] = area_c[i];
+    m.perim[j] = p;
+  }
+
+  // 6. Two-launch layout: edges sorted by their lower internal cell.
+  if (with_edges) {
+    std::vector<int64_t> ekey(m.E);
+    for (int64_t e = 0; e < m.E; ++e) {
+      int64_t a = m.iperm[cL[e]];
+      int64_t b = cR[e] >= 0 ? m.iperm[cR[e]] : a;
+      ekey[e] = (std::min(a, b) << 32) | std::max(a, b);
+    }
+    std::vector<int32_t> eorder(m.E);
+    std::iota(eorder.begin(), eorder.end(), 0);
+    std::stable_sort(eorder.begin(), eorder.end(),
+                     [&](int32_t p, int32_t r) { return ekey[p] < ekey[r]; });
+    std::vector<int32_t> enew(m.E);
+    m.eL.resize(m.E); m.eR.resize(m.E); m.nx.resize(m.E); m.ny.resize(m.E); m.len.resize(m.E);
+    for (int64_t s = 0; s < m.E; ++s) {
+      int32_t e = eorder[s];
+      enew[e] = (int32_t)s;
+      m.eL[s] = m.iperm[cL[e]];
+      m.eR[s] = cR[e] >= 0 ? m.iperm[cR[e]] : -1;
+      m.nx[s] = gnx[e]; m.ny[s] = gny[e]; m.len[s] = glen[e];
+    }
+    for (int k = 0; k < 3; ++k) m.cface[k].resize(T);
+    for (int64_t j = 0; j < T; ++j) {
+      int64_t i = m.perm[j];
+      for (int k = 0; k < 3; ++k) {
+        int32_t e = edge_of_half[3 * i + k];
+        bool right = (cL[e] != i);
+        m.cface[k][j] = enew[e] | (right ? (int32_t)0x80000000 : 0);
+      }
+    }
+  }
+
+  // 7. Tiled layout.
+  if (tile > 0) {
+    if (tile % 32 != 0 || 3 * (int64_t)tile > 32767) return -1;
+    m.tile = tile;
+    m.ntiles = (T + tile - 1) / tile;
+    m.toff.assign(m.ntiles + 1, 0);
+    // Records per tile: every face of every tile cell, an interior face whose
+    // both cells lie in the tile counted once.
+    std::vector<int64_t> cnt(m.ntiles, 0);
+    for (int64_t e = 0; e < m.E; ++e) {
+      int64_t ta = m.iperm[cL[e]] / tile;
+      cnt[ta]++;
+      if (cR[e] >= 0) {
+        int64_t tb = m.iperm[cR[e]] / tile;
+        if (tb != ta) cnt[tb]++;
+      }
+    }
+    for (int64_t t = 0; t < m.ntiles; ++t) {
+      int64_t padded = (cnt[t] + 3) / 4 * 4;
+      m.null_records += padded - cnt[t];
+      m.toff[t + 1] = m.toff[t] + padded;
+    }
+    int64_t R = m.toff[m.ntiles];
+    m.tA.assign(R, kWall);
+    m.tB.assign(R, kWall);
+    m.tnx.assign(R, 0.0);
+    m.tny.assign(R, 0.0);
+    m.tlen.assign(R, 0.0);  // null records: zero length, both sides "wall"
+    std::vector<int64_t> pos(m.toff.begin(), m.toff.end() - 1);
+    // Walk the tile cells in internal order so records follow their cells.
+    for (int64_t j = 0; j < T; ++j) {
+      int64_t i = m.perm[j];
+      int64_t t = j / tile;
+      for (int k = 0; k < 3; ++k) {
+        int32_t e = edge_of_half[3 * i + k];
+        bool right = (cL[e] != i);
+        int32_t other = right ? cL[e] : cR[e];
+        int64_t jo = other >= 0 ? m.iperm[other] : -1;
+        bool other_local = (jo >= 0 && jo / tile == t);
+        // An interior face inside the tile is emitted once, by its left cell.
+        if (right && other_local) continue;
+        int32_t slot_self = -1 - (int32_t)((j - t * tile) * 3 + k);
+        int32_t enc_other;
+        if (jo < 0) {
+          enc_other = kWall;
+        } else if (other_local) {
+          // the other cell's face index for this edge
+          int ko = -1;
+          for (int kk = 0; kk < 3; ++kk)
+            if (edge_of_half[3 * (int64_t)other + kk] == e) ko = kk;
+          enc_other = -1 - (int32_t)((jo - t * tile) * 3 + ko);
+        } else {
+          enc_other = (int32_t)jo;
+        }
+        int64_t r = pos[t]++;
+        // side A is always the edge's left cell
+        if (!right) { m.tA[r] = slot_self; m.tB[r] = enc_other; }
+        else        { m.tA[r] = enc_other; m.tB[r] = slot_self; }
+        m.tnx[r] = gnx[e];
+        m.tny[r] = gny[e];
+        m.tlen[r] = glen[e];
+      }
+    }
+  }
+  return 0;
+}
+
+}  // namespace swe

@@ -1,0 +1,46 @@
+// Host-side mesh construction for the CUDA step: edges, FP64 geometry,
+// locality renumbering and per-tile face lists. No CUDA in here.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace swe {
+
+// Encoding of one side of a tile face record:
+//   >= 0             global (internal) index of a cell outside the tile
+//   kWall            wall (mirror ghost)
+//   < 0, != kWall    local face slot s = -1 - value (cell s / 3, face s % 3)
+constexpr int32_t kWall = INT32_MIN;
+
+struct HostMesh {
+  int64_t V = 0, T = 0, E = 0, Eb = 0;
+  // perm[j] = caller index of internal cell j; iperm is its inverse.
+  std::vector<int32_t> perm, iperm;
+  // Internal-order cell data (FP64).
+  std::vector<double> area, perim;
+  // Two-launch layout: edges in internal order, and per cell the ids of its
+  // three faces (face k joins the cell's oriented nodes k and k+1), with bit 31
+  // set when the cell is the edge's right side.
+  std::vector<int32_t> eL, eR;   // eR = -1 for a wall
+  std::vector<double> nx, ny, len;
+  std::vector<int32_t> cface[3];
+  // Tiled layout: tiles of `tile` consecutive internal cells; for tile t the
+  // face records [toff[t], toff[t+1]) (each tile's start padded to a multiple
+  // of 4 records with null records), each with two encoded sides and the
+  // edge's geometry oriented from side A to side B.
+  int32_t tile = 0;
+  int64_t ntiles = 0;
+  std::vector<int64_t> toff;
+  std::vector<int32_t> tA, tB;
+  std::vector<double> tnx, tny, tlen;
+  int64_t null_records = 0;
+};
+
+// Returns 0 or a negative status: -1 bad arguments, -2 invalid mesh.
+// order: 0 = caller order, 1 = Morton order of centroids.
+// tile > 0 also builds the tiled layout; with_edges builds the two-launch one.
+int build_host_mesh(const double* xy, int64_t V, const int32_t* tri, int64_t T, int order,
+                    int32_t tile, bool with_edges, HostMesh& out);
+
+}  // namespace swe

@@ -1,0 +1,672 @@
+// C ABI of the shallow-water step library (declared in include/swe.h).
+//
+// Handles own one device arena each (mesh: geometry and connectivity; state:
+// two state buffers, bed, friction, scratch and the control word). Steps are
+// queued on the mesh's stream; repeated steps replay a captured CUDA graph of
+// kStepsPerGraph steps. Kernels pick the current buffer, dt and the stop flag
+// from the control word, so one graph serves any step count and end time
+// (the host crosses PCIe/C2C only at set-up and copy-out, Sec. 2.3).
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "../../include/swe.h"
+#include "mesh_build.h"
+#include "swe_kernels.cuh"
+
+namespace {
+
+constexpr int kStepsPerGraph = 16;
+constexpr int kDefaultTile = 256;
+
+thread_local std::string g_cuda_msg;
+
+bool cuda_failed_at(cudaError_t e, const char* what, int line) {
+  if (e == cudaSuccess) return false;
+  g_cuda_msg = std::string(cudaGetErrorString(e)) + " in " + what + " (swe_api.cu:" +
+               std::to_string(line) + ")";
+  return true;
+}
+#define cuda_failed(call) cuda_failed_at((call), #call, __LINE__)
+
+#define CK(call)                                  \
+  do {                                            \
+    if (cuda_failed(call)) return SWE_ECUDA;      \
+  } while (0)
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Bump allocator over one cudaMalloc. take() returns nullptr (and sets
+// overflow) instead of handing out memory past the allocation.
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  bool overflow = false;
+  void* take(size_t bytes) {
+    if (used + align_up(bytes) > size) {
+      overflow = true;
+      return nullptr;
+    }
+    void* p = base + used;
+    used += align_up(bytes);
+    return p;
+  }
+};
+
+struct Layout {
+  size_t total = 0;
+  void add(size_t bytes) { total += align_up(bytes); }
+};
+
+}  // namespace
+
+struct swe_mesh {
+  swe_params prm{};
+  int device = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t V = 0, T = 0, E = 0, Eb = 0;
+  int kernel = SWE_KERNEL_TILED;
+  int tile = kDefaultTile;
+  int64_t ntiles = 0, records = 0;
+  Arena arena;
+  int32_t* perm = nullptr;
+  void* area = nullptr;
+  void* irP = nullptr;
+  int32_t *eL = nullptr, *eR = nullptr, *cf[3] = {nullptr, nullptr, nullptr};
+  void *nx = nullptr, *ny = nullptr, *len = nullptr;
+  int64_t* toff = nullptr;
+  int32_t *tA = nullptr, *tB = nullptr;
+  void *tnx = nullptr, *tny = nullptr, *tlen = nullptr;
+  int grid_edge = 1, grid_cell = 1, grid_tiled = 1, grid_cfl = 1, max_grid = 1;
+};
+
+struct swe_state {
+  swe_mesh* mesh = nullptr;
+  Arena arena;
+  void *h[2] = {nullptr, nullptr}, *hu[2] = {nullptr, nullptr}, *hv[2] = {nullptr, nullptr};
+  void *z = nullptr, *gn2 = nullptr;
+  void* fx[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* partial = nullptr;
+  double* stage = nullptr;  // T doubles in caller order
+  swe::Ctl* ctl = nullptr;
+  swe::Ctl* host_ctl = nullptr;  // pinned mirror
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool open_ended = true;  // the device t_end is +inf
+};
+
+namespace {
+
+swe::Num num_of(const swe_mesh* m) { return swe::Num{m->prm.g, m->prm.courant, m->prm.h_eps}; }
+
+template <typename Real>
+swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
+  swe::DevMesh<Real> d{};
+  d.T = m->T;
+  d.E = m->E;
+  d.area = (const Real*)m->area;
+  d.irP = (const Real*)m->irP;
+  d.eL = m->eL;
+  d.eR = m->eR;
+  d.nx = (const Real*)m->nx;
+  d.ny = (const Real*)m->ny;
+  d.len = (const Real*)m->len;
+  d.cf0 = m->cf[0];
+  d.cf1 = m->cf[1];
+  d.cf2 = m->cf[2];
+  d.ntiles = m->ntiles;
+  d.toff = m->toff;
+  d.tA = m->tA;
+  d.tB = m->tB;
+  d.tnx = (const Real*)m->tnx;
+  d.tny = (const Real*)m->tny;
+  d.tlen = (const Real*)m->tlen;
+  return d;
+}
+
+template <typename Real>
+swe::DevState<Real> dev_state(const swe_state* s) {
+  swe::DevState<Real> d{};
+  for (int b = 0; b < 2; ++b) {
+    d.h[b] = (Real*)s->h[b];
+    d.hu[b] = (Real*)s->hu[b];
+    d.hv[b] = (Real*)s->hv[b];
+  }
+  d.z = (const Real*)s->z;
+  d.gn2 = (const Real*)s->gn2;
+  for (int k = 0; k < 5; ++k) d.fx[k] = (Real*)s->fx[k];
+  d.partial = s->partial;
+  d.ctl = s->ctl;
+  return d;
+}
+
+int grid_for(int64_t n, int threads, int cap) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+template <typename Real>
+int blocks_per_sm_tiled(int tile) {
+  int n = 0;
+  constexpr bool comp = sizeof(Real) == 4;
+  if (tile == 128)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swe::k_tiled_step<Real, comp, 128>, 128, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swe::k_tiled_step<Real, comp, 256>, 256, 0);
+  return n > 0 ? n : 1;
+}
+
+template <typename Real>
+void set_grids(swe_mesh* m) {
+  int occ_cell = 0, occ_edge = 0, occ_cfl = 0;
+  constexpr bool comp = sizeof(Real) == 4;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cell, swe::k_cell_update<Real, comp>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_edge, swe::k_edge_flux<Real>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cfl, swe::k_cfl<Real>, 256, 0);
+  occ_cell = occ_cell > 0 ? occ_cell : 1;
+  occ_edge = occ_edge > 0 ? occ_edge : 1;
+  occ_cfl = occ_cfl > 0 ? occ_cfl : 1;
+  m->grid_edge = grid_for(m->E, 256, m->sms * occ_edge * 4);
+  m->grid_cell = grid_for(m->T, 256, m->sms * occ_cell);
+  m->grid_cfl = grid_for(m->T, 256, m->sms * occ_cfl);
+  if (m->kernel == SWE_KERNEL_TILED) {
+    int64_t g = (int64_t)m->sms * blocks_per_sm_tiled<Real>(m->tile);
+    m->grid_tiled = (int)(m->ntiles < g ? m->ntiles : g);
+    if (m->grid_tiled < 1) m->grid_tiled = 1;
+  }
+  m->max_grid = std::max(std::max(m->grid_cell, m->grid_cfl), m->grid_tiled);
+}
+
+template <typename Real>
+void launch_step(const swe_state* s, cudaStream_t st) {
+  const swe_mesh* m = s->mesh;
+  constexpr bool comp = sizeof(Real) == 4;
+  swe::DevMesh<Real> dm = dev_mesh<Real>(m);
+  swe::DevState<Real> ds = dev_state<Real>(s);
+  swe::Num num = num_of(m);
+  if (m->kernel == SWE_KERNEL_EDGE) {
+    swe::k_edge_flux<Real><<<m->grid_edge, 256, 0, st>>>(dm, ds, num);
+    swe::k_cell_update<Real, comp><<<m->grid_cell, 256, 0, st>>>(dm, ds, num);
+  } else if (m->tile == 128) {
+    swe::k_tiled_step<Real, comp, 128><<<m->grid_tiled, 128, 0, st>>>(dm, ds, num);
+  } else {
+    swe::k_tiled_step<Real, comp, 256><<<m->grid_tiled, 256, 0, st>>>(dm, ds, num);
+  }
+}
+
+void launch_one_step(const swe_state* s, cudaStream_t st) {
+  if (s->mesh->prm.precision == SWE_F64) launch_step<double>(s, st);
+  else launch_step<float>(s, st);
+}
+
+template <typename Real>
+void launch_cfl(const swe_state* s) {
+  const swe_mesh* m = s->mesh;
+  swe::k_cfl<Real><<<m->grid_cfl, 256, 0, m->stream>>>(dev_mesh<Real>(m), dev_state<Real>(s), num_of(m));
+}
+
+template <typename Real>
+void launch_gather(const swe_mesh* m, const double* src, void* dst) {
+  swe::k_gather<Real><<<grid_for(m->T, 256, m->sms * 16), 256, 0, m->stream>>>(src, m->perm, (Real*)dst, m->T);
+}
+
+template <typename Real>
+void launch_scatter(const swe_mesh* m, const void* src, double* dst) {
+  swe::k_scatter<Real><<<grid_for(m->T, 256, m->sms * 16), 256, 0, m->stream>>>((const Real*)src, m->perm, dst, m->T);
+}
+
+size_t real_size(const swe_mesh* m) { return m->prm.precision == SWE_F64 ? 8 : 4; }
+
+// Host FP64 vector -> device array of the mesh precision.
+swe_status upload_real(const swe_mesh* m, const std::vector<double>& v, void* dst) {
+  if (v.empty()) return SWE_OK;
+  if (m->prm.precision == SWE_F64) {
+    CK(cudaMemcpyAsync(dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice, m->stream));
+  } else {
+    std::vector<float> f(v.size());
+    for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
+    CK(cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaStreamSynchronize(m->stream));  // f goes out of scope
+  }
+  return SWE_OK;
+}
+
+template <typename T>
+swe_status upload(const swe_mesh* m, const std::vector<T>& v, void* dst) {
+  if (v.empty()) return SWE_OK;
+  CK(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, m->stream));
+  return SWE_OK;
+}
+
+swe_status status_from_ctl(const swe::Ctl& c) {
+  if (c.err & swe::kErrNan) return SWE_ENAN;
+  if (c.err & swe::kErrDry) return SWE_EDRY;
+  return SWE_OK;
+}
+
+swe_status read_ctl(const swe_state* s) {
+  CK(cudaMemcpyAsync(s->host_ctl, s->ctl, sizeof(swe::Ctl), cudaMemcpyDeviceToHost, s->mesh->stream));
+  CK(cudaStreamSynchronize(s->mesh->stream));
+  return SWE_OK;
+}
+
+swe_status ensure_graph(swe_state* s) {
+  if (s->graph) return SWE_OK;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < kStepsPerGraph; ++k) launch_one_step(s, s->capture);
+  cudaError_t e = cudaStreamEndCapture(s->capture, &g);
+  if (cuda_failed(e)) return SWE_ECUDA;
+  e = cudaGraphInstantiate(&s->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (cuda_failed(e)) { s->graph = nullptr; return SWE_ECUDA; }
+  return SWE_OK;
+}
+
+// Queues n steps: whole graphs, then single launches for the remainder.
+swe_status queue_steps(swe_state* s, int64_t n) {
+  cudaStream_t st = s->mesh->stream;
+  if (n >= kStepsPerGraph) {
+    swe_status r = ensure_graph(s);
+    if (r != SWE_OK) return r;
+    for (int64_t k = 0; k < n / kStepsPerGraph; ++k) CK(cudaGraphLaunch(s->graph, st));
+    n %= kStepsPerGraph;
+  }
+  for (int64_t k = 0; k < n; ++k) launch_one_step(s, st);
+  CK(cudaGetLastError());
+  return SWE_OK;
+}
+
+// Makes the device end time +inf (no clamp) unless it already is.
+void open_end(swe_state* s) {
+  if (s->open_ended) return;
+  swe::k_set_end<<<1, 1, 0, s->mesh->stream>>>(s->ctl, std::numeric_limits<double>::infinity());
+  s->open_ended = true;
+}
+
+swe_status upload_state_fields(swe_state* s, const double* h, const double* hu, const double* hv) {
+  const swe_mesh* m = s->mesh;
+  const double* src[3] = {h, hu, hv};
+  void* dst[3] = {s->h[0], s->hu[0], s->hv[0]};
+  for (int k = 0; k < 3; ++k) {
+    CK(cudaMemcpyAsync(s->stage, src[k], m->T * 8, cudaMemcpyHostToDevice, m->stream));
+    if (m->prm.precision == SWE_F64) launch_gather<double>(m, s->stage, dst[k]);
+    else launch_gather<float>(m, s->stage, dst[k]);
+  }
+  CK(cudaGetLastError());
+  return SWE_OK;
+}
+
+// Resets the control word to t = 0 in buffer 0 and computes dt and mass.
+swe_status reset_and_cfl(swe_state* s) {
+  const swe_mesh* m = s->mesh;
+  swe::Ctl c{};
+  c.t = 0.0;
+  c.t_end = std::numeric_limits<double>::infinity();
+  s->open_ended = true;
+  *s->host_ctl = c;
+  CK(cudaMemcpyAsync(s->ctl, s->host_ctl, sizeof(swe::Ctl), cudaMemcpyHostToDevice, m->stream));
+  if (m->prm.precision == SWE_F64) launch_cfl<double>(s);
+  else launch_cfl<float>(s);
+  CK(cudaGetLastError());
+  swe_status r = read_ctl(s);
+  if (r != SWE_OK) return r;
+  return status_from_ctl(*s->host_ctl);
+}
+
+}  // namespace
+
+extern "C" {
+
+void swe_params_default(swe_params* p) {
+  if (!p) return;
+  p->g = 9.81;
+  p->courant = 0.7;
+  p->h_eps = 1e-6;
+  p->precision = SWE_F64;
+  p->order = SWE_ORDER_MORTON;
+  p->kernel = SWE_KERNEL_AUTO;
+  p->tile = 0;
+}
+
+const char* swe_strerror(swe_status s) {
+  switch (s) {
+    case SWE_OK: return "ok";
+    case SWE_EINVAL: return "invalid argument";
+    case SWE_EMESH: return "invalid mesh";
+    case SWE_ENOMEM: return "out of memory";
+    case SWE_ECUDA: return "CUDA error";
+    case SWE_ENAN: return "non-finite value in the state";
+    case SWE_ETIMEOUT: return "device wait timed out";
+    case SWE_EDRY: return "no wet cell: CFL time step undefined";
+    case SWE_ESTATE: return "call not valid for this handle";
+    default: return "unknown status";
+  }
+}
+
+const char* swe_last_cuda_error(void) { return g_cuda_msg.c_str(); }
+
+swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tris,
+                           const swe_params* params, void* cuda_stream, swe_mesh** out) {
+  if (!out) return SWE_EINVAL;
+  *out = nullptr;
+  if (n_tris == 0) return SWE_EMESH;
+  if (!xy || !tri || n_nodes <= 0 || n_tris < 0) return SWE_EINVAL;
+  swe_params p;
+  swe_params_default(&p);
+  if (params) p = *params;
+  if (p.precision != SWE_F64 && p.precision != SWE_F32) return SWE_EINVAL;
+  if (p.order != SWE_ORDER_NONE && p.order != SWE_ORDER_MORTON) return SWE_EINVAL;
+  if (p.kernel < SWE_KERNEL_AUTO || p.kernel > SWE_KERNEL_TILED) return SWE_EINVAL;
+  if (p.tile == 0) p.tile = kDefaultTile;
+  if (p.tile != 128 && p.tile != 256) return SWE_EINVAL;
+  if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
+  const int kernel = (p.kernel == SWE_KERNEL_EDGE) ? SWE_KERNEL_EDGE : SWE_KERNEL_TILED;
+
+  // Host-side construction and validation first: no device is touched for
+  // an invalid mesh.
+  swe::HostMesh hm;
+  int rc = swe::build_host_mesh(xy, n_nodes, tri, n_tris, p.order,
+                                kernel == SWE_KERNEL_TILED ? p.tile : 0,
+                                kernel == SWE_KERNEL_EDGE, hm);
+  if (rc == -2) return SWE_EMESH;
+  if (rc != 0) return SWE_EINVAL;
+
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+  swe_mesh* m = new swe_mesh();
+  m->prm = p;
+  m->device = dev;
+  m->sms = sms;
+  m->V = hm.V; m->T = hm.T; m->E = hm.E; m->Eb = hm.Eb;
+  m->kernel = kernel;
+  m->tile = p.tile;
+  m->ntiles = hm.ntiles;
+  m->records = (int64_t)hm.tA.size();
+  if (cuda_stream) {
+    m->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cuda_failed(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking))) {
+      delete m;
+      return SWE_ECUDA;
+    }
+    m->own_stream = true;
+  }
+  const size_t w = real_size(m);
+  const int64_t T = m->T, E = m->E, R = m->records;
+  Layout L;
+  L.add(4 * T);  // perm
+  L.add(w * T);  // area
+  L.add(w * T);  // irP
+  if (kernel == SWE_KERNEL_EDGE) {
+    L.add(4 * E); L.add(4 * E);
+    L.add(w * E); L.add(w * E); L.add(w * E);
+    L.add(4 * T); L.add(4 * T); L.add(4 * T);
+  } else {
+    L.add(8 * (m->ntiles + 1));
+    L.add(4 * R); L.add(4 * R);
+    L.add(w * R); L.add(w * R); L.add(w * R);
+  }
+  if (cudaMalloc((void**)&m->arena.base, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    swe_mesh_destroy(m);
+    return SWE_ENOMEM;
+  }
+  m->arena.size = L.total;
+  m->perm = (int32_t*)m->arena.take(4 * T);
+  m->area = m->arena.take(w * T);
+  m->irP = m->arena.take(w * T);
+  std::vector<double> irp(T);
+  for (int64_t j = 0; j < T; ++j) irp[j] = hm.perim[j] / hm.area[j];
+  swe_status st = SWE_OK;
+  auto chk = [&](swe_status s) { if (st == SWE_OK) st = s; };
+  auto carved = [&]() { if (m->arena.overflow && st == SWE_OK) { g_cuda_msg = "mesh arena layout"; st = SWE_ECUDA; } return st == SWE_OK; };
+  if (!carved()) { swe_mesh_destroy(m); return st; }
+  chk(upload(m, hm.perm, m->perm));
+  chk(upload_real(m, hm.area, m->area));
+  chk(upload_real(m, irp, m->irP));
+  if (kernel == SWE_KERNEL_EDGE) {
+    m->eL = (int32_t*)m->arena.take(4 * E);
+    m->eR = (int32_t*)m->arena.take(4 * E);
+    m->nx = m->arena.take(w * E);
+    m->ny = m->arena.take(w * E);
+    m->len = m->arena.take(w * E);
+    for (int k = 0; k < 3; ++k) m->cf[k] = (int32_t*)m->arena.take(4 * T);
+    if (!carved()) { swe_mesh_destroy(m); return st; }
+    chk(upload(m, hm.eL, m->eL));
+    chk(upload(m, hm.eR, m->eR));
+    chk(upload_real(m, hm.nx, m->nx));
+    chk(upload_real(m, hm.ny, m->ny));
+    chk(upload_real(m, hm.len, m->len));
+    for (int k = 0; k < 3; ++k) chk(upload(m, hm.cface[k], m->cf[k]));
+  } else {
+    m->toff = (int64_t*)m->arena.take(8 * (m->ntiles + 1));
+    m->tA = (int32_t*)m->arena.take(4 * R);
+    m->tB = (int32_t*)m->arena.take(4 * R);
+    m->tnx = m->arena.take(w * R);
+    m->tny = m->arena.take(w * R);
+    m->tlen = m->arena.take(w * R);
+    if (!carved()) { swe_mesh_destroy(m); return st; }
+    chk(upload(m, hm.toff, m->toff));
+    chk(upload(m, hm.tA, m->tA));
+    chk(upload(m, hm.tB, m->tB));
+    chk(upload_real(m, hm.tnx, m->tnx));
+    chk(upload_real(m, hm.tny, m->tny));
+    chk(upload_real(m, hm.tlen, m->tlen));
+  }
+  if (st == SWE_OK && cuda_failed(cudaStreamSynchronize(m->stream))) st = SWE_ECUDA;
+  if (st != SWE_OK) {
+    swe_mesh_destroy(m);
+    return st;
+  }
+  if (p.precision == SWE_F64) set_grids<double>(m);
+  else set_grids<float>(m);
+  *out = m;
+  return SWE_OK;
+}
+
+swe_status swe_mesh_counts(const swe_mesh* m, int64_t* counts) {
+  if (!m || !counts) return SWE_EINVAL;
+  counts[0] = m->V; counts[1] = m->T; counts[2] = m->E; counts[3] = m->Eb;
+  return SWE_OK;
+}
+
+swe_status swe_mesh_device_bytes(const swe_mesh* m, int64_t* bytes) {
+  if (!m || !bytes) return SWE_EINVAL;
+  *bytes = (int64_t)m->arena.size;
+  return SWE_OK;
+}
+
+void swe_mesh_destroy(swe_mesh* m) {
+  if (!m) return;
+  if (m->arena.base) cudaFree(m->arena.base);
+  if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+  delete m;
+}
+
+swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const double* hv,
+                          const double* z, const double* manning, double manning_const,
+                          swe_state** out) {
+  if (!out) return SWE_EINVAL;
+  *out = nullptr;
+  if (!m || !h || !hu || !hv || !z) return SWE_EINVAL;
+  if (!manning && !(manning_const >= 0.0)) return SWE_EINVAL;
+  const size_t w = real_size(m);
+  const int64_t T = m->T, E = m->E;
+  swe_state* s = new swe_state();
+  s->mesh = m;
+  Layout L;
+  for (int k = 0; k < 6; ++k) L.add(w * T);  // h, hu, hv x 2
+  L.add(w * T); L.add(w * T);                // z, gn2
+  if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) L.add(w * E);
+  L.add(8 * (size_t)m->max_grid);
+  L.add(8 * T);                              // staging
+  L.add(sizeof(swe::Ctl));
+  if (cudaMalloc((void**)&s->arena.base, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return SWE_ENOMEM;
+  }
+  s->arena.size = L.total;
+  for (int b = 0; b < 2; ++b) {
+    s->h[b] = s->arena.take(w * T);
+    s->hu[b] = s->arena.take(w * T);
+    s->hv[b] = s->arena.take(w * T);
+  }
+  s->z = s->arena.take(w * T);
+  s->gn2 = s->arena.take(w * T);
+  if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) s->fx[k] = s->arena.take(w * E);
+  s->partial = (double*)s->arena.take(8 * (size_t)m->max_grid);
+  s->stage = (double*)s->arena.take(8 * T);
+  s->ctl = (swe::Ctl*)s->arena.take(sizeof(swe::Ctl));
+  swe_status st = SWE_OK;
+  if (s->arena.overflow) {
+    g_cuda_msg = "state arena layout";
+    swe_state_destroy(s);
+    return SWE_ECUDA;
+  }
+  if (cudaMallocHost((void**)&s->host_ctl, sizeof(swe::Ctl)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    swe_state_destroy(s);
+    return SWE_ECUDA;
+  }
+  // Bed and friction coefficient g n^2 (FP64 on the host, caller order).
+  std::vector<double> gn2(T);
+  for (int64_t i = 0; i < T; ++i) {
+    const double n = manning ? manning[i] : manning_const;
+    gn2[i] = m->prm.g * (n * n);
+  }
+  const double* fields[2] = {z, gn2.data()};
+  void* dsts[2] = {s->z, s->gn2};
+  for (int k = 0; k < 2 && st == SWE_OK; ++k) {
+    if (cuda_failed(cudaMemcpyAsync(s->stage, fields[k], T * 8, cudaMemcpyHostToDevice, m->stream))) {
+      st = SWE_ECUDA;
+      break;
+    }
+    if (m->prm.precision == SWE_F64) launch_gather<double>(m, s->stage, dsts[k]);
+    else launch_gather<float>(m, s->stage, dsts[k]);
+  }
+  if (st == SWE_OK && cuda_failed(cudaStreamSynchronize(m->stream))) st = SWE_ECUDA;
+  if (st == SWE_OK) st = upload_state_fields(s, h, hu, hv);
+  if (st == SWE_OK) st = reset_and_cfl(s);
+  if (st != SWE_OK) {
+    swe_state_destroy(s);
+    return st;
+  }
+  *out = s;
+  return SWE_OK;
+}
+
+swe_status swe_state_set(swe_state* s, const double* h, const double* hu, const double* hv) {
+  if (!s || !h || !hu || !hv) return SWE_EINVAL;
+  swe_status st = upload_state_fields(s, h, hu, hv);
+  if (st != SWE_OK) return st;
+  return reset_and_cfl(s);
+}
+
+swe_status swe_step(swe_state* s, double* dt_used) {
+  if (!s) return SWE_EINVAL;
+  swe_status st = swe_sync(s);
+  if (st != SWE_OK) return st;
+  cudaStream_t str = s->mesh->stream;
+  open_end(s);
+  launch_one_step(s, str);
+  CK(cudaGetLastError());
+  st = read_ctl(s);
+  if (st != SWE_OK) return st;
+  if (dt_used) *dt_used = s->host_ctl->dt_last;
+  return status_from_ctl(*s->host_ctl);
+}
+
+swe_status swe_run(swe_state* s, int64_t n_steps) {
+  if (!s || n_steps < 0) return SWE_EINVAL;
+  open_end(s);
+  return queue_steps(s, n_steps);
+}
+
+swe_status swe_advance(swe_state* s, double t_end, int64_t* n_steps) {
+  if (!s || !(t_end == t_end)) return SWE_EINVAL;
+  swe_status st = read_ctl(s);
+  if (st != SWE_OK) return st;
+  const long long start = s->host_ctl->steps;
+  swe::k_set_end<<<1, 1, 0, s->mesh->stream>>>(s->ctl, t_end);
+  s->open_ended = false;
+  CK(cudaGetLastError());
+  for (;;) {
+    st = read_ctl(s);
+    if (st != SWE_OK) return st;
+    if (s->host_ctl->done) break;
+    st = queue_steps(s, kStepsPerGraph);
+    if (st != SWE_OK) return st;
+  }
+  if (n_steps) *n_steps = s->host_ctl->steps - start;
+  return status_from_ctl(*s->host_ctl);
+}
+
+swe_status swe_sync(swe_state* s) {
+  if (!s) return SWE_EINVAL;
+  swe_status st = read_ctl(s);
+  if (st != SWE_OK) return st;
+  return status_from_ctl(*s->host_ctl);
+}
+
+swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, double* t,
+                        double* mass) {
+  if (!s) return SWE_EINVAL;
+  const swe_mesh* m = s->mesh;
+  swe_status st = read_ctl(s);
+  if (st != SWE_OK) return st;
+  const int cur = s->host_ctl->cur;
+  double* dst[3] = {h, hu, hv};
+  const void* src[3] = {s->h[cur], s->hu[cur], s->hv[cur]};
+  for (int k = 0; k < 3; ++k) {
+    if (!dst[k]) continue;
+    if (m->prm.precision == SWE_F64) launch_scatter<double>(m, src[k], s->stage);
+    else launch_scatter<float>(m, src[k], s->stage);
+    CK(cudaMemcpyAsync(dst[k], s->stage, m->T * 8, cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+  }
+  if (t) *t = s->host_ctl->t;
+  if (mass) *mass = s->host_ctl->mass;
+  return status_from_ctl(*s->host_ctl);
+}
+
+swe_status swe_state_info(const swe_state* s, int64_t* info) {
+  if (!s || !info) return SWE_EINVAL;
+  swe_status st = read_ctl(s);
+  if (st != SWE_OK) return st;
+  info[0] = s->host_ctl->steps;
+  info[1] = s->host_ctl->neg;
+  info[2] = s->host_ctl->err;
+  return SWE_OK;
+}
+
+swe_status swe_next_dt(const swe_state* s, double* dt) {
+  if (!s || !dt) return SWE_EINVAL;
+  swe_status st = read_ctl(s);
+  if (st != SWE_OK) return st;
+  *dt = s->host_ctl->dt_cfl;
+  return status_from_ctl(*s->host_ctl);
+}
+
+void swe_state_destroy(swe_state* s) {
+  if (!s) return;
+  if (s->mesh && s->mesh->stream) cudaStreamSynchronize(s->mesh->stream);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->capture) cudaStreamDestroy(s->capture);
+  if (s->host_ctl) cudaFreeHost(s->host_ctl);
+  if (s->arena.base) cudaFree(s->arena.base);
+  delete s;
+}
+
+}  // extern "C"

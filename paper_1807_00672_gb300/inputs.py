@@ -170,19 +170,23 @@ def _gaussian_humps(c: np.ndarray, rng, k: int, lx: float, ly: float,
 def humps_case(nx: int = 1000, ny: int = 500, *, lx: float = 10_000.0, ly: float = 5_000.0,
                eta0: float = 2.0, bump: float = 1.0, bump_size: float = 1_000.0,
                manning: float = 0.03, jitter: float = 0.3, seed: int = 2,
-               fully_wet: bool = False) -> Case:
+               fully_wet: bool = False, dry_top: float = 0.3) -> Case:
     """Jittered grid, bed = 3 Gaussian humps (0.5-2 m, sigma 300-800 m).
 
     Free surface eta0 with +bump inside a bump_size square at the domain
-    centre; h = max(0, eta - z), so hump tops above the surface start dry.
-    ``fully_wet`` raises the surface to max(z) + 1 m (+bump) instead, which
-    gives h >= 1 m everywhere. Sizes scale the hump widths with the domain.
+    centre; h = max(0, eta - z). The bed is shifted vertically so that its
+    highest point lies dry_top above eta0, so the highest hump starts with a
+    dry top and wet/dry fronts are present. ``fully_wet`` instead leaves the
+    bed and raises the surface to max(z) + 1 m (+bump), which gives h >= 1 m
+    everywhere. Sizes scale the hump widths with the domain.
     """
     m = jittered_grid(nx, ny, lx, ly, jitter=jitter, diagonal="shorter", seed=seed)
     rng = np.random.default_rng(seed + 1000)
     c = centroids(m)
     scale = lx / 10_000.0
     z = _gaussian_humps(c, rng, 3, lx, ly, sigma=(300.0 * scale, 800.0 * scale))
+    if not fully_wet:
+        z += (eta0 + dry_top) - float(z.max())
     base = (float(z.max()) + 1.0) if fully_wet else eta0
     inside = (np.abs(c[:, 0] - lx / 2) <= bump_size * scale / 2) & (
         np.abs(c[:, 1] - ly / 2) <= bump_size * scale / 2)

@@ -1,0 +1,242 @@
+"""ctypes binding of libswe.so (the C ABI declared in include/swe.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. The library must have been built (``build.build()``); if it is
+missing, ``lib()`` raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libswe.so")
+
+SWE_OK = 0
+SWE_EINVAL = -1
+SWE_EMESH = -2
+SWE_ENOMEM = -3
+SWE_ECUDA = -4
+SWE_ENAN = -5
+SWE_ETIMEOUT = -7
+SWE_EDRY = -8
+SWE_ESTATE = -9
+
+PRECISION = {"f64": 0, "f32": 1}
+ORDER = {"none": 0, "morton": 1}
+KERNEL = {"auto": 0, "edge": 1, "tiled": 2}
+
+# Every symbol include/swe.h declares.
+EXPORTS = (
+    "swe_params_default", "swe_mesh_create", "swe_mesh_counts", "swe_mesh_device_bytes",
+    "swe_mesh_destroy", "swe_state_init", "swe_state_set", "swe_step", "swe_run",
+    "swe_advance", "swe_sync", "swe_copy_out", "swe_state_info", "swe_next_dt",
+    "swe_state_destroy", "swe_strerror", "swe_last_cuda_error",
+)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("g", ctypes.c_double),
+        ("courant", ctypes.c_double),
+        ("h_eps", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("order", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("tile", ctypes.c_int32),
+    ]
+
+
+class SweError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib().swe_strerror(status).decode()
+        extra = lib().swe_last_cuda_error().decode() if status == SWE_ECUDA else ""
+        super().__init__(f"{what}: {msg} ({status}){' - ' + extra if extra else ''}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Loads libswe.so once. Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1807_00672_gb300.build` (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, dbl, st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    P = ctypes.POINTER(Params)
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "swe_params_default": (None, [P]),
+        "swe_mesh_create": (st, [vp, i64, vp, i64, P, vp, pp]),
+        "swe_mesh_counts": (st, [vp, vp]),
+        "swe_mesh_device_bytes": (st, [vp, vp]),
+        "swe_mesh_destroy": (None, [vp]),
+        "swe_state_init": (st, [vp, vp, vp, vp, vp, vp, dbl, pp]),
+        "swe_state_set": (st, [vp, vp, vp, vp]),
+        "swe_step": (st, [vp, vp]),
+        "swe_run": (st, [vp, i64]),
+        "swe_advance": (st, [vp, dbl, vp]),
+        "swe_sync": (st, [vp]),
+        "swe_copy_out": (st, [vp, vp, vp, vp, vp, vp]),
+        "swe_state_info": (st, [vp, vp]),
+        "swe_next_dt": (st, [vp, vp]),
+        "swe_state_destroy": (None, [vp]),
+        "swe_strerror": (ctypes.c_char_p, [st]),
+        "swe_last_cuda_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(status: int, what: str):
+    if status != SWE_OK:
+        raise SweError(status, what)
+
+
+def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, courant=0.7,
+           h_eps=1e-6) -> Params:
+    p = Params()
+    lib().swe_params_default(ctypes.byref(p))
+    p.g, p.courant, p.h_eps = g, courant, h_eps
+    p.precision = PRECISION[precision]
+    p.order = ORDER[order]
+    p.kernel = KERNEL[kernel]
+    p.tile = tile
+    return p
+
+
+class Mesh:
+    """Device-resident mesh (swe_mesh_create)."""
+
+    def __init__(self, xy, tri, *, precision="f64", order="morton", kernel="auto", tile=0,
+                 stream=None, g=9.81, courant=0.7, h_eps=1e-6):
+        xy = _f64(xy).reshape(-1, 2)
+        tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        self.prm = params(precision, order, kernel, tile, g, courant, h_eps)
+        self.precision = precision
+        h = ctypes.c_void_p()
+        s = lib().swe_mesh_create(_p(xy), xy.shape[0], _p(tri), tri.shape[0],
+                                  ctypes.byref(self.prm), stream, ctypes.byref(h))
+        _check(s, "swe_mesh_create")
+        self._h = h
+        c = np.zeros(4, dtype=np.int64)
+        lib().swe_mesh_counts(self._h, _p(c))
+        self.V, self.T, self.E, self.Eb = (int(x) for x in c)
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        _check(lib().swe_mesh_device_bytes(self._h, ctypes.byref(b)), "swe_mesh_device_bytes")
+        return b.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().swe_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """Device-resident state on a Mesh (swe_state_init and friends)."""
+
+    def __init__(self, mesh: Mesh, h, hu, hv, z, n=None, manning_const: float = 0.0):
+        self.mesh = mesh
+        h, hu, hv, z = (_f64(a) for a in (h, hu, hv, z))
+        for a in (h, hu, hv, z):
+            if a.shape != (mesh.T,):
+                raise ValueError("cell arrays must have one value per triangle")
+        nn = None if n is None else _f64(n)
+        hdl = ctypes.c_void_p()
+        s = lib().swe_state_init(mesh._h, _p(h), _p(hu), _p(hv), _p(z),
+                                 None if nn is None else _p(nn), float(manning_const),
+                                 ctypes.byref(hdl))
+        _check(s, "swe_state_init")
+        self._h = hdl
+
+    def set(self, h, hu, hv):
+        h, hu, hv = (_f64(a) for a in (h, hu, hv))
+        _check(lib().swe_state_set(self._h, _p(h), _p(hu), _p(hv)), "swe_state_set")
+
+    def step(self) -> float:
+        dt = ctypes.c_double()
+        _check(lib().swe_step(self._h, ctypes.byref(dt)), "swe_step")
+        return dt.value
+
+    def run(self, n_steps: int, sync: bool = True):
+        _check(lib().swe_run(self._h, int(n_steps)), "swe_run")
+        if sync:
+            self.sync()
+
+    def advance(self, t_end: float) -> int:
+        k = ctypes.c_int64()
+        _check(lib().swe_advance(self._h, float(t_end), ctypes.byref(k)), "swe_advance")
+        return k.value
+
+    def sync(self):
+        _check(lib().swe_sync(self._h), "swe_sync")
+
+    def copy_out(self, h=None, hu=None, hv=None):
+        """Fills the given float64 arrays (any may be None); returns (t, mass)."""
+        t = ctypes.c_double()
+        m = ctypes.c_double()
+        args = [None if a is None else _p(a) for a in (h, hu, hv)]
+        _check(lib().swe_copy_out(self._h, *args, ctypes.byref(t), ctypes.byref(m)), "swe_copy_out")
+        return t.value, m.value
+
+    def fields(self):
+        T = self.mesh.T
+        h, hu, hv = np.empty(T), np.empty(T), np.empty(T)
+        self.copy_out(h, hu, hv)
+        return h, hu, hv
+
+    @property
+    def t(self) -> float:
+        return self.copy_out()[0]
+
+    @property
+    def mass(self) -> float:
+        return self.copy_out()[1]
+
+    def info(self):
+        a = np.zeros(3, dtype=np.int64)
+        _check(lib().swe_state_info(self._h, _p(a)), "swe_state_info")
+        return dict(steps=int(a[0]), neg=int(a[1]), err=int(a[2]))
+
+    def next_dt(self) -> float:
+        dt = ctypes.c_double()
+        _check(lib().swe_next_dt(self._h, ctypes.byref(dt)), "swe_next_dt")
+        return dt.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().swe_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

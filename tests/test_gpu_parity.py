@@ -1,0 +1,279 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bar: the FP64 path matches the oracle to 1e-11 relative after 100 steps:
+per field, the max error over cells divided by max |h_ref| for h and by the
+discharge scale max(max |q_ref|, h_max sqrt(g h_max)) for hu and hv. The FP32 path's
+L1/Linf errors against the FP64 oracle are stated and gated loosely.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_00672_gb300 import inputs, swe
+
+from closed_forms import stoker_depth
+from gpu_util import ensure_built, field_errors, gpu_state, l1_linf, oracle_run, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+KERNELS = [("tiled", "morton", 256), ("tiled", "morton", 128), ("tiled", "none", 256),
+           ("edge", "morton", 0), ("edge", "none", 0)]
+
+
+def small_cases():
+    # sizes span several tiles with a ragged tail (T not a multiple of 128/256)
+    return [
+        inputs.random_flow_case(nx=37, ny=23, seed=41),            # 1,702 cells, wet/dry
+        inputs.lake_at_rest_case(nx=45, ny=19, seed=43),           # 1,710 cells, dry islands
+        inputs.humps_case(nx=61, ny=33, lx=2_000.0, ly=1_000.0, seed=45),  # 4,026 cells
+        inputs.uniform_flow_case(nx=29, ny=17, seed=47),           # friction
+    ]
+
+
+@pytest.mark.parametrize("kernel,order,tile", KERNELS)
+def test_fp64_matches_oracle_100_steps(kernel, order, tile):
+    for case in small_cases():
+        ref, dts = oracle_run(case, 100)
+        mesh, st = gpu_state(case, "f64", kernel, order, tile)
+        st.run(100)
+        errs, _ = field_errors(st, ref)
+        assert max(errs.values()) <= TOL64, (case.name, errs)
+        t, mass = st.copy_out()
+        assert t == pytest.approx(dts.sum(), rel=1e-13)
+        assert mass == pytest.approx(ref.mass(), rel=1e-13)
+        info = st.info()
+        assert info["steps"] == 100 and info["neg"] == 0 and info["err"] == 0
+
+
+def test_fp64_first_dt_matches_oracle():
+    case = inputs.random_flow_case(nx=30, ny=20, seed=3)
+    ref = oracle.state_from_case(case)
+    mesh, st = gpu_state(case, "f64")
+    assert st.next_dt() == pytest.approx(ref.cfl_dt(), rel=1e-14)
+    dt = st.step()
+    assert dt == pytest.approx(ref.cfl_dt(), rel=1e-14)
+
+
+@pytest.mark.parametrize("kernel", ["tiled", "edge"])
+def test_stoker_to_end_time(kernel):
+    """Config: 2,500 triangles, dam break to T_s = 2 s (FP64), walls, n = 0."""
+    case = inputs.stoker_case()
+    ref = oracle.state_from_case(case)
+    k_ref = ref.advance(2.0)
+    mesh, st = gpu_state(case, "f64", kernel)
+    k = st.advance(2.0)
+    assert k == k_ref
+    t, _ = st.copy_out()
+    assert t == 2.0
+    errs, (h, hu, hv) = field_errors(st, ref)
+    assert max(errs.values()) <= TOL64, errs
+    # and the closed form along the centreline
+    cen = inputs.centroids(case.mesh)
+    band = np.abs(cen[:, 1] - 25.0) <= 2.0
+    he = stoker_depth(cen[band, 0], 2.0, 10.0, 1.0, 50.0)
+    assert np.abs(h[band] - he).sum() / he.sum() <= 0.03
+
+
+def test_advance_in_pieces_equals_one_advance():
+    case = inputs.random_flow_case(nx=20, ny=14, seed=5)
+    mesh, a = gpu_state(case, "f64")
+    a.advance(0.3)
+    a.advance(0.7)
+    _, b = gpu_state(case, "f64")
+    b.advance(0.7)
+    assert a.t == 0.7 and b.t == 0.7
+    ref = oracle.state_from_case(case)
+    ref.advance(0.3)
+    ref.advance(0.7)
+    errs, _ = field_errors(a, ref)
+    assert max(errs.values()) <= TOL64
+
+
+def test_graph_replay_equals_single_steps_bitwise():
+    case = inputs.random_flow_case(nx=33, ny=21, seed=9)
+    for prec in ("f64", "f32"):
+        _, a = gpu_state(case, prec)
+        a.run(40)   # two graphs of 16 + 8 single launches
+        _, b = gpu_state(case, prec)
+        for _ in range(40):
+            b.step()
+        for x, y in zip(a.fields(), b.fields()):
+            assert np.array_equal(x, y)
+
+
+def test_runs_are_deterministic_bitwise():
+    case = inputs.humps_case(nx=80, ny=40, lx=2_000.0, ly=1_000.0, seed=13)
+    for prec in ("f64", "f32"):
+        for kernel in ("tiled", "edge"):
+            outs = []
+            for _ in range(2):
+                _, s = gpu_state(case, prec, kernel)
+                s.run(50)
+                outs.append(s.fields() + s.copy_out())
+            for x, y in zip(outs[0], outs[1]):
+                assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_tiled_and_edge_kernels_agree_fp64():
+    case = inputs.humps_case(nx=90, ny=45, lx=3_000.0, ly=1_500.0, seed=17)
+    _, a = gpu_state(case, "f64", "tiled")
+    _, b = gpu_state(case, "f64", "edge")
+    a.run(60)
+    b.run(60)
+    for x, y in zip(a.fields(), b.fields()):
+        assert rel_err(x, y) <= 1e-13
+
+
+def test_fp32_error_against_fp64_oracle():
+    """FP32 state and fluxes with compensated face sums: stated L1/Linf error."""
+    case = inputs.humps_case(nx=120, ny=60, lx=4_000.0, ly=2_000.0, seed=19)
+    ref, _ = oracle_run(case, 100)
+    area = ref.mesh.cells()["area"]
+    for kernel in ("tiled", "edge"):
+        _, st = gpu_state(case, "f32", kernel)
+        st.run(100)
+        h, hu, hv = st.fields()
+        l1h, linfh = l1_linf(h, ref.h, area)
+        assert l1h <= 1e-4, (kernel, l1h, linfh)
+        for f, r in ((hu, ref.hu), (hv, ref.hv)):
+            l1, _ = l1_linf(f, r, area)
+            assert l1 <= 1e-3, (kernel, l1)
+        info = st.info()
+        assert info["neg"] == 0 and info["err"] == 0
+
+
+def test_lake_at_rest_on_gpu():
+    case = inputs.lake_at_rest_case(nx=50, ny=30, seed=21)
+    scale = 9.81 * case.h.max() ** 2
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-5)):
+        for kernel in ("tiled", "edge"):
+            _, st = gpu_state(case, prec, kernel)
+            st.run(100)
+            h, hu, hv = st.fields()
+            assert np.abs(hu).max() <= tol * scale and np.abs(hv).max() <= tol * scale, (prec, kernel)
+            assert np.abs(h - case.h).max() <= tol * case.h.max() * 10
+
+
+def test_mass_conservation_on_gpu():
+    case = inputs.random_flow_case(nx=40, ny=30, seed=23)
+    for prec, tol in (("f64", 1e-13), ("f32", 1e-6)):
+        for kernel in ("tiled", "edge"):
+            _, st = gpu_state(case, prec, kernel)
+            m0 = st.mass
+            st.run(100)
+            assert abs(st.mass - m0) <= tol * m0, (prec, kernel)
+            assert st.info()["neg"] == 0
+
+
+def test_single_triangle_all_walls():
+    xy = np.array([[0.0, 0.0], [2.0, 0.0], [0.5, 1.5]])
+    tri = np.array([[0, 1, 2]], dtype=np.int32)
+    case = inputs.Case(inputs.Mesh(xy, tri), np.array([1.0]), np.array([0.3]), np.array([-0.2]),
+                       np.array([0.0]), np.array([0.02]))
+    ref, _ = oracle_run(case, 10)
+    for kernel in ("tiled", "edge"):
+        _, st = gpu_state(case, "f64", kernel)
+        st.run(10)
+        errs, (h, _, _) = field_errors(st, ref)
+        assert max(errs.values()) <= TOL64
+        assert h[0] == pytest.approx(1.0, rel=1e-15)  # walls: no mass flux
+
+
+def test_fewer_cells_than_a_tile_and_ragged_tail():
+    for nx, ny in ((3, 2), (11, 6), (16, 8), (17, 8)):   # 12, 132, 256, 272 cells
+        case = inputs.random_flow_case(nx=nx, ny=ny, lx=10.0 * nx, ly=10.0 * ny, seed=nx)
+        ref, _ = oracle_run(case, 30)
+        for kernel, order, tile in KERNELS:
+            _, st = gpu_state(case, "f64", kernel, order, tile)
+            st.run(30)
+            errs, _ = field_errors(st, ref)
+            assert max(errs.values()) <= TOL64, (nx, ny, kernel, tile, errs)
+
+
+def test_all_dry_is_reported():
+    ensure_built()
+    case = inputs.random_flow_case(nx=8, ny=6)
+    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri)
+    with pytest.raises(swe.SweError) as ei:
+        swe.State(mesh, np.zeros(mesh.T), np.zeros(mesh.T), np.zeros(mesh.T), case.z, case.n)
+    assert ei.value.status == swe.SWE_EDRY
+
+
+def test_nan_input_is_reported():
+    ensure_built()
+    case = inputs.random_flow_case(nx=8, ny=6)
+    h = case.h.copy()
+    h[5] = np.nan
+    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri)
+    with pytest.raises(swe.SweError) as ei:
+        swe.State(mesh, h, case.hu, case.hv, case.z, case.n)
+    assert ei.value.status == swe.SWE_ENAN
+
+
+def test_state_set_restarts_from_new_fields():
+    case = inputs.random_flow_case(nx=20, ny=10, seed=29)
+    ref, _ = oracle_run(case, 20)
+    _, st = gpu_state(case, "f64")
+    st.run(7)
+    st.set(case.h, case.hu, case.hv)
+    assert st.t == 0.0
+    st.run(20)
+    errs, _ = field_errors(st, ref)
+    assert max(errs.values()) <= TOL64
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_constant_manning_equals_per_cell_array(prec):
+    case = inputs.uniform_flow_case(nx=20, ny=10)
+    ensure_built()
+    m = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=prec)
+    a = swe.State(m, case.h, case.hu, case.hv, case.z, case.n)
+    b = swe.State(m, case.h, case.hu, case.hv, case.z, None, manning_const=0.05)
+    a.run(20)
+    b.run(20)
+    for x, y in zip(a.fields(), b.fields()):
+        assert np.array_equal(x, y)
+
+
+# ------------------------------------------------------------------ full sizes
+
+@pytest.mark.slow
+def test_fp64_1m_humps_matches_oracle_after_100_steps():
+    """1,000,000 triangles, bed of three Gaussian humps, wet/dry fronts."""
+    case = inputs.humps_case()
+    ref, dts = oracle_run(case, 100)
+    mesh, st = gpu_state(case, "f64")
+    st.run(100)
+    errs, _ = field_errors(st, ref)
+    assert max(errs.values()) <= TOL64, errs
+
+
+@pytest.mark.slow
+def test_fp32_10m_sinusoid_sampled_cells():
+    """10,001,406 triangles in the benchmark's launch configuration: after 20
+    FP32 steps, one more step checked cell by cell on a seeded sample against
+    the oracle's FP64 update of the same (FP32-rounded) state with the same
+    dt; and properties at full size: mass, positivity, finiteness."""
+    case = inputs.sinusoid_case()
+    mesh, st = gpu_state(case, "f32")
+    m0 = st.mass
+    st.run(20)
+    h, hu, hv = st.fields()
+    dt = st.next_dt()
+    st.run(1)
+    h1, hu1, hv1 = st.fields()
+    # the FP32 step used dt rounded to float
+    dt32 = float(np.float32(dt))
+    o = oracle.State(oracle.Mesh(case.mesh.xy, case.mesh.tri), h, hu, hv, case.z, case.n)
+    rng = np.random.default_rng(77)
+    cells = rng.choice(mesh.T, size=20_000, replace=False)
+    want = o.cells_after_step(dt32, cells)
+    for got, w, full in ((h1, want[0], h), (hu1, want[1], hu), (hv1, want[2], hv)):
+        scale = max(np.abs(full).max(), 1e-30)
+        assert np.abs(got[cells] - w).max() <= 2e-6 * scale
+    assert np.all(h1 >= 0) and np.all(np.isfinite(h1))
+    assert abs(st.mass - m0) <= 1e-6 * m0
