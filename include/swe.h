@@ -154,6 +154,54 @@ swe_status swe_next_dt(const swe_state* state, double* dt);
 
 void swe_state_destroy(swe_state* state);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free step (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc: code running inside CUDA graph
+ * capture, programs that must not allocate after start-up, and hosts whose
+ * device memory comes from their own pool. swe_step_edges_static makes one
+ * FP64 step of the two-launch kernels (per-edge face outputs, then each cell
+ * gathers its three faces) with every input and output a caller-owned device
+ * pointer, and its scratch (per-edge face outputs, per-block partial sums,
+ * the control word) in one static device array of SWE_STATIC_SCRATCH_BYTES
+ * that each GPU loading the library keeps until the process exits.
+ *
+ * Meshes up to SWE_STATIC_MAX_EDGES edges; larger ones (or n_cells > n_edges,
+ * which no triangle mesh has) return SWE_EINVAL before any GPU work.
+ * The first call on a device looks up the array's device address and the
+ * launch sizes (with that device current); make that first call before any
+ * stream capture. Calls share the array: each resets what must start at zero,
+ * but calls whose work overlaps on the GPU race with each other.
+ * --------------------------------------------------------------------------- */
+#define SWE_STATIC_SCRATCH_BYTES (16 * 1024 * 1024)
+#define SWE_STATIC_MAX_EDGES 417792 /* (16 MiB - 64 KiB) / (5 values * 8 bytes) */
+
+/* Device inputs (caller cell order, FP64 unless noted):
+ *   edge_left, edge_right  [n_edges] int32 cells on each side of each edge;
+ *                          edge_right = -1 for a wall edge.
+ *   edge_nx, edge_ny       [n_edges] unit normal pointing out of edge_left.
+ *   edge_len               [n_edges] edge length.
+ *   cell_face              [3*n_cells] int32, cell i's face k at [k*n_cells + i]:
+ *                          the edge id, with bit 31 set when cell i is that
+ *                          edge's right side; face k joins the cell's
+ *                          counter-clockwise nodes k and k+1 (faces are summed
+ *                          in this order).
+ *   cell_area, cell_perim_over_area, gn2 (= g n^2), z, h, hu, hv  [n_cells].
+ * Device outputs: h_out, hu_out, hv_out [n_cells] (must not alias the inputs).
+ * Host outputs (either may be NULL): *next_dt = CFL dt of the new state,
+ * *mass = sum of area * h_out. If either is given the call synchronises the
+ * stream and also reports SWE_ENAN / SWE_EDRY; if both are NULL it returns
+ * after queueing the work. dt is the length of this step. */
+swe_status swe_step_edges_static(int64_t n_cells, int64_t n_edges, const int32_t* edge_left,
+                                 const int32_t* edge_right, const double* edge_nx,
+                                 const double* edge_ny, const double* edge_len,
+                                 const int32_t* cell_face, const double* cell_area,
+                                 const double* cell_perim_over_area, const double* gn2,
+                                 const double* z, const double* h, const double* hu,
+                                 const double* hv, double g, double courant, double h_eps,
+                                 double dt, double* h_out, double* hu_out, double* hv_out,
+                                 double* next_dt, double* mass, void* cuda_stream);
+
 /* Static description of a status code. */
 const char* swe_strerror(swe_status status);
 

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["swe_api.cu", "mesh_build.cpp"]
+SOURCES = ["swe_api.cu", "mesh_build.cpp", "swe_noalloc.cu"]
 HEADERS = ["swe_kernels.cuh", "mesh_build.h"]
 
 

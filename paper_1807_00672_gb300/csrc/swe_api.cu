@@ -16,6 +16,21 @@
 #include "mesh_build.h"
 #include "swe_kernels.cuh"
 
+namespace swe {
+
+// Sets the end time and re-clamps the next dt (one thread).
+__global__ void k_set_end(Ctl* ctl, double t_end) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctl->t_end = t_end;
+  if (ctl->err) { ctl->done = 1; return; }
+  const double rest = t_end - ctl->t;
+  ctl->done = (ctl->t >= t_end) ? 1 : 0;
+  if (ctl->dt_cfl >= rest) { ctl->dt = rest; ctl->clamped = 1; }
+  else { ctl->dt = ctl->dt_cfl; ctl->clamped = 0; }
+}
+
+}  // namespace swe
+
 namespace {
 
 constexpr int kStepsPerGraph = 16;

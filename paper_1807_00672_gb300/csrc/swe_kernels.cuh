@@ -538,17 +538,6 @@ __global__ void __launch_bounds__(256) k_cfl(DevMesh<Real> m, DevState<Real> s, 
   finish_launch<256>(ctl, s.partial, mass, rate, bad, 0, false, num.courant);
 }
 
-// Sets the end time and re-clamps the next dt (one thread).
-__global__ void k_set_end(Ctl* ctl, double t_end) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  ctl->t_end = t_end;
-  if (ctl->err) { ctl->done = 1; return; }
-  const double rest = t_end - ctl->t;
-  ctl->done = (ctl->t >= t_end) ? 1 : 0;
-  if (ctl->dt_cfl >= rest) { ctl->dt = rest; ctl->clamped = 1; }
-  else { ctl->dt = ctl->dt_cfl; ctl->clamped = 0; }
-}
-
 // Caller order (double) -> internal order (Real): dst[j] = src[perm[j]].
 template <typename Real>
 __global__ void k_gather(const double* __restrict__ src, const int32_t* __restrict__ perm,

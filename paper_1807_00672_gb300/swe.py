@@ -33,7 +33,7 @@ EXPORTS = (
     "swe_params_default", "swe_mesh_create", "swe_mesh_counts", "swe_mesh_device_bytes",
     "swe_mesh_destroy", "swe_state_init", "swe_state_set", "swe_step", "swe_run",
     "swe_advance", "swe_sync", "swe_copy_out", "swe_state_info", "swe_next_dt",
-    "swe_state_destroy", "swe_strerror", "swe_last_cuda_error",
+    "swe_state_destroy", "swe_strerror", "swe_last_cuda_error", "swe_step_edges_static",
 )
 
 
@@ -90,6 +90,8 @@ def lib():
         "swe_state_destroy": (None, [vp]),
         "swe_strerror": (ctypes.c_char_p, [st]),
         "swe_last_cuda_error": (ctypes.c_char_p, []),
+        "swe_step_edges_static": (st, [i64, i64] + [vp] * 13 + [dbl] * 4 + [vp] * 3
+                                  + [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
