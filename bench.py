@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
     ap.add_argument("--kernel", choices=["auto", "tiled", "edge"], default="auto")
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=0, help="solver steps per e2e call (0 = --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -214,7 +215,7 @@ def main():
     case = make_case(args.workload)
     stream = torch.cuda.Stream(device=dev)
     mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=args.precision, kernel=args.kernel,
-                    tile=args.tile, stream=ctypes_stream(stream))
+                    tile=args.tile, stages=args.stages, stream=ctypes_stream(stream))
     st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
     T = mesh.T
     kernels_per_step = 2 if args.kernel == "edge" else 1
@@ -272,7 +273,8 @@ def main():
         "config": {
             "workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
             "triangles": T, "edges": mesh.E, "precision": args.precision,
-            "kernel": args.kernel, "order": "morton", "seed": WORKLOADS[args.workload]["seed"],
+            "kernel": args.kernel, "tile": args.tile or 256, "stages": args.stages or 2,
+            "order": "morton", "seed": WORKLOADS[args.workload]["seed"],
             "l2": f"inputs larger than L2: {mesh.device_bytes() / 1e6:.0f} MB of mesh + "
                   f"{6 * word * T / 1e6:.0f} MB of state vs 129 MB L2",
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",

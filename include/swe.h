@@ -81,7 +81,10 @@ typedef struct {
   int32_t precision;  /* swe_precision (default SWE_F64) */
   int32_t order;      /* swe_order (default SWE_ORDER_MORTON) */
   int32_t kernel;     /* swe_kernel (default SWE_KERNEL_AUTO) */
-  int32_t tile;       /* cells per tile of SWE_KERNEL_TILED; 0 = library default */
+  int32_t tile;       /* cells (= threads) per tile of SWE_KERNEL_TILED: 32, 64, 128 or 256;
+                         0 = default */
+  int32_t stages;     /* shared-memory pipeline stages of SWE_KERNEL_TILED (2 or 3);
+                         0 = default */
 } swe_params;
 
 typedef struct swe_mesh swe_mesh;

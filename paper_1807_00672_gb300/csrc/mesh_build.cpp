@@ -215,67 +215,91 @@ int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t 
 
   // 7. Tiled layout.
   if (tile > 0) {
-    if (tile % 32 != 0 || 3 * (int64_t)tile > 32767) return -1;
+    if (tile % 32 != 0 || tile > 4096) return -1;
     m.tile = tile;
     m.ntiles = (T + tile - 1) / tile;
-    m.toff.assign(m.ntiles + 1, 0);
-    // Records per tile: every face of every tile cell, an interior face whose
-    // both cells lie in the tile counted once.
-    std::vector<int64_t> cnt(m.ntiles, 0);
-    for (int64_t e = 0; e < m.E; ++e) {
-      int64_t ta = m.iperm[cL[e]] / tile;
-      cnt[ta]++;
-      if (cR[e] >= 0) {
-        int64_t tb = m.iperm[cR[e]] / tile;
-        if (tb != ta) cnt[tb]++;
-      }
-    }
+    m.toff.assign(1, 0);
+    m.hoff.assign(1, 0);
+    m.tA.reserve((size_t)(1.75 * T) + 64);
+    // Per tile: every face of every tile cell, an interior face whose cells
+    // are both in the tile emitted once. Sides: a tile cell by its face slot
+    // (face k of tile cell j is slot k * tile + j, encoded -1 - slot), a cell
+    // of another tile by its index in the tile's halo list (>= 0), a wall as
+    // kWall. Records with both cells in the tile come first, then those with a
+    // halo side, then walls (fewer divergent warps); within a class, in cell
+    // order. Record and halo lists are padded to multiples of 4 entries
+    // (null records: both sides kWall, zero length; halo padding repeats the
+    // tile's first cell).
+    struct Rec { int32_t a, b; int32_t e; int cls; };
+    std::vector<Rec> recs;
+    std::vector<int32_t> halo;
+    std::vector<int32_t> halo_pos(T, -1);  // internal cell -> index in the current halo
     for (int64_t t = 0; t < m.ntiles; ++t) {
-      int64_t padded = (cnt[t] + 3) / 4 * 4;
-      m.null_records += padded - cnt[t];
-      m.toff[t + 1] = m.toff[t] + padded;
-    }
-    int64_t R = m.toff[m.ntiles];
-    m.tA.assign(R, kWall);
-    m.tB.assign(R, kWall);
-    m.tnx.assign(R, 0.0);
-    m.tny.assign(R, 0.0);
-    m.tlen.assign(R, 0.0);  // null records: zero length, both sides "wall"
-    std::vector<int64_t> pos(m.toff.begin(), m.toff.end() - 1);
-    // Walk the tile cells in internal order so records follow their cells.
-    for (int64_t j = 0; j < T; ++j) {
-      int64_t i = m.perm[j];
-      int64_t t = j / tile;
-      for (int k = 0; k < 3; ++k) {
-        int32_t e = edge_of_half[3 * i + k];
-        bool right = (cL[e] != i);
-        int32_t other = right ? cL[e] : cR[e];
-        int64_t jo = other >= 0 ? m.iperm[other] : -1;
-        bool other_local = (jo >= 0 && jo / tile == t);
-        // An interior face inside the tile is emitted once, by its left cell.
-        if (right && other_local) continue;
-        int32_t slot_self = -1 - (int32_t)((j - t * tile) * 3 + k);
-        int32_t enc_other;
-        if (jo < 0) {
-          enc_other = kWall;
-        } else if (other_local) {
-          // the other cell's face index for this edge
-          int ko = -1;
-          for (int kk = 0; kk < 3; ++kk)
-            if (edge_of_half[3 * (int64_t)other + kk] == e) ko = kk;
-          enc_other = -1 - (int32_t)((jo - t * tile) * 3 + ko);
-        } else {
-          enc_other = (int32_t)jo;
+      recs.clear();
+      halo.clear();
+      const int64_t j0 = t * tile, j1 = std::min<int64_t>(T, j0 + tile);
+      for (int64_t j = j0; j < j1; ++j) {
+        int64_t i = m.perm[j];
+        for (int k = 0; k < 3; ++k) {
+          int32_t e = edge_of_half[3 * i + k];
+          bool right = (cL[e] != i);
+          int32_t other = right ? cL[e] : cR[e];
+          int64_t jo = other >= 0 ? m.iperm[other] : -1;
+          bool other_local = (jo >= j0 && jo < j1);
+          if (right && other_local) continue;
+          int32_t slot_self = -1 - (int32_t)(k * tile + (j - j0));
+          int32_t enc_other;
+          int cls;
+          if (jo < 0) {
+            enc_other = kWall;
+            cls = 2;
+          } else if (other_local) {
+            int ko = -1;  // the other cell's face index for this edge
+            for (int kk = 0; kk < 3; ++kk)
+              if (edge_of_half[3 * (int64_t)other + kk] == e) ko = kk;
+            enc_other = -1 - (int32_t)(ko * tile + (jo - j0));
+            cls = 0;
+          } else {
+            if (halo_pos[jo] < 0) {
+              halo_pos[jo] = (int32_t)halo.size();
+              halo.push_back((int32_t)jo);
+            }
+            enc_other = halo_pos[jo];
+            cls = 1;
+          }
+          // side A is always the edge's left cell
+          if (!right) recs.push_back({slot_self, enc_other, e, cls});
+          else        recs.push_back({enc_other, slot_self, e, cls});
         }
-        int64_t r = pos[t]++;
-        // side A is always the edge's left cell
-        if (!right) { m.tA[r] = slot_self; m.tB[r] = enc_other; }
-        else        { m.tA[r] = enc_other; m.tB[r] = slot_self; }
-        m.tnx[r] = gnx[e];
-        m.tny[r] = gny[e];
-        m.tlen[r] = glen[e];
       }
+      for (int32_t c : halo) halo_pos[c] = -1;
+      std::stable_sort(recs.begin(), recs.end(),
+                       [](const Rec& p, const Rec& q) { return p.cls < q.cls; });
+      const size_t nrec = (recs.size() + 3) / 4 * 4;
+      for (const Rec& rc : recs) {
+        m.tA.push_back(rc.a);
+        m.tB.push_back(rc.b);
+        m.tnx.push_back(gnx[rc.e]);
+        m.tny.push_back(gny[rc.e]);
+        m.tlen.push_back(glen[rc.e]);
+      }
+      for (size_t r = recs.size(); r < nrec; ++r) {
+        m.tA.push_back(kWall);
+        m.tB.push_back(kWall);
+        m.tnx.push_back(0.0);
+        m.tny.push_back(0.0);
+        m.tlen.push_back(0.0);
+        m.null_records++;
+      }
+      m.toff.push_back((int64_t)m.tA.size());
+      const size_t nh = (halo.size() + 3) / 4 * 4;
+      for (int32_t c : halo) m.hidx.push_back(c);
+      for (size_t h = halo.size(); h < nh; ++h) m.hidx.push_back((int32_t)j0);
+      m.hoff.push_back((int64_t)m.hidx.size());
+      m.rec_cap = std::max<int64_t>(m.rec_cap, (int64_t)nrec);
+      m.halo_cap = std::max<int64_t>(m.halo_cap, (int64_t)nh);
     }
+    if (m.halo_cap == 0) m.halo_cap = 4;
   }
   return 0;
 }

@@ -8,9 +8,9 @@
 namespace swe {
 
 // Encoding of one side of a tile face record:
-//   >= 0             global (internal) index of a cell outside the tile
+//   >= 0             index of a cell of another tile in the tile's halo list
 //   kWall            wall (mirror ghost)
-//   < 0, != kWall    local face slot s = -1 - value (cell s / 3, face s % 3)
+//   < 0, != kWall    local face slot s = -1 - value: face s / tile of tile cell s % tile
 constexpr int32_t kWall = INT32_MIN;
 
 struct HostMesh {
@@ -25,15 +25,18 @@ struct HostMesh {
   std::vector<int32_t> eL, eR;   // eR = -1 for a wall
   std::vector<double> nx, ny, len;
   std::vector<int32_t> cface[3];
-  // Tiled layout: tiles of `tile` consecutive internal cells; for tile t the
-  // face records [toff[t], toff[t+1]) (each tile's start padded to a multiple
-  // of 4 records with null records), each with two encoded sides and the
-  // edge's geometry oriented from side A to side B.
+  // Tiled layout: tiles of `tile` consecutive internal cells. Tile t owns
+  // the face records [toff[t], toff[t+1]), each with two encoded sides and
+  // the edge's geometry oriented from side A (the edge's left cell) to side
+  // B, and the halo list hidx[hoff[t] .. hoff[t+1]) of the internal indices
+  // of the other tiles' cells its records touch. rec_cap and halo_cap are
+  // the largest padded record and halo counts of any tile.
   int32_t tile = 0;
   int64_t ntiles = 0;
-  std::vector<int64_t> toff;
-  std::vector<int32_t> tA, tB;
+  std::vector<int64_t> toff, hoff;
+  std::vector<int32_t> tA, tB, hidx;
   std::vector<double> tnx, tny, tlen;
+  int64_t rec_cap = 0, halo_cap = 0;
   int64_t null_records = 0;
 };
 

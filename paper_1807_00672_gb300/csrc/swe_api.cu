@@ -86,15 +86,18 @@ struct swe_mesh {
   int64_t V = 0, T = 0, E = 0, Eb = 0;
   int kernel = SWE_KERNEL_TILED;
   int tile = kDefaultTile;
-  int64_t ntiles = 0, records = 0;
+  int64_t ntiles = 0, records = 0, halos = 0;
+  int stages = 2;
+  swe::TileLayout layout{};
+  int64_t Tp = 0;  // cell arrays' length (padded to whole tiles for the tiled kernel)
   Arena arena;
   int32_t* perm = nullptr;
   void* area = nullptr;
   void* irP = nullptr;
   int32_t *eL = nullptr, *eR = nullptr, *cf[3] = {nullptr, nullptr, nullptr};
   void *nx = nullptr, *ny = nullptr, *len = nullptr;
-  int64_t* toff = nullptr;
-  int32_t *tA = nullptr, *tB = nullptr;
+  int64_t *toff = nullptr, *hoff = nullptr;
+  int32_t *tA = nullptr, *tB = nullptr, *hidx = nullptr;
   void *tnx = nullptr, *tny = nullptr, *tlen = nullptr;
   int grid_edge = 1, grid_cell = 1, grid_tiled = 1, grid_cfl = 1, max_grid = 1;
 };
@@ -116,7 +119,7 @@ struct swe_state {
 
 namespace {
 
-swe::Num num_of(const swe_mesh* m) { return swe::Num{m->prm.g, m->prm.courant, m->prm.h_eps}; }
+swe::Num num_of(const swe_mesh* m) { return swe::make_num(m->prm.g, m->prm.courant, m->prm.h_eps); }
 
 template <typename Real>
 swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
@@ -135,6 +138,8 @@ swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
   d.cf2 = m->cf[2];
   d.ntiles = m->ntiles;
   d.toff = m->toff;
+  d.hoff = m->hoff;
+  d.hidx = m->hidx;
   d.tA = m->tA;
   d.tB = m->tB;
   d.tnx = (const Real*)m->tnx;
@@ -166,15 +171,47 @@ int grid_for(int64_t n, int threads, int cap) {
   return (int)g;
 }
 
-template <typename Real>
-int blocks_per_sm_tiled(int tile) {
-  int n = 0;
+// Opts the tiled kernel into its dynamic shared memory and returns its
+// resident blocks per SM (0 if it cannot run with this layout).
+template <typename Real, int NT, int NS>
+int prepare_tiled(const swe::TileLayout& L) {
   constexpr bool comp = sizeof(Real) == 4;
-  if (tile == 128)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swe::k_tiled_step<Real, comp, 128>, 128, 0);
+  auto k = swe::k_tiled_step<Real, comp, NT, NS>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <typename Real, int NT>
+int blocks_per_sm_tiled_nt(const swe_mesh* m) {
+  return m->stages == 3 ? prepare_tiled<Real, NT, 3>(m->layout) : prepare_tiled<Real, NT, 2>(m->layout);
+}
+
+template <typename Real>
+int blocks_per_sm_tiled(const swe_mesh* m) {
+  switch (m->tile) {
+    case 32: return blocks_per_sm_tiled_nt<Real, 32>(m);
+    case 64: return blocks_per_sm_tiled_nt<Real, 64>(m);
+    case 128: return blocks_per_sm_tiled_nt<Real, 128>(m);
+    default: return blocks_per_sm_tiled_nt<Real, 256>(m);
+  }
+}
+
+template <typename Real, bool Comp, int NT>
+void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::DevState<Real>& ds,
+                     const swe::Num& num, cudaStream_t st) {
+  const swe::TileLayout& L = m->layout;
+  if (m->stages == 3)
+    swe::k_tiled_step<Real, Comp, NT, 3><<<m->grid_tiled, NT, L.total, st>>>(dm, ds, num, L);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swe::k_tiled_step<Real, comp, 256>, 256, 0);
-  return n > 0 ? n : 1;
+    swe::k_tiled_step<Real, Comp, NT, 2><<<m->grid_tiled, NT, L.total, st>>>(dm, ds, num, L);
 }
 
 template <typename Real>
@@ -191,9 +228,9 @@ void set_grids(swe_mesh* m) {
   m->grid_cell = grid_for(m->T, 256, m->sms * occ_cell);
   m->grid_cfl = grid_for(m->T, 256, m->sms * occ_cfl);
   if (m->kernel == SWE_KERNEL_TILED) {
-    int64_t g = (int64_t)m->sms * blocks_per_sm_tiled<Real>(m->tile);
+    int64_t g = (int64_t)m->sms * blocks_per_sm_tiled<Real>(m);
     m->grid_tiled = (int)(m->ntiles < g ? m->ntiles : g);
-    if (m->grid_tiled < 1) m->grid_tiled = 1;
+    if (m->grid_tiled < 1) m->grid_tiled = 0;  // the layout does not fit: reported by mesh_create
   }
   m->max_grid = std::max(std::max(m->grid_cell, m->grid_cfl), m->grid_tiled);
 }
@@ -208,10 +245,13 @@ void launch_step(const swe_state* s, cudaStream_t st) {
   if (m->kernel == SWE_KERNEL_EDGE) {
     swe::k_edge_flux<Real><<<m->grid_edge, 256, 0, st>>>(dm, ds, num);
     swe::k_cell_update<Real, comp><<<m->grid_cell, 256, 0, st>>>(dm, ds, num);
-  } else if (m->tile == 128) {
-    swe::k_tiled_step<Real, comp, 128><<<m->grid_tiled, 128, 0, st>>>(dm, ds, num);
   } else {
-    swe::k_tiled_step<Real, comp, 256><<<m->grid_tiled, 256, 0, st>>>(dm, ds, num);
+    switch (m->tile) {
+      case 32: launch_tiled_nt<Real, comp, 32>(m, dm, ds, num, st); break;
+      case 64: launch_tiled_nt<Real, comp, 64>(m, dm, ds, num, st); break;
+      case 128: launch_tiled_nt<Real, comp, 128>(m, dm, ds, num, st); break;
+      default: launch_tiled_nt<Real, comp, 256>(m, dm, ds, num, st); break;
+    }
   }
 }
 
@@ -260,6 +300,7 @@ swe_status upload(const swe_mesh* m, const std::vector<T>& v, void* dst) {
 }
 
 swe_status status_from_ctl(const swe::Ctl& c) {
+  if (c.err & swe::kErrTimeout) return SWE_ETIMEOUT;
   if (c.err & swe::kErrNan) return SWE_ENAN;
   if (c.err & swe::kErrDry) return SWE_EDRY;
   return SWE_OK;
@@ -348,6 +389,7 @@ void swe_params_default(swe_params* p) {
   p->order = SWE_ORDER_MORTON;
   p->kernel = SWE_KERNEL_AUTO;
   p->tile = 0;
+  p->stages = 0;
 }
 
 const char* swe_strerror(swe_status s) {
@@ -380,7 +422,9 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
   if (p.order != SWE_ORDER_NONE && p.order != SWE_ORDER_MORTON) return SWE_EINVAL;
   if (p.kernel < SWE_KERNEL_AUTO || p.kernel > SWE_KERNEL_TILED) return SWE_EINVAL;
   if (p.tile == 0) p.tile = kDefaultTile;
-  if (p.tile != 128 && p.tile != 256) return SWE_EINVAL;
+  if (p.tile != 32 && p.tile != 64 && p.tile != 128 && p.tile != 256) return SWE_EINVAL;
+  if (p.stages == 0) p.stages = 2;
+  if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
   if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
   const int kernel = (p.kernel == SWE_KERNEL_EDGE) ? SWE_KERNEL_EDGE : SWE_KERNEL_TILED;
 
@@ -405,8 +449,10 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
   m->V = hm.V; m->T = hm.T; m->E = hm.E; m->Eb = hm.Eb;
   m->kernel = kernel;
   m->tile = p.tile;
+  m->stages = p.stages;
   m->ntiles = hm.ntiles;
   m->records = (int64_t)hm.tA.size();
+  m->halos = (int64_t)hm.hidx.size();
   if (cuda_stream) {
     m->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -418,18 +464,23 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
   }
   const size_t w = real_size(m);
   const int64_t T = m->T, E = m->E, R = m->records;
+  m->Tp = (kernel == SWE_KERNEL_TILED) ? m->ntiles * m->tile : T;
+  const int64_t Tp = m->Tp;
   Layout L;
-  L.add(4 * T);  // perm
-  L.add(w * T);  // area
-  L.add(w * T);  // irP
+  L.add(4 * T);   // perm
+  L.add(w * Tp);  // area
+  L.add(w * Tp);  // irP
   if (kernel == SWE_KERNEL_EDGE) {
     L.add(4 * E); L.add(4 * E);
     L.add(w * E); L.add(w * E); L.add(w * E);
     L.add(4 * T); L.add(4 * T); L.add(4 * T);
   } else {
-    L.add(8 * (m->ntiles + 1));
+    L.add(8 * (m->ntiles + 1)); L.add(8 * (m->ntiles + 1));
     L.add(4 * R); L.add(4 * R);
     L.add(w * R); L.add(w * R); L.add(w * R);
+    L.add(4 * m->halos);
+    m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)m->tile, (uint32_t)m->stages,
+                                      (uint32_t)hm.rec_cap, (uint32_t)hm.halo_cap);
   }
   if (cudaMalloc((void**)&m->arena.base, L.total) != cudaSuccess) {
     cudaGetLastError();
@@ -437,9 +488,13 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
     return SWE_ENOMEM;
   }
   m->arena.size = L.total;
+  if (cuda_failed(cudaMemsetAsync(m->arena.base, 0, L.total, m->stream))) {
+    swe_mesh_destroy(m);
+    return SWE_ECUDA;
+  }
   m->perm = (int32_t*)m->arena.take(4 * T);
-  m->area = m->arena.take(w * T);
-  m->irP = m->arena.take(w * T);
+  m->area = m->arena.take(w * Tp);
+  m->irP = m->arena.take(w * Tp);
   std::vector<double> irp(T);
   for (int64_t j = 0; j < T; ++j) irp[j] = hm.perim[j] / hm.area[j];
   swe_status st = SWE_OK;
@@ -465,13 +520,17 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
     for (int k = 0; k < 3; ++k) chk(upload(m, hm.cface[k], m->cf[k]));
   } else {
     m->toff = (int64_t*)m->arena.take(8 * (m->ntiles + 1));
+    m->hoff = (int64_t*)m->arena.take(8 * (m->ntiles + 1));
     m->tA = (int32_t*)m->arena.take(4 * R);
     m->tB = (int32_t*)m->arena.take(4 * R);
     m->tnx = m->arena.take(w * R);
     m->tny = m->arena.take(w * R);
     m->tlen = m->arena.take(w * R);
+    m->hidx = (int32_t*)m->arena.take(4 * m->halos);
     if (!carved()) { swe_mesh_destroy(m); return st; }
     chk(upload(m, hm.toff, m->toff));
+    chk(upload(m, hm.hoff, m->hoff));
+    chk(upload(m, hm.hidx, m->hidx));
     chk(upload(m, hm.tA, m->tA));
     chk(upload(m, hm.tB, m->tB));
     chk(upload_real(m, hm.tnx, m->tnx));
@@ -485,6 +544,11 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
   }
   if (p.precision == SWE_F64) set_grids<double>(m);
   else set_grids<float>(m);
+  if (m->kernel == SWE_KERNEL_TILED && m->grid_tiled < 1) {
+    g_cuda_msg = "tiled kernel layout does not fit in shared memory";
+    swe_mesh_destroy(m);
+    return SWE_ECUDA;
+  }
   *out = m;
   return SWE_OK;
 }
@@ -516,12 +580,12 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
   if (!m || !h || !hu || !hv || !z) return SWE_EINVAL;
   if (!manning && !(manning_const >= 0.0)) return SWE_EINVAL;
   const size_t w = real_size(m);
-  const int64_t T = m->T, E = m->E;
+  const int64_t T = m->T, E = m->E, Tp = m->Tp;
   swe_state* s = new swe_state();
   s->mesh = m;
   Layout L;
-  for (int k = 0; k < 6; ++k) L.add(w * T);  // h, hu, hv x 2
-  L.add(w * T); L.add(w * T);                // z, gn2
+  for (int k = 0; k < 6; ++k) L.add(w * Tp);  // h, hu, hv x 2
+  L.add(w * Tp); L.add(w * Tp);                // z, gn2
   if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) L.add(w * E);
   L.add(8 * (size_t)m->max_grid);
   L.add(8 * T);                              // staging
@@ -532,13 +596,17 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
     return SWE_ENOMEM;
   }
   s->arena.size = L.total;
-  for (int b = 0; b < 2; ++b) {
-    s->h[b] = s->arena.take(w * T);
-    s->hu[b] = s->arena.take(w * T);
-    s->hv[b] = s->arena.take(w * T);
+  if (cuda_failed(cudaMemsetAsync(s->arena.base, 0, L.total, m->stream))) {
+    swe_state_destroy(s);
+    return SWE_ECUDA;
   }
-  s->z = s->arena.take(w * T);
-  s->gn2 = s->arena.take(w * T);
+  for (int b = 0; b < 2; ++b) {
+    s->h[b] = s->arena.take(w * Tp);
+    s->hu[b] = s->arena.take(w * Tp);
+    s->hv[b] = s->arena.take(w * Tp);
+  }
+  s->z = s->arena.take(w * Tp);
+  s->gn2 = s->arena.take(w * Tp);
   if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) s->fx[k] = s->arena.take(w * E);
   s->partial = (double*)s->arena.take(8 * (size_t)m->max_grid);
   s->stage = (double*)s->arena.take(8 * T);
@@ -639,6 +707,7 @@ swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, d
                         double* mass) {
   if (!s) return SWE_EINVAL;
   const swe_mesh* m = s->mesh;
+  if (mass) swe::k_mass_sum<<<1, 256, 0, m->stream>>>(s->ctl, s->partial);
   swe_status st = read_ctl(s);
   if (st != SWE_OK) return st;
   const int cur = s->host_ctl->cur;

@@ -8,10 +8,19 @@
 //
 // Determinism: every face contribution is written to its own slot and each
 // cell sums its three faces in a fixed order; the grid-wide CFL rate is an
-// integer max on non-negative IEEE bit patterns; the FP64 mass integral is a
+// integer max on non-negative IEEE bit patterns; the mass integral is a
 // per-block sum finished by the last block in block order. No float atomics.
+//
+// Precision. The FP64 path uses IEEE division and square root throughout.
+// The FP32 path uses the hardware's approximate reciprocal and reciprocal
+// square root and exp2/log2 for h^{-7/3}; its face sums and Euler update are
+// compensated (TwoSum with exact FMA products); its dry-depth tests decide
+// exactly as an FP64 comparison of the same value would (see Num::h_eps_f32);
+// its mass integral uses exact FP32 products with compensated per-thread sums
+// finished in FP64.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -26,6 +35,7 @@ struct Ctl {
   double dt_cfl;     // unclamped CFL dt of the current state
   double mass;       // sum of area * h of the current state (FP64)
   double dt_last;    // dt of the last step taken
+  long long nparts;  // mass partial sums written by the last launch (one per block)
   unsigned long long rate_bits;  // running max of the CFL rate (bits of a double >= 0)
   long long steps;   // steps taken
   long long neg;     // cells whose depth was clipped at zero
@@ -39,18 +49,30 @@ struct Ctl {
 
 constexpr int kErrNan = 1;
 constexpr int kErrDry = 2;
+constexpr int kErrTimeout = 4;
 
 struct Num {
   double g;
   double courant;
   double h_eps;
+  // Largest float <= h_eps: for a float h, (double)h > h_eps exactly when
+  // h > h_eps_f32 (no float lies in (h_eps_f32, h_eps]), so the FP32 path
+  // takes every dry-depth decision as an FP64 comparison would.
+  float h_eps_f32;
 };
+
+// Numerics of a run; h_eps_f32 derived from h_eps on the host.
+inline Num make_num(double g, double courant, double h_eps) {
+  float f = (float)h_eps;
+  if ((double)f > h_eps) f = std::nextafter(f, -INFINITY);
+  return Num{g, courant, h_eps, f};
+}
 
 template <typename Real>
 struct DevMesh {
   int64_t T;
   int64_t E;
-  // cells (internal order)
+  // cells (internal order; the tiled layout pads them to whole tiles)
   const Real* area;
   const Real* irP;  // perimeter / area
   // two-launch layout
@@ -65,6 +87,8 @@ struct DevMesh {
   // tiled layout
   int64_t ntiles;
   const int64_t* toff;
+  const int64_t* hoff;
+  const int32_t* hidx;
   const int32_t* tA;
   const int32_t* tB;
   const Real* tnx;
@@ -98,8 +122,6 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double cbrt_(double a) { return cbrt(a); }
-__device__ __forceinline__ float cbrt_(float a) { return cbrtf(a); }
 
 // Knuth's TwoSum: s + e == a + b exactly.
 template <typename Real>
@@ -111,6 +133,60 @@ __device__ __forceinline__ void two_sum(Real a, Real b, Real& s, Real& e) {
 }
 
 // ---------------------------------------------------------------------------
+// Precision-specific operations.
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct Ops;
+
+template <>
+struct Ops<double> {
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ bool wet(double h, const Num& n) { return h > n.h_eps; }
+  // dt g n^2 |q| / h^{7/3}
+  static __device__ __forceinline__ double friction(double dt, double gn2, double q, double h) {
+    return dt * gn2 * q / (h * h * cbrt(h));
+  }
+};
+
+template <>
+struct Ops<float> {
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+  static __device__ __forceinline__ bool wet(float h, const Num& n) { return h > n.h_eps_f32; }
+  static __device__ __forceinline__ float friction(float dt, float gn2, float q, float h) {
+    // h^{-7/3} = 2^{-(7/3) log2 h}; only called for h > h_eps > 0
+    return dt * gn2 * q * exp2f(-2.3333333333333335f * __log2f(h));
+  }
+};
+
+// Mass integral accumulator: plain FP64, or for FP32 exact products and a
+// compensated running sum, converted to FP64 at the end.
+template <typename Real>
+struct MassAcc;
+
+template <>
+struct MassAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double h) { s += a * h; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct MassAcc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float a, float h) {
+    const float p = __fmul_rn(a, h);
+    const float pe = __fmaf_rn(a, h, -p);
+    float s, e;
+    two_sum(hi, p, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// ---------------------------------------------------------------------------
 // HLLC flux in the face frame (Toro's shallow-water form). hA, hB are the
 // reconstructed depths, 0 meaning dry. Returns mass, normal and tangential
 // momentum fluxes.
@@ -118,13 +194,14 @@ __device__ __forceinline__ void two_sum(Real a, Real b, Real& s, Real& e) {
 template <typename Real>
 __device__ __forceinline__ void hllc(Real hA, Real unA, Real utA, Real hB, Real unB, Real utB,
                                      Real g, Real& F0, Real& F1, Real& F2) {
+  using O = Ops<Real>;
   const Real zero = Real(0), half = Real(0.5);
   if (hA == zero && hB == zero) {
     F0 = zero; F1 = zero; F2 = zero;
     return;
   }
-  const Real cA = sqrt(g * hA);
-  const Real cB = sqrt(g * hB);
+  const Real cA = O::sqrt_(g * hA);
+  const Real cB = O::sqrt_(g * hB);
   Real SA, SB;
   if (hA == zero) {
     SA = unB - Real(2) * cB;
@@ -150,7 +227,7 @@ __device__ __forceinline__ void hllc(Real hA, Real unA, Real utA, Real hB, Real 
   }
   const Real FA1 = qA * unA + half * g * hA * hA;
   const Real FB1 = qB * unB + half * g * hB * hB;
-  const Real inv = Real(1) / (SB - SA);
+  const Real inv = O::div(Real(1), SB - SA);
   F0 = (SB * qA - SA * qB + SA * SB * (hB - hA)) * inv;
   F1 = (SB * FA1 - SA * FB1 + SA * SB * (qB - qA)) * inv;
   // Contact speed S* = num / den with den < 0 whenever a side is wet, so
@@ -159,28 +236,36 @@ __device__ __forceinline__ void hllc(Real hA, Real unA, Real utA, Real hB, Real 
   F2 = F0 * (num <= zero ? utA : utB);
 }
 
-// One face: states of sides A (the edge's left cell) and B, unit normal n
-// from A to B, length len. Produces the contribution to A's residual
-// (c0, cA1, cA2) and the one subtracted from B's residual (c0, cB1, cB2):
-// l (F + P_side n) with the hydrostatic-reconstruction bed pressure P_side.
+// Velocity of a cell: (hu, hv) / h when wet, else 0.
 template <typename Real>
-__device__ __forceinline__ void face_flux(Real hA, Real huA, Real hvA, Real zA,
-                                          Real hB, Real huB, Real hvB, Real zB, bool wall,
+__device__ __forceinline__ void velocity(Real h, Real hu, Real hv, const Num& num, Real& u, Real& v) {
+  if (Ops<Real>::wet(h, num)) {
+    u = Ops<Real>::div(hu, h);
+    v = Ops<Real>::div(hv, h);
+  } else {
+    u = Real(0);
+    v = Real(0);
+  }
+}
+
+// One face: depth, velocity and bed of sides A (the edge's left cell) and B,
+// unit normal n from A to B, length len. Produces the contribution to A's
+// residual (c0, cA1, cA2) and the one subtracted from B's residual
+// (c0, cB1, cB2): l (F + P_side n) with the hydrostatic-reconstruction bed
+// pressure P_side.
+template <typename Real>
+__device__ __forceinline__ void face_flux(Real hA, Real uA, Real vA, Real zA,
+                                          Real hB, Real uB, Real vB, Real zB, bool wall,
                                           Real nx, Real ny, Real len, const Num& num,
                                           Real& c0, Real& cA1, Real& cA2, Real& cB1, Real& cB2) {
   const Real zero = Real(0), half = Real(0.5);
   const Real g = Real(num.g);
-  const double eps = num.h_eps;
-  Real uA = zero, vA = zero;
-  if ((double)hA > eps) { uA = huA / hA; vA = hvA / hA; }
   const Real unA = uA * nx + vA * ny;
   const Real utA = vA * nx - uA * ny;
   Real unB, utB;
   if (wall) {
     hB = hA; zB = zA; unB = -unA; utB = utA;
   } else {
-    Real uB = zero, vB = zero;
-    if ((double)hB > eps) { uB = huB / hB; vB = hvB / hB; }
     unB = uB * nx + vB * ny;
     utB = vB * nx - uB * ny;
   }
@@ -188,8 +273,8 @@ __device__ __forceinline__ void face_flux(Real hA, Real huA, Real hvA, Real zA,
   const Real zs = fmax(zA, zB);
   Real hAs = fmax(zero, hA + zA - zs);
   Real hBs = fmax(zero, hB + zB - zs);
-  if ((double)hAs <= eps) hAs = zero;
-  if ((double)hBs <= eps) hBs = zero;
+  if (!Ops<Real>::wet(hAs, num)) hAs = zero;
+  if (!Ops<Real>::wet(hBs, num)) hBs = zero;
   Real F0, F1, F2;
   hllc(hAs, unA, utA, hBs, unB, utB, g, F0, F1, F2);
   if (wall) { F0 = zero; F2 = zero; }
@@ -205,47 +290,52 @@ __device__ __forceinline__ void face_flux(Real hA, Real huA, Real hvA, Real zA,
 }
 
 // Per-cell end of the step: residual -> Euler update (Eq. 4) -> friction ->
-// next-step CFL rate. r*_hi/_lo: the residual as an unevaluated sum (lo = 0
+// next-step CFL rate. rhi/rlo: the residual as an unevaluated sum (lo = 0
 // for the plain path). Writes the new state and accumulates mass/rate.
 template <typename Real, bool Comp>
 __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area, Real irP, Real gn2,
                                             Real dt, const Real rhi[3], const Real rlo[3],
                                             const Num& num, Real& h1, Real& hu1, Real& hv1,
-                                            double& mass, double& rate, int& bad, int& neg) {
+                                            MassAcc<Real>& mass, Real& rate, int& bad, int& neg) {
+  using O = Ops<Real>;
   const Real zero = Real(0);
-  const Real a = dt / area;
+  const Real a = O::div(dt, area);
   Real U[3] = {h, hu, hv};
   Real out[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     if (Comp) {
-      // U - a (rhi + rlo) with the product error and the sum error carried.
-      const Real p = mul_rn(a, rhi[c]);
-      const Real pe = fma_rn(a, rhi[c], -p);
-      Real s, e;
-      two_sum(U[c], -p, s, e);
-      out[c] = add_rn(s, sub_rn(sub_rn(e, pe), mul_rn(a, rlo[c])));
+      // The compensated face sum rounded once, then U - a R in one FMA.
+      out[c] = fma_rn(-a, add_rn(rhi[c], rlo[c]), U[c]);
     } else {
       out[c] = U[c] - a * rhi[c];
     }
   }
   Real hs = out[0], qx = out[1], qy = out[2];
   if (hs < zero) { hs = zero; neg += 1; }
-  const double eps = num.h_eps;
-  if ((double)hs > eps) {
-    const Real q = sqrt(qx * qx + qy * qy);
-    const Real d = Real(1) + dt * gn2 * q / (hs * hs * cbrt_(hs));
-    qx = qx / d;
-    qy = qy / d;
-    const Real lam = sqrt(qx * qx + qy * qy) / hs + sqrt(Real(num.g) * hs);
-    rate = fmax(rate, (double)(lam * irP));
+  if (O::wet(hs, num)) {
+    const Real q = O::sqrt_(qx * qx + qy * qy);
+    const Real d = Real(1) + O::friction(dt, gn2, q, hs);
+    Real qn;  // |q| after friction
+    if constexpr (sizeof(Real) == 8) {
+      qx = qx / d;
+      qy = qy / d;
+      qn = sqrt(qx * qx + qy * qy);
+    } else {
+      const Real rd = O::div(Real(1), d);
+      qx = qx * rd;
+      qy = qy * rd;
+      qn = q * rd;
+    }
+    const Real lam = O::div(qn, hs) + O::sqrt_(Real(num.g) * hs);
+    rate = fmax(rate, lam * irP);
   } else {
     qx = zero;
     qy = zero;
   }
-  if (!isfinite(hs) || !isfinite(qx) || !isfinite(qy)) bad = 1;
+  if (!isfinite(hs + qx + qy)) bad = 1;
   h1 = hs; hu1 = qx; hv1 = qy;
-  mass += (double)area * (double)hs;
+  mass.add(area, hs);
 }
 
 // ---------------------------------------------------------------------------
@@ -264,9 +354,10 @@ __device__ __forceinline__ double warp_max(double v) {
 
 // Every thread of the block calls this once at the end of an update launch.
 // stepped: the launch advanced the state by ctl->dt (false: CFL/mass only).
+// err: kErr* bits seen by this thread.
 template <int NT>
-__device__ void finish_launch(Ctl* ctl, double* partial, double mass, double rate, int bad, int neg,
-                              bool stepped, double courant) {
+__device__ void finish_launch(Ctl* ctl, double* partial, double mass, double rate, int err_bits,
+                              int neg, bool stepped, double courant) {
   __shared__ double s_mass[NT / 32];
   __shared__ double s_rate[NT / 32];
   __shared__ int s_bad[NT / 32];
@@ -275,10 +366,12 @@ __device__ void finish_launch(Ctl* ctl, double* partial, double mass, double rat
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   mass = warp_sum(mass);
   rate = warp_max(rate);
-  const int wbad = __any_sync(0xffffffffu, bad);
-  int wneg = neg;
+  int wbad = err_bits, wneg = neg;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wneg += __shfl_xor_sync(0xffffffffu, wneg, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    wneg += __shfl_xor_sync(0xffffffffu, wneg, o);
+    wbad |= __shfl_xor_sync(0xffffffffu, wbad, o);
+  }
   if (lane == 0) { s_mass[wid] = mass; s_rate[wid] = rate; s_bad[wid] = wbad; s_neg[wid] = wneg; }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -286,7 +379,7 @@ __device__ void finish_launch(Ctl* ctl, double* partial, double mass, double rat
     int b = 0, n = 0;
     for (int w = 0; w < NT / 32; ++w) { m += s_mass[w]; r = fmax(r, s_rate[w]); b |= s_bad[w]; n += s_neg[w]; }
     atomicMax(&ctl->rate_bits, (unsigned long long)__double_as_longlong(r));
-    if (b) atomicOr(&ctl->err, kErrNan);
+    if (b) atomicOr(&ctl->err, b);
     if (n) atomicAdd((unsigned long long*)&ctl->neg, (unsigned long long)n);
     partial[blockIdx.x] = m;
     __threadfence();
@@ -296,16 +389,10 @@ __device__ void finish_launch(Ctl* ctl, double* partial, double mass, double rat
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // Last block: the mass integral over all blocks, in block order per thread.
-  double s = 0.0;
-  for (unsigned int j = threadIdx.x; j < gridDim.x; j += NT) s += __ldcg(&partial[j]);
-  s = warp_sum(s);
-  __syncthreads();
-  if (lane == 0) s_mass[wid] = s;
-  __syncthreads();
+  // Last block: the step's control update. The mass partial sums stay in
+  // `partial` and are added up by k_mass_sum when the host asks for them.
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int w = 0; w < NT / 32; ++w) m += s_mass[w];
+    ctl->nparts = gridDim.x;
     const unsigned long long bits = atomicExch(&ctl->rate_bits, 0ull);
     ctl->ticket = 0u;
     double t = ctl->t;
@@ -316,7 +403,6 @@ __device__ void finish_launch(Ctl* ctl, double* partial, double mass, double rat
       ctl->steps += 1;
       ctl->cur ^= 1;
     }
-    ctl->mass = m;
     int err = atomicOr(&ctl->err, 0);
     const double maxrate = __longlong_as_double((long long)bits);
     if (!(maxrate > 0.0)) err |= kErrDry;
@@ -352,11 +438,17 @@ __global__ void __launch_bounds__(256) k_edge_flux(DevMesh<Real> m, DevState<Rea
        e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t A = m.eL[e], B = m.eR[e];
     const bool wall = B < 0;
-    const Real hA = h[A], huA = hu[A], hvA = hv[A], zA = z[A];
-    Real hB = 0, huB = 0, hvB = 0, zB = 0;
-    if (!wall) { hB = h[B]; huB = hu[B]; hvB = hv[B]; zB = z[B]; }
+    const Real hA = h[A], zA = z[A];
+    Real uA, vA;
+    velocity(hA, hu[A], hv[A], num, uA, vA);
+    Real hB = 0, uB = 0, vB = 0, zB = 0;
+    if (!wall) {
+      hB = h[B];
+      zB = z[B];
+      velocity(hB, hu[B], hv[B], num, uB, vB);
+    }
     Real c0, cA1, cA2, cB1, cB2;
-    face_flux<Real>(hA, huA, hvA, zA, hB, huB, hvB, zB, wall, m.nx[e], m.ny[e], m.len[e], num,
+    face_flux<Real>(hA, uA, vA, zA, hB, uB, vB, zB, wall, m.nx[e], m.ny[e], m.len[e], num,
                     c0, cA1, cA2, cB1, cB2);
     s.fx[0][e] = c0;
     s.fx[1][e] = cA1;
@@ -379,7 +471,8 @@ __global__ void __launch_bounds__(256) k_cell_update(DevMesh<Real> m, DevState<R
   Real* __restrict__ h1 = cur ? s.h[0] : s.h[1];
   Real* __restrict__ hu1 = cur ? s.hu[0] : s.hu[1];
   Real* __restrict__ hv1 = cur ? s.hv[0] : s.hv[1];
-  double mass = 0.0, rate = 0.0;
+  MassAcc<Real> mass;
+  Real rate = Real(0);
   int bad = 0, neg = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m.T;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -412,22 +505,147 @@ __global__ void __launch_bounds__(256) k_cell_update(DevMesh<Real> m, DevState<R
     hu1[i] = b1;
     hv1[i] = c1;
   }
-  finish_launch<256>(ctl, s.partial, mass, rate, bad, neg, true, num.courant);
+  finish_launch<256>(ctl, s.partial, mass.value(), (double)rate, bad ? kErrNan : 0, neg, true,
+                     num.courant);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies, cp.async gathers and mbarriers (inline PTX).
+// ---------------------------------------------------------------------------
+// A waiting thread sleeps in try_wait for up to kSuspendNs per round instead
+// of spinning; after kWaitLimit rounds (about a second) the wait gives up.
+constexpr uint32_t kSuspendNs = 20000;
+constexpr uint32_t kWaitLimit = 50000;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 1D bulk copy global -> shared; src, dst 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false if it never came.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// One value global -> shared, asynchronously (completed by cp_async_wait_all).
+__device__ __forceinline__ void cp_async(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Shared-memory plan of k_tiled_step, sized on the host from the mesh's
+// largest per-tile record and halo counts. Each of the NS stages holds one
+// tile: the extended state arrays (the tile's NT cells followed by its halo
+// cells) h, hu, hv, z; the tile's gn2, area, irP; its face records (tA, tB,
+// nx, ny, len); its halo index list. After the stages: the face slots
+// (3 components x 3 faces x NT), the extended velocities u, v and the NS
+// mbarriers. Every offset is a multiple of 16 bytes.
+struct TileLayout {
+  uint32_t ext, rec_cap, halo_cap;
+  uint32_t off_h, off_hu, off_hv, off_z, off_gn2, off_area, off_irP;
+  uint32_t off_tA, off_tB, off_nx, off_ny, off_len, off_hidx;
+  uint32_t stage;
+  uint32_t off_slots, off_u, off_v, off_bars, total;
+};
+
+inline TileLayout make_tile_layout(uint32_t w, uint32_t nt, uint32_t ns, uint32_t rec_cap,
+                                   uint32_t halo_cap) {
+  auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+  TileLayout L{};
+  L.rec_cap = rec_cap;
+  L.halo_cap = halo_cap;
+  L.ext = nt + halo_cap;
+  uint32_t o = 0;
+  L.off_h = o; o += a16(L.ext * w);
+  L.off_hu = o; o += a16(L.ext * w);
+  L.off_hv = o; o += a16(L.ext * w);
+  L.off_z = o; o += a16(L.ext * w);
+  L.off_gn2 = o; o += a16(nt * w);
+  L.off_area = o; o += a16(nt * w);
+  L.off_irP = o; o += a16(nt * w);
+  L.off_tA = o; o += a16(rec_cap * 4);
+  L.off_tB = o; o += a16(rec_cap * 4);
+  L.off_nx = o; o += a16(rec_cap * w);
+  L.off_ny = o; o += a16(rec_cap * w);
+  L.off_len = o; o += a16(rec_cap * w);
+  L.off_hidx = o; o += a16(halo_cap * 4);
+  L.stage = o;
+  o = ns * L.stage;
+  L.off_slots = o; o += a16(9 * nt * w);
+  L.off_u = o; o += a16(L.ext * w);
+  L.off_v = o; o += a16(L.ext * w);
+  L.off_bars = o; o += a16(ns * 8);
+  L.total = o;
+  return L;
 }
 
 // ---------------------------------------------------------------------------
 // Tiled one-launch step. A persistent block walks tiles of NT consecutive
-// cells: (1) stage the tile's states in shared memory, (2) compute every face
-// record of the tile once (interior faces of the tile serve both of their
-// cells; faces to other tiles are recomputed there), writing each
-// contribution into its cell's face slot, (3) sum each cell's three slots in
-// face order and update. Remote neighbour states come from global memory
-// (L2 hits under the locality ordering).
+// cells (tile = blockIdx.x + k gridDim.x) through NS shared-memory stages:
+//   - thread 0 queues bulk async copies (TMA) of tile k+NS-1's cell arrays,
+//     face records and halo list while the block works on tile k;
+//   - once tile k+1's copies have landed (mid-iteration k), every thread
+//     gathers its halo cells' states from global memory with cp.async;
+//   (1) velocities of the tile's cells and halo cells;
+//   (2) every face record of the tile once: interior faces of the tile fill
+//       both of their cells' slots, faces shared with another tile fill only
+//       this tile's slot (that tile computes the same face from the same
+//       inputs), walls mirror; slots are face-major (face k of tile cell j at
+//       k NT + j);
+//   (3) each cell sums its three face slots in face order and is updated.
+// Cell arrays are padded to whole tiles so every copy moves NT values.
 // ---------------------------------------------------------------------------
-template <typename Real, bool Comp, int NT>
-__global__ void __launch_bounds__(NT) k_tiled_step(DevMesh<Real> m, DevState<Real> s, Num num) {
-  __shared__ Real sh_h[NT], sh_hu[NT], sh_hv[NT], sh_z[NT];
-  __shared__ Real sh_c[3][3 * NT];
+// Resident blocks per SM the tiled kernel is compiled for (register budget):
+// 1024 threads per SM for FP32, 512 for FP64.
+template <typename Real, int NT>
+constexpr int tiled_min_blocks() { return (sizeof(Real) == 4 ? 1024 : 512) / NT; }
+
+template <typename Real, bool Comp, int NT, int NS>
+__global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
+    k_tiled_step(DevMesh<Real> m, DevState<Real> s, Num num, TileLayout L) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  Real* slots = reinterpret_cast<Real*>(smem + L.off_slots);
+  Real* eu = reinterpret_cast<Real*>(smem + L.off_u);
+  Real* ev = reinterpret_cast<Real*>(smem + L.off_v);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bars);
+
   Ctl* ctl = s.ctl;
   if (ctl->done) return;
   const int cur = ctl->cur;
@@ -439,59 +657,161 @@ __global__ void __launch_bounds__(NT) k_tiled_step(DevMesh<Real> m, DevState<Rea
   Real* __restrict__ h1 = cur ? s.h[0] : s.h[1];
   Real* __restrict__ hu1 = cur ? s.hu[0] : s.hu[1];
   Real* __restrict__ hv1 = cur ? s.hv[0] : s.hv[1];
-  double mass = 0.0, rate = 0.0;
-  int bad = 0, neg = 0;
   const int tid = threadIdx.x;
-  for (int64_t tile = blockIdx.x; tile < m.ntiles; tile += gridDim.x) {
-    const int64_t base = tile * NT;
-    const int nc = (int)min((int64_t)NT, m.T - base);
-    Real myh = 0, myhu = 0, myhv = 0;
-    if (tid < nc) {
-      myh = h[base + tid]; myhu = hu[base + tid]; myhv = hv[base + tid];
-      sh_h[tid] = myh; sh_hu[tid] = myhu; sh_hv[tid] = myhv; sh_z[tid] = z[base + tid];
+  const int ntiles = (int)m.ntiles;
+  const int G = (int)gridDim.x;
+
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // Thread 0 tracks, per stage, the parity of the next phase to wait for and
+  // whether a copy is in flight (bit st of each mask).
+  uint32_t parity_bits = 0, pending = 0;
+  // Thread 0: queue the bulk copies of tile t into stage st.
+  auto issue = [&](int st, int t) {
+    unsigned char* p = smem + st * L.stage;
+    const int64_t base = (int64_t)t * NT;
+    const int64_t r0 = m.toff[t], h0 = m.hoff[t];
+    const uint32_t nrec = (uint32_t)(m.toff[t + 1] - r0);
+    const uint32_t nh = (uint32_t)(m.hoff[t + 1] - h0);
+    const uint32_t cell = NT * (uint32_t)sizeof(Real);
+    const uint32_t rb = nrec * (uint32_t)sizeof(Real);
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], 7 * cell + nrec * 8 + 3 * rb + nh * 4);
+    bulk_g2s(p + L.off_h, h + base, cell, &bar[st]);
+    bulk_g2s(p + L.off_hu, hu + base, cell, &bar[st]);
+    bulk_g2s(p + L.off_hv, hv + base, cell, &bar[st]);
+    bulk_g2s(p + L.off_z, z + base, cell, &bar[st]);
+    bulk_g2s(p + L.off_gn2, s.gn2 + base, cell, &bar[st]);
+    bulk_g2s(p + L.off_area, m.area + base, cell, &bar[st]);
+    bulk_g2s(p + L.off_irP, m.irP + base, cell, &bar[st]);
+    bulk_g2s(p + L.off_tA, m.tA + r0, nrec * 4, &bar[st]);
+    bulk_g2s(p + L.off_tB, m.tB + r0, nrec * 4, &bar[st]);
+    bulk_g2s(p + L.off_nx, m.tnx + r0, rb, &bar[st]);
+    bulk_g2s(p + L.off_ny, m.tny + r0, rb, &bar[st]);
+    bulk_g2s(p + L.off_len, m.tlen + r0, rb, &bar[st]);
+    if (nh > 0) bulk_g2s(p + L.off_hidx, m.hidx + h0, nh * 4, &bar[st]);
+    pending |= 1u << st;
+  };
+  // Thread 0: wait for stage st's copies.
+  auto wait_stage = [&](int st) -> bool {
+    const bool ok = mbar_wait(&bar[st], (parity_bits >> st) & 1u);
+    if (ok) {
+      parity_bits ^= 1u << st;
+      pending &= ~(1u << st);
     }
+    return ok;
+  };
+  // All threads: gather tile t's halo states into stage st (after its copies landed).
+  auto gather_halo = [&](int st, int t) {
+    unsigned char* p = smem + st * L.stage;
+    const int32_t* hl = reinterpret_cast<const int32_t*>(p + L.off_hidx);
+    const int nh = (int)(m.hoff[t + 1] - m.hoff[t]);
+    Real* xh = reinterpret_cast<Real*>(p + L.off_h) + NT;
+    Real* xhu = reinterpret_cast<Real*>(p + L.off_hu) + NT;
+    Real* xhv = reinterpret_cast<Real*>(p + L.off_hv) + NT;
+    Real* xz = reinterpret_cast<Real*>(p + L.off_z) + NT;
+    for (int q = tid; q < nh; q += NT) {
+      const int c = hl[q];
+      cp_async(xh + q, h + c);
+      cp_async(xhu + q, hu + c);
+      cp_async(xhv + q, hv + c);
+      cp_async(xz + q, z + c);
+    }
+  };
+
+  MassAcc<Real> mass;
+  Real rate = Real(0);
+  int bad = 0, neg = 0, timeout = 0;
+  int tile = blockIdx.x;
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NS - 1; ++i)
+      if (tile + i * G < ntiles) issue(i, tile + i * G);
+  }
+  if (tile < ntiles) {
+    const bool ok = (tid == 0) ? wait_stage(0) : true;
+    if (__syncthreads_or(!ok)) {
+      timeout = 1;
+    } else {
+      gather_halo(0, tile);
+      cp_async_wait_all();
+      __syncthreads();
+    }
+  }
+  for (int k = 0; !timeout && tile < ntiles; tile += G, ++k) {
+    const int st = k % NS;
+    const int t_next = tile + G;
+    // The stage that receives tile k+NS-1 was released by the barrier that
+    // ended iteration k-1.
+    if (tid == 0 && tile + (NS - 1) * G < ntiles) issue((k + NS - 1) % NS, tile + (NS - 1) * G);
+    const unsigned char* p = smem + st * L.stage;
+    const Real* xh = reinterpret_cast<const Real*>(p + L.off_h);
+    const Real* xhu = reinterpret_cast<const Real*>(p + L.off_hu);
+    const Real* xhv = reinterpret_cast<const Real*>(p + L.off_hv);
+    const Real* xz = reinterpret_cast<const Real*>(p + L.off_z);
+    const Real* c_gn2 = reinterpret_cast<const Real*>(p + L.off_gn2);
+    const Real* c_area = reinterpret_cast<const Real*>(p + L.off_area);
+    const Real* c_irP = reinterpret_cast<const Real*>(p + L.off_irP);
+    const int32_t* rA = reinterpret_cast<const int32_t*>(p + L.off_tA);
+    const int32_t* rB = reinterpret_cast<const int32_t*>(p + L.off_tB);
+    const Real* rnx = reinterpret_cast<const Real*>(p + L.off_nx);
+    const Real* rny = reinterpret_cast<const Real*>(p + L.off_ny);
+    const Real* rlen = reinterpret_cast<const Real*>(p + L.off_len);
+    const int base = tile * NT;
+    const int nc = min(NT, (int)m.T - base);
+    const int nrec = (int)(m.toff[tile + 1] - m.toff[tile]);
+    const int nh = (int)(m.hoff[tile + 1] - m.hoff[tile]);
+
+    // (1) velocities of the tile's cells and of its halo cells
+    if (tid < nc) velocity(xh[tid], xhu[tid], xhv[tid], num, eu[tid], ev[tid]);
+    for (int q = tid; q < nh; q += NT)
+      velocity(xh[NT + q], xhu[NT + q], xhv[NT + q], num, eu[NT + q], ev[NT + q]);
     __syncthreads();
-    const int64_t r0 = m.toff[tile], r1 = m.toff[tile + 1];
-    for (int64_t r = r0 + tid; r < r1; r += NT) {
-      const int32_t a = m.tA[r];
+
+    // (2) face records
+    for (int r = tid; r < nrec; r += NT) {
+      const int32_t a = rA[r];
       if (a == kWallSide) continue;  // padding record
-      const int32_t b = m.tB[r];
-      Real hA, huA, hvA, zA, hB = 0, huB = 0, hvB = 0, zB = 0;
-      if (a < 0) {
-        const int j = (-1 - a) / 3;
-        hA = sh_h[j]; huA = sh_hu[j]; hvA = sh_hv[j]; zA = sh_z[j];
-      } else {
-        hA = h[a]; huA = hu[a]; hvA = hv[a]; zA = z[a];
-      }
+      const int32_t b = rB[r];
       const bool wall = (b == kWallSide);
-      if (!wall) {
-        if (b < 0) {
-          const int j = (-1 - b) / 3;
-          hB = sh_h[j]; huB = sh_hu[j]; hvB = sh_hv[j]; zB = sh_z[j];
-        } else {
-          hB = h[b]; huB = hu[b]; hvB = hv[b]; zB = z[b];
-        }
-      }
+      const int ia = a < 0 ? ((-1 - a) & (NT - 1)) : NT + a;
+      const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (NT - 1)) : NT + b);
       Real c0, cA1, cA2, cB1, cB2;
-      face_flux<Real>(hA, huA, hvA, zA, hB, huB, hvB, zB, wall, m.tnx[r], m.tny[r], m.tlen[r], num,
-                      c0, cA1, cA2, cB1, cB2);
+      face_flux<Real>(xh[ia], eu[ia], ev[ia], xz[ia], xh[ib], eu[ib], ev[ib], xz[ib], wall, rnx[r],
+                      rny[r], rlen[r], num, c0, cA1, cA2, cB1, cB2);
       if (a < 0) {
         const int sl = -1 - a;
-        sh_c[0][sl] = c0; sh_c[1][sl] = cA1; sh_c[2][sl] = cA2;
+        slots[sl] = c0; slots[3 * NT + sl] = cA1; slots[6 * NT + sl] = cA2;
       }
       if (b < 0 && !wall) {
         const int sl = -1 - b;
-        sh_c[0][sl] = -c0; sh_c[1][sl] = -cB1; sh_c[2][sl] = -cB2;
+        slots[sl] = -c0; slots[3 * NT + sl] = -cB1; slots[6 * NT + sl] = -cB2;
       }
     }
-    __syncthreads();
+    // The next tile's copies must have landed before its halo is gathered.
+    const bool ok = (tid == 0 && t_next < ntiles) ? wait_stage((k + 1) % NS) : true;
+    if (__syncthreads_or(!ok)) {
+      timeout = 1;
+      break;
+    }
+
+    // (3) cells; meanwhile the next tile's halo gathers are in flight
+    if (t_next < ntiles) gather_halo((k + 1) % NS, t_next);
     if (tid < nc) {
-      Real rhi[3] = {Real(0), Real(0), Real(0)}, rlo[3] = {Real(0), Real(0), Real(0)};
+      Real rhi[3], rlo[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int q = 0; q < 3; ++q) {
+        const Real* cq = slots + q * 3 * NT + tid;  // faces kf at cq[kf * NT]
+        rhi[q] = cq[0];
+        rlo[q] = Real(0);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const Real c = sh_c[q][3 * tid + k];
+        for (int kf = 1; kf < 3; ++kf) {
+          const Real c = cq[kf * NT];
           if (Comp) {
             Real sum, err;
             two_sum(rhi[q], c, sum, err);
@@ -502,40 +822,68 @@ __global__ void __launch_bounds__(NT) k_tiled_step(DevMesh<Real> m, DevState<Rea
           }
         }
       }
-      const int64_t i = base + tid;
+      const int i = base + tid;
       Real a1, b1, c1;
-      cell_finish<Real, Comp>(myh, myhu, myhv, m.area[i], m.irP[i], s.gn2[i], dt, rhi, rlo, num,
-                              a1, b1, c1, mass, rate, bad, neg);
+      cell_finish<Real, Comp>(xh[tid], xhu[tid], xhv[tid], c_area[tid], c_irP[tid], c_gn2[tid], dt,
+                              rhi, rlo, num, a1, b1, c1, mass, rate, bad, neg);
       h1[i] = a1;
       hu1[i] = b1;
       hv1[i] = c1;
     }
+    cp_async_wait_all();
     __syncthreads();
   }
-  finish_launch<NT>(ctl, s.partial, mass, rate, bad, neg, true, num.courant);
+  // After a timed-out wait, let every copy still in flight land before the
+  // block's shared memory is released (bounded as well).
+  if (timeout && tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+      if ((pending >> i) & 1u) mbar_wait(&bar[i], (parity_bits >> i) & 1u);
+  }
+  finish_launch<NT>(ctl, s.partial, mass.value(), (double)rate,
+                    (bad ? kErrNan : 0) | (timeout ? kErrTimeout : 0), neg, true, num.courant);
 }
 
 // CFL rate and mass of the current state, no step (initialisation).
 template <typename Real>
 __global__ void __launch_bounds__(256) k_cfl(DevMesh<Real> m, DevState<Real> s, Num num) {
+  using O = Ops<Real>;
   Ctl* ctl = s.ctl;
   const int cur = ctl->cur;
   const Real* __restrict__ h = cur ? s.h[1] : s.h[0];
   const Real* __restrict__ hu = cur ? s.hu[1] : s.hu[0];
   const Real* __restrict__ hv = cur ? s.hv[1] : s.hv[0];
-  double mass = 0.0, rate = 0.0;
+  MassAcc<Real> mass;
+  Real rate = Real(0);
   int bad = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m.T;
        i += (int64_t)gridDim.x * blockDim.x) {
     const Real hh = h[i], qx = hu[i], qy = hv[i];
-    if ((double)hh > num.h_eps) {
-      const Real lam = sqrt(qx * qx + qy * qy) / hh + sqrt(Real(num.g) * hh);
-      rate = fmax(rate, (double)(lam * m.irP[i]));
+    if (O::wet(hh, num)) {
+      const Real lam = O::div(O::sqrt_(qx * qx + qy * qy), hh) + O::sqrt_(Real(num.g) * hh);
+      rate = fmax(rate, lam * m.irP[i]);
     }
-    if (!isfinite(hh) || !isfinite(qx) || !isfinite(qy)) bad = 1;
-    mass += (double)m.area[i] * (double)hh;
+    if (!isfinite(hh + qx + qy)) bad = 1;
+    mass.add(m.area[i], hh);
   }
-  finish_launch<256>(ctl, s.partial, mass, rate, bad, 0, false, num.courant);
+  finish_launch<256>(ctl, s.partial, mass.value(), (double)rate, bad ? kErrNan : 0, 0, false,
+                     num.courant);
+}
+
+// Mass integral of the latest launch: the sum of its per-block partial sums,
+// in a fixed order (one block of 256 threads).
+static __global__ void __launch_bounds__(256) k_mass_sum(Ctl* ctl, const double* __restrict__ partial) {
+  __shared__ double sh[256];
+  const long long n = ctl->nparts;
+  double acc = 0.0;
+  for (long long j = threadIdx.x; j < n; j += 256) acc += partial[j];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ctl->mass = sh[0];
 }
 
 // Caller order (double) -> internal order (Real): dst[j] = src[perm[j]].

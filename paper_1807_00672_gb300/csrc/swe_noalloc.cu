@@ -132,13 +132,14 @@ extern "C" swe_status swe_step_edges_static(
   for (int k = 0; k < 5; ++k) s.fx[k] = faces + (size_t)k * n_edges;
   s.partial = partial;
   s.ctl = ctl;
-  const swe::Num num{g, courant, h_eps};
+  const swe::Num num = swe::make_num(g, courant, h_eps);
 
   const int ge = (int)std::min<int64_t>((n_edges + 255) / 256, g_grid_edge[dev]);
   const int gc = (int)std::min<int64_t>((n_cells + 255) / 256, g_grid_cell[dev]);
   k_static_begin<<<1, 1, 0, stream>>>(ctl, dt);
   swe::k_edge_flux<double><<<ge, 256, 0, stream>>>(m, s, num);
   swe::k_cell_update<double, false><<<gc, 256, 0, stream>>>(m, s, num);
+  if (mass) swe::k_mass_sum<<<1, 256, 0, stream>>>(ctl, partial);
   if (cudaGetLastError() != cudaSuccess) return SWE_ECUDA;
   if (next_dt || mass) {
     swe::Ctl c;
