@@ -184,11 +184,14 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "tiled", "edge"], default="auto")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--cpt", type=int, default=0, help="cells per thread of the tiled kernel")
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=0, help="solver steps per e2e call (0 = --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the fp64 and error legs")
     ap.add_argument("--ref-cells", type=int, default=25_000)
+    ap.add_argument("--cpu-cells", type=int, default=1_000_000)
+    ap.add_argument("--cpu-steps", type=int, default=150)
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -215,7 +218,8 @@ def main():
     case = make_case(args.workload)
     stream = torch.cuda.Stream(device=dev)
     mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=args.precision, kernel=args.kernel,
-                    tile=args.tile, stages=args.stages, stream=ctypes_stream(stream))
+                    tile=args.tile, stages=args.stages, cells_per_thread=args.cpt,
+                    stream=ctypes_stream(stream))
     st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
     T = mesh.T
     kernels_per_step = 2 if args.kernel == "edge" else 1
@@ -273,7 +277,8 @@ def main():
         "config": {
             "workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
             "triangles": T, "edges": mesh.E, "precision": args.precision,
-            "kernel": args.kernel, "tile": args.tile or 256, "stages": args.stages or 2,
+            "kernel": args.kernel, "tile": args.tile or 256, "stages": args.stages or 3,
+            "cells_per_thread": args.cpt or 2,
             "order": "morton", "seed": WORKLOADS[args.workload]["seed"],
             "l2": f"inputs larger than L2: {mesh.device_bytes() / 1e6:.0f} MB of mesh + "
                   f"{6 * word * T / 1e6:.0f} MB of state vs 129 MB L2",
@@ -319,9 +324,10 @@ def main():
     st.close()
     mesh.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        small = small_case(args.workload, args.ref_cells)
-        k = 40
-        rate, secs = oracle_rate(small, k, 2)
+        # about 10-20 s of single-thread oracle work on the same recipe
+        small = small_case(args.workload, args.cpu_cells)
+        k = args.cpu_steps
+        rate, secs = oracle_rate(small, k, 1)
         out["cpu_baseline"] = {
             "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"FP64 oracle, 1 thread, {k} steps of the same recipe at "

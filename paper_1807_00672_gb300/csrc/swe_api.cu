@@ -88,6 +88,7 @@ struct swe_mesh {
   int tile = kDefaultTile;
   int64_t ntiles = 0, records = 0, halos = 0;
   int stages = 2;
+  int cpt = 1;  // cells per thread of the tiled kernel (threads = tile / cpt)
   swe::TileLayout layout{};
   int64_t Tp = 0;  // cell arrays' length (padded to whole tiles for the tiled kernel)
   Arena arena;
@@ -97,8 +98,8 @@ struct swe_mesh {
   int32_t *eL = nullptr, *eR = nullptr, *cf[3] = {nullptr, nullptr, nullptr};
   void *nx = nullptr, *ny = nullptr, *len = nullptr;
   int64_t *toff = nullptr, *hoff = nullptr;
-  int32_t *tA = nullptr, *tB = nullptr, *hidx = nullptr;
-  void *tnx = nullptr, *tny = nullptr, *tlen = nullptr;
+  int32_t *tS = nullptr, *hidx = nullptr;
+  void *tg0 = nullptr, *tg1 = nullptr, *tg2 = nullptr;
   int grid_edge = 1, grid_cell = 1, grid_tiled = 1, grid_cfl = 1, max_grid = 1;
 };
 
@@ -140,11 +141,10 @@ swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
   d.toff = m->toff;
   d.hoff = m->hoff;
   d.hidx = m->hidx;
-  d.tA = m->tA;
-  d.tB = m->tB;
-  d.tnx = (const Real*)m->tnx;
-  d.tny = (const Real*)m->tny;
-  d.tlen = (const Real*)m->tlen;
+  d.tS = m->tS;
+  d.tg0 = (const Real*)m->tg0;
+  d.tg1 = (const Real*)m->tg1;
+  d.tg2 = (const Real*)m->tg2;
   return d;
 }
 
@@ -173,10 +173,10 @@ int grid_for(int64_t n, int threads, int cap) {
 
 // Opts the tiled kernel into its dynamic shared memory and returns its
 // resident blocks per SM (0 if it cannot run with this layout).
-template <typename Real, int NT, int NS>
+template <typename Real, int NT, int NS, int CPT>
 int prepare_tiled(const swe::TileLayout& L) {
   constexpr bool comp = sizeof(Real) == 4;
-  auto k = swe::k_tiled_step<Real, comp, NT, NS>;
+  auto k = swe::k_tiled_step<Real, comp, NT, NS, CPT>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -189,29 +189,44 @@ int prepare_tiled(const swe::TileLayout& L) {
   return n;
 }
 
-template <typename Real, int NT>
+template <typename Real, int NT, int CPT>
 int blocks_per_sm_tiled_nt(const swe_mesh* m) {
-  return m->stages == 3 ? prepare_tiled<Real, NT, 3>(m->layout) : prepare_tiled<Real, NT, 2>(m->layout);
+  return m->stages == 3 ? prepare_tiled<Real, NT, 3, CPT>(m->layout)
+                        : prepare_tiled<Real, NT, 2, CPT>(m->layout);
+}
+
+template <typename Real, int CPT>
+int blocks_per_sm_tiled_cpt(const swe_mesh* m) {
+  switch (m->tile / CPT) {
+    case 64: return blocks_per_sm_tiled_nt<Real, 64, CPT>(m);
+    case 128: return blocks_per_sm_tiled_nt<Real, 128, CPT>(m);
+    default: return blocks_per_sm_tiled_nt<Real, 256, CPT>(m);
+  }
 }
 
 template <typename Real>
 int blocks_per_sm_tiled(const swe_mesh* m) {
-  switch (m->tile) {
-    case 32: return blocks_per_sm_tiled_nt<Real, 32>(m);
-    case 64: return blocks_per_sm_tiled_nt<Real, 64>(m);
-    case 128: return blocks_per_sm_tiled_nt<Real, 128>(m);
-    default: return blocks_per_sm_tiled_nt<Real, 256>(m);
-  }
+  return m->cpt == 2 ? blocks_per_sm_tiled_cpt<Real, 2>(m) : blocks_per_sm_tiled_cpt<Real, 1>(m);
 }
 
-template <typename Real, bool Comp, int NT>
+template <typename Real, bool Comp, int NT, int CPT>
 void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::DevState<Real>& ds,
                      const swe::Num& num, cudaStream_t st) {
   const swe::TileLayout& L = m->layout;
   if (m->stages == 3)
-    swe::k_tiled_step<Real, Comp, NT, 3><<<m->grid_tiled, NT, L.total, st>>>(dm, ds, num, L);
+    swe::k_tiled_step<Real, Comp, NT, 3, CPT><<<m->grid_tiled, NT, L.total, st>>>(dm, ds, num, L);
   else
-    swe::k_tiled_step<Real, Comp, NT, 2><<<m->grid_tiled, NT, L.total, st>>>(dm, ds, num, L);
+    swe::k_tiled_step<Real, Comp, NT, 2, CPT><<<m->grid_tiled, NT, L.total, st>>>(dm, ds, num, L);
+}
+
+template <typename Real, bool Comp, int CPT>
+void launch_tiled_cpt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::DevState<Real>& ds,
+                      const swe::Num& num, cudaStream_t st) {
+  switch (m->tile / CPT) {
+    case 64: launch_tiled_nt<Real, Comp, 64, CPT>(m, dm, ds, num, st); break;
+    case 128: launch_tiled_nt<Real, Comp, 128, CPT>(m, dm, ds, num, st); break;
+    default: launch_tiled_nt<Real, Comp, 256, CPT>(m, dm, ds, num, st); break;
+  }
 }
 
 template <typename Real>
@@ -245,13 +260,10 @@ void launch_step(const swe_state* s, cudaStream_t st) {
   if (m->kernel == SWE_KERNEL_EDGE) {
     swe::k_edge_flux<Real><<<m->grid_edge, 256, 0, st>>>(dm, ds, num);
     swe::k_cell_update<Real, comp><<<m->grid_cell, 256, 0, st>>>(dm, ds, num);
+  } else if (m->cpt == 2) {
+    launch_tiled_cpt<Real, comp, 2>(m, dm, ds, num, st);
   } else {
-    switch (m->tile) {
-      case 32: launch_tiled_nt<Real, comp, 32>(m, dm, ds, num, st); break;
-      case 64: launch_tiled_nt<Real, comp, 64>(m, dm, ds, num, st); break;
-      case 128: launch_tiled_nt<Real, comp, 128>(m, dm, ds, num, st); break;
-      default: launch_tiled_nt<Real, comp, 256>(m, dm, ds, num, st); break;
-    }
+    launch_tiled_cpt<Real, comp, 1>(m, dm, ds, num, st);
   }
 }
 
@@ -390,6 +402,7 @@ void swe_params_default(swe_params* p) {
   p->kernel = SWE_KERNEL_AUTO;
   p->tile = 0;
   p->stages = 0;
+  p->cells_per_thread = 0;
 }
 
 const char* swe_strerror(swe_status s) {
@@ -422,8 +435,13 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
   if (p.order != SWE_ORDER_NONE && p.order != SWE_ORDER_MORTON) return SWE_EINVAL;
   if (p.kernel < SWE_KERNEL_AUTO || p.kernel > SWE_KERNEL_TILED) return SWE_EINVAL;
   if (p.tile == 0) p.tile = kDefaultTile;
-  if (p.tile != 32 && p.tile != 64 && p.tile != 128 && p.tile != 256) return SWE_EINVAL;
-  if (p.stages == 0) p.stages = 2;
+  if (p.cells_per_thread == 0) p.cells_per_thread = 2;
+  if (p.cells_per_thread != 1 && p.cells_per_thread != 2) return SWE_EINVAL;
+  {
+    const int nt = p.tile / p.cells_per_thread;
+    if (p.tile % p.cells_per_thread != 0 || (nt != 64 && nt != 128 && nt != 256)) return SWE_EINVAL;
+  }
+  if (p.stages == 0) p.stages = 3;
   if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
   if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
   const int kernel = (p.kernel == SWE_KERNEL_EDGE) ? SWE_KERNEL_EDGE : SWE_KERNEL_TILED;
@@ -450,8 +468,10 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
   m->kernel = kernel;
   m->tile = p.tile;
   m->stages = p.stages;
+  m->cpt = p.cells_per_thread;
   m->ntiles = hm.ntiles;
   m->records = (int64_t)hm.tA.size();
+  const int geo_arrays = (p.precision == SWE_F64) ? 3 : 2;
   m->halos = (int64_t)hm.hidx.size();
   if (cuda_stream) {
     m->stream = (cudaStream_t)cuda_stream;
@@ -476,11 +496,12 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
     L.add(4 * T); L.add(4 * T); L.add(4 * T);
   } else {
     L.add(8 * (m->ntiles + 1)); L.add(8 * (m->ntiles + 1));
-    L.add(4 * R); L.add(4 * R);
-    L.add(w * R); L.add(w * R); L.add(w * R);
+    L.add(4 * R);
+    for (int g = 0; g < geo_arrays; ++g) L.add(w * R);
     L.add(4 * m->halos);
-    m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)m->tile, (uint32_t)m->stages,
-                                      (uint32_t)hm.rec_cap, (uint32_t)hm.halo_cap);
+    m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)geo_arrays, (uint32_t)m->tile,
+                                      (uint32_t)m->stages, (uint32_t)hm.rec_cap,
+                                      (uint32_t)hm.halo_cap);
   }
   if (cudaMalloc((void**)&m->arena.base, L.total) != cudaSuccess) {
     cudaGetLastError();
@@ -521,21 +542,40 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
   } else {
     m->toff = (int64_t*)m->arena.take(8 * (m->ntiles + 1));
     m->hoff = (int64_t*)m->arena.take(8 * (m->ntiles + 1));
-    m->tA = (int32_t*)m->arena.take(4 * R);
-    m->tB = (int32_t*)m->arena.take(4 * R);
-    m->tnx = m->arena.take(w * R);
-    m->tny = m->arena.take(w * R);
-    m->tlen = m->arena.take(w * R);
+    m->tS = (int32_t*)m->arena.take(4 * R);
+    m->tg0 = m->arena.take(w * R);
+    m->tg1 = m->arena.take(w * R);
+    if (geo_arrays > 2) m->tg2 = m->arena.take(w * R);
     m->hidx = (int32_t*)m->arena.take(4 * m->halos);
     if (!carved()) { swe_mesh_destroy(m); return st; }
     chk(upload(m, hm.toff, m->toff));
     chk(upload(m, hm.hoff, m->hoff));
     chk(upload(m, hm.hidx, m->hidx));
-    chk(upload(m, hm.tA, m->tA));
-    chk(upload(m, hm.tB, m->tB));
-    chk(upload_real(m, hm.tnx, m->tnx));
-    chk(upload_real(m, hm.tny, m->tny));
-    chk(upload_real(m, hm.tlen, m->tlen));
+    // Sides as int16 codes packed in one word (A high, B low).
+    std::vector<int32_t> packed(R);
+    auto code = [](int32_t v) { return v == swe::kWall ? (int32_t)swe::kSideWall : v; };
+    bool fits = true;
+    for (int64_t r = 0; r < R; ++r) {
+      const int32_t a = code(hm.tA[r]), b = code(hm.tB[r]);
+      fits = fits && a >= -32768 && a <= 32767 && b >= -32768 && b <= 32767;
+      packed[r] = (int32_t)(((uint32_t)(uint16_t)a << 16) | (uint32_t)(uint16_t)b);
+    }
+    if (!fits) chk(SWE_EINVAL);
+    chk(upload(m, packed, m->tS));
+    if (geo_arrays > 2) {
+      chk(upload_real(m, hm.tnx, m->tg0));
+      chk(upload_real(m, hm.tny, m->tg1));
+      chk(upload_real(m, hm.tlen, m->tg2));
+    } else {  // scaled normal l n
+      std::vector<double> gx(R), gy(R);
+      for (int64_t r = 0; r < R; ++r) {
+        gx[r] = hm.tlen[r] * hm.tnx[r];
+        gy[r] = hm.tlen[r] * hm.tny[r];
+      }
+      chk(upload_real(m, gx, m->tg0));
+      chk(upload_real(m, gy, m->tg1));
+    }
+    chk(cuda_failed(cudaStreamSynchronize(m->stream)) ? SWE_ECUDA : SWE_OK);  // host vectors end here
   }
   if (st == SWE_OK && cuda_failed(cudaStreamSynchronize(m->stream))) st = SWE_ECUDA;
   if (st != SWE_OK) {

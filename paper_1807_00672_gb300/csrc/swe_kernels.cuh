@@ -89,11 +89,13 @@ struct DevMesh {
   const int64_t* toff;
   const int64_t* hoff;
   const int32_t* hidx;
-  const int32_t* tA;
-  const int32_t* tB;
-  const Real* tnx;
-  const Real* tny;
-  const Real* tlen;
+  // face records: both sides packed as int16 codes (side A in the high half,
+  // side B in the low half; see kSideWall), then the geometry arrays of
+  // Geo<Real>
+  const int32_t* tS;
+  const Real* tg0;
+  const Real* tg1;
+  const Real* tg2;
 };
 
 template <typename Real>
@@ -109,7 +111,10 @@ struct DevState {
   Ctl* ctl;
 };
 
-constexpr int32_t kWallSide = INT32_MIN;
+// Side codes of packed face records (int16): -1 - slot for a cell of the
+// tile, the halo index (>= 0) for a cell of another tile, kSideWall for a
+// wall (and for side A of a padding record).
+constexpr int kSideWall = -32768;
 
 // ---------------------------------------------------------------------------
 // Exact arithmetic helpers (never contracted into FMAs).
@@ -149,14 +154,79 @@ struct Ops<double> {
   }
 };
 
+// FP32: single-instruction hardware approximations (reciprocal and square
+// root about 1 ulp, exp2/log2 about 2 ulp), flushing subnormals to zero.
+// Every divisor here is an area, a wet depth (> h_eps), a friction factor
+// (>= 1) or a wave-speed span (>= one wave celerity); every square-root
+// argument is a depth or a squared speed, where a subnormal value and zero
+// give the same update.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 template <>
 struct Ops<float> {
-  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-  static __device__ __forceinline__ float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+  static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrt_approx(x); }
   static __device__ __forceinline__ bool wet(float h, const Num& n) { return h > n.h_eps_f32; }
   static __device__ __forceinline__ float friction(float dt, float gn2, float q, float h) {
     // h^{-7/3} = 2^{-(7/3) log2 h}; only called for h > h_eps > 0
-    return dt * gn2 * q * exp2f(-2.3333333333333335f * __log2f(h));
+    return dt * gn2 * q * ex2_approx(-2.3333333333333335f * lg2_approx(h));
+  }
+};
+
+// Face geometry of the tiled records. FP64: unit normal and length as
+// computed on the host. FP32: the scaled normal (l nx, l ny) only, from which
+// the unit normal and the length are recovered with one reciprocal square
+// root (both tiles of a shared face recover the same bits).
+template <typename Real>
+struct Geo;
+
+template <>
+struct Geo<double> {
+  static constexpr int kArrays = 3;
+  static __device__ __forceinline__ void get(const double* g0, const double* g1, const double* g2,
+                                             int r, double& nx, double& ny, double& len) {
+    nx = g0[r];
+    ny = g1[r];
+    len = g2[r];
+  }
+};
+
+template <>
+struct Geo<float> {
+  static constexpr int kArrays = 2;
+  static __device__ __forceinline__ void get(const float* g0, const float* g1, const float*, int r,
+                                             float& nx, float& ny, float& len) {
+    const float gx = g0[r], gy = g1[r];
+    const float l2 = gx * gx + gy * gy;
+    const float rl = rsqrt_approx(l2);
+    nx = gx * rl;
+    ny = gy * rl;
+    len = l2 * rl;
   }
 };
 
@@ -194,57 +264,47 @@ struct MassAcc<float> {
 template <typename Real>
 __device__ __forceinline__ void hllc(Real hA, Real unA, Real utA, Real hB, Real unB, Real utB,
                                      Real g, Real& F0, Real& F1, Real& F2) {
+  // Straight-line form: every case is computed and the right one selected
+  // (the same values the case analysis picks; no divergent branches).
   using O = Ops<Real>;
   const Real zero = Real(0), half = Real(0.5);
-  if (hA == zero && hB == zero) {
-    F0 = zero; F1 = zero; F2 = zero;
-    return;
-  }
+  const bool wetA = hA > zero, wetB = hB > zero;
   const Real cA = O::sqrt_(g * hA);
   const Real cB = O::sqrt_(g * hB);
-  Real SA, SB;
-  if (hA == zero) {
-    SA = unB - Real(2) * cB;
-    SB = unB + cB;
-  } else if (hB == zero) {
-    SA = unA - cA;
-    SB = unA + Real(2) * cA;
-  } else {
-    const Real us = (unA + unB) * half + cA - cB;
-    const Real cs = (cA + cB) * half + (unA - unB) * Real(0.25);
-    SA = fmin(unA - cA, us - cs);
-    SB = fmax(unB + cB, us + cs);
-  }
+  // wave speeds: two-rarefaction estimates when both sides are wet, Toro's
+  // dry-bed speeds when one side is dry
+  const Real us = (unA + unB) * half + cA - cB;
+  const Real cs = (cA + cB) * half + (unA - unB) * Real(0.25);
+  const Real SA = wetA ? (wetB ? fmin(unA - cA, us - cs) : unA - cA) : unB - Real(2) * cB;
+  const Real SB = wetA ? (wetB ? fmax(unB + cB, us + cs) : unA + Real(2) * cA) : unB + cB;
   const Real qA = hA * unA;
   const Real qB = hB * unB;
-  if (SA >= zero) {
-    F0 = qA; F1 = qA * unA + half * g * hA * hA; F2 = qA * utA;
-    return;
-  }
-  if (SB <= zero) {
-    F0 = qB; F1 = qB * unB + half * g * hB * hB; F2 = qB * utB;
-    return;
-  }
   const Real FA1 = qA * unA + half * g * hA * hA;
   const Real FB1 = qB * unB + half * g * hB * hB;
   const Real inv = O::div(Real(1), SB - SA);
-  F0 = (SB * qA - SA * qB + SA * SB * (hB - hA)) * inv;
-  F1 = (SB * FA1 - SA * FB1 + SA * SB * (qB - qA)) * inv;
+  const Real H0 = (SB * qA - SA * qB + SA * SB * (hB - hA)) * inv;
+  const Real H1 = (SB * FA1 - SA * FB1 + SA * SB * (qB - qA)) * inv;
   // Contact speed S* = num / den with den < 0 whenever a side is wet, so
   // S* >= 0 exactly when num <= 0: no division needed for the upwind choice.
   const Real num = SA * hB * (unB - SB) - SB * hA * (unA - SA);
-  F2 = F0 * (num <= zero ? utA : utB);
+  const Real H2 = H0 * (num <= zero ? utA : utB);
+  const bool left = SA >= zero, right = SB <= zero, dry = !wetA && !wetB;
+  F0 = dry ? zero : left ? qA : right ? qB : H0;
+  F1 = dry ? zero : left ? FA1 : right ? FB1 : H1;
+  F2 = dry ? zero : left ? qA * utA : right ? qB * utB : H2;
 }
 
 // Velocity of a cell: (hu, hv) / h when wet, else 0.
 template <typename Real>
 __device__ __forceinline__ void velocity(Real h, Real hu, Real hv, const Num& num, Real& u, Real& v) {
-  if (Ops<Real>::wet(h, num)) {
-    u = Ops<Real>::div(hu, h);
-    v = Ops<Real>::div(hv, h);
+  const bool w = Ops<Real>::wet(h, num);
+  if constexpr (sizeof(Real) == 8) {
+    u = w ? hu / h : 0.0;
+    v = w ? hv / h : 0.0;
   } else {
-    u = Real(0);
-    v = Real(0);
+    const float r = rcp_approx(h);
+    u = w ? hu * r : 0.0f;
+    v = w ? hv * r : 0.0f;
   }
 }
 
@@ -572,43 +632,39 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Shared-memory plan of k_tiled_step, sized on the host from the mesh's
 // largest per-tile record and halo counts. Each of the NS stages holds one
-// tile: the extended state arrays (the tile's NT cells followed by its halo
-// cells) h, hu, hv, z; the tile's gn2, area, irP; its face records (tA, tB,
-// nx, ny, len); its halo index list. After the stages: the face slots
-// (3 components x 3 faces x NT), the extended velocities u, v and the NS
-// mbarriers. Every offset is a multiple of 16 bytes.
+// tile: the extended state arrays (the tile's tc cells followed by its halo
+// cells) h, hu, hv, z; its packed face records and their geometry arrays;
+// its halo index list. After the stages: the face slots (3 components x
+// 3 faces x tc), the extended velocities u, v and the NS mbarriers. Every
+// offset is a multiple of 16 bytes.
 struct TileLayout {
   uint32_t ext, rec_cap, halo_cap;
-  uint32_t off_h, off_hu, off_hv, off_z, off_gn2, off_area, off_irP;
-  uint32_t off_tA, off_tB, off_nx, off_ny, off_len, off_hidx;
+  uint32_t off_h, off_hu, off_hv, off_z;
+  uint32_t off_tS, off_g0, off_g1, off_g2, off_hidx;
   uint32_t stage;
   uint32_t off_slots, off_u, off_v, off_bars, total;
 };
 
-inline TileLayout make_tile_layout(uint32_t w, uint32_t nt, uint32_t ns, uint32_t rec_cap,
-                                   uint32_t halo_cap) {
+inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, uint32_t ns,
+                                   uint32_t rec_cap, uint32_t halo_cap) {
   auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
   TileLayout L{};
   L.rec_cap = rec_cap;
   L.halo_cap = halo_cap;
-  L.ext = nt + halo_cap;
+  L.ext = tc + halo_cap;
   uint32_t o = 0;
   L.off_h = o; o += a16(L.ext * w);
   L.off_hu = o; o += a16(L.ext * w);
   L.off_hv = o; o += a16(L.ext * w);
   L.off_z = o; o += a16(L.ext * w);
-  L.off_gn2 = o; o += a16(nt * w);
-  L.off_area = o; o += a16(nt * w);
-  L.off_irP = o; o += a16(nt * w);
-  L.off_tA = o; o += a16(rec_cap * 4);
-  L.off_tB = o; o += a16(rec_cap * 4);
-  L.off_nx = o; o += a16(rec_cap * w);
-  L.off_ny = o; o += a16(rec_cap * w);
-  L.off_len = o; o += a16(rec_cap * w);
+  L.off_tS = o; o += a16(rec_cap * 4);
+  L.off_g0 = o; o += a16(rec_cap * w);
+  L.off_g1 = o; o += a16(rec_cap * w);
+  L.off_g2 = o; o += geo_arrays > 2 ? a16(rec_cap * w) : 0u;
   L.off_hidx = o; o += a16(halo_cap * 4);
   L.stage = o;
   o = ns * L.stage;
-  L.off_slots = o; o += a16(9 * nt * w);
+  L.off_slots = o; o += a16(9 * tc * w);
   L.off_u = o; o += a16(L.ext * w);
   L.off_v = o; o += a16(L.ext * w);
   L.off_bars = o; o += a16(ns * 8);
@@ -617,29 +673,35 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t nt, uint32_t ns, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// Tiled one-launch step. A persistent block walks tiles of NT consecutive
-// cells (tile = blockIdx.x + k gridDim.x) through NS shared-memory stages:
+// Tiled one-launch step. A persistent block of NT threads walks tiles of
+// TC = NT * CPT consecutive cells (tile = blockIdx.x + k gridDim.x) through
+// NS shared-memory stages:
 //   - thread 0 queues bulk async copies (TMA) of tile k+NS-1's cell arrays,
 //     face records and halo list while the block works on tile k;
 //   - once tile k+1's copies have landed (mid-iteration k), every thread
-//     gathers its halo cells' states from global memory with cp.async;
-//   (1) velocities of the tile's cells and halo cells;
-//   (2) every face record of the tile once: interior faces of the tile fill
+//     gathers its halo cells' states from global memory with cp.async, and
+//     the velocities of tile k+1's cells and halo cells are derived at the
+//     end of iteration k;
+//   (1) every face record of the tile once: interior faces of the tile fill
 //       both of their cells' slots, faces shared with another tile fill only
 //       this tile's slot (that tile computes the same face from the same
 //       inputs), walls mirror; slots are face-major (face k of tile cell j at
-//       k NT + j);
-//   (3) each cell sums its three face slots in face order and is updated.
-// Cell arrays are padded to whole tiles so every copy moves NT values.
+//       k TC + j);
+//   (2) each cell sums its three face slots in face order and is updated.
+// Two block barriers per tile. Cell arrays are padded to whole tiles so every
+// copy moves TC values.
 // ---------------------------------------------------------------------------
 // Resident blocks per SM the tiled kernel is compiled for (register budget):
 // 1024 threads per SM for FP32, 512 for FP64.
 template <typename Real, int NT>
 constexpr int tiled_min_blocks() { return (sizeof(Real) == 4 ? 1024 : 512) / NT; }
 
-template <typename Real, bool Comp, int NT, int NS>
+// NT threads per block, CPT cells per thread: tiles of TC = NT * CPT cells.
+template <typename Real, bool Comp, int NT, int NS, int CPT>
 __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     k_tiled_step(DevMesh<Real> m, DevState<Real> s, Num num, TileLayout L) {
+  constexpr int TC = NT * CPT;
+  __shared__ int s_nrec[NS], s_nh[NS];  // record and halo counts of each stage's tile
   extern __shared__ __align__(128) unsigned char smem[];
   Real* slots = reinterpret_cast<Real*>(smem + L.off_slots);
   Real* eu = reinterpret_cast<Real*>(smem + L.off_u);
@@ -674,26 +736,24 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   // Thread 0: queue the bulk copies of tile t into stage st.
   auto issue = [&](int st, int t) {
     unsigned char* p = smem + st * L.stage;
-    const int64_t base = (int64_t)t * NT;
+    const int64_t base = (int64_t)t * TC;
     const int64_t r0 = m.toff[t], h0 = m.hoff[t];
     const uint32_t nrec = (uint32_t)(m.toff[t + 1] - r0);
     const uint32_t nh = (uint32_t)(m.hoff[t + 1] - h0);
-    const uint32_t cell = NT * (uint32_t)sizeof(Real);
+    const uint32_t cell = TC * (uint32_t)sizeof(Real);
+    s_nrec[st] = (int)nrec;
+    s_nh[st] = (int)nh;
     const uint32_t rb = nrec * (uint32_t)sizeof(Real);
     fence_proxy_async();
-    mbar_expect_tx(&bar[st], 7 * cell + nrec * 8 + 3 * rb + nh * 4);
+    mbar_expect_tx(&bar[st], 4 * cell + nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
     bulk_g2s(p + L.off_h, h + base, cell, &bar[st]);
     bulk_g2s(p + L.off_hu, hu + base, cell, &bar[st]);
     bulk_g2s(p + L.off_hv, hv + base, cell, &bar[st]);
     bulk_g2s(p + L.off_z, z + base, cell, &bar[st]);
-    bulk_g2s(p + L.off_gn2, s.gn2 + base, cell, &bar[st]);
-    bulk_g2s(p + L.off_area, m.area + base, cell, &bar[st]);
-    bulk_g2s(p + L.off_irP, m.irP + base, cell, &bar[st]);
-    bulk_g2s(p + L.off_tA, m.tA + r0, nrec * 4, &bar[st]);
-    bulk_g2s(p + L.off_tB, m.tB + r0, nrec * 4, &bar[st]);
-    bulk_g2s(p + L.off_nx, m.tnx + r0, rb, &bar[st]);
-    bulk_g2s(p + L.off_ny, m.tny + r0, rb, &bar[st]);
-    bulk_g2s(p + L.off_len, m.tlen + r0, rb, &bar[st]);
+    bulk_g2s(p + L.off_tS, m.tS + r0, nrec * 4, &bar[st]);
+    bulk_g2s(p + L.off_g0, m.tg0 + r0, rb, &bar[st]);
+    bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
+    if (Geo<Real>::kArrays > 2) bulk_g2s(p + L.off_g2, m.tg2 + r0, rb, &bar[st]);
     if (nh > 0) bulk_g2s(p + L.off_hidx, m.hidx + h0, nh * 4, &bar[st]);
     pending |= 1u << st;
   };
@@ -706,15 +766,17 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     }
     return ok;
   };
-  // All threads: gather tile t's halo states into stage st (after its copies landed).
-  auto gather_halo = [&](int st, int t) {
+  // All threads: gather the halo states of stage st's tile (after its copies
+  // landed) with cp.async; the thread that gathers halo cell q later derives
+  // that cell's velocity (halo_velocities).
+  auto gather_halo = [&](int st) {
     unsigned char* p = smem + st * L.stage;
     const int32_t* hl = reinterpret_cast<const int32_t*>(p + L.off_hidx);
-    const int nh = (int)(m.hoff[t + 1] - m.hoff[t]);
-    Real* xh = reinterpret_cast<Real*>(p + L.off_h) + NT;
-    Real* xhu = reinterpret_cast<Real*>(p + L.off_hu) + NT;
-    Real* xhv = reinterpret_cast<Real*>(p + L.off_hv) + NT;
-    Real* xz = reinterpret_cast<Real*>(p + L.off_z) + NT;
+    const int nh = s_nh[st];
+    Real* xh = reinterpret_cast<Real*>(p + L.off_h) + TC;
+    Real* xhu = reinterpret_cast<Real*>(p + L.off_hu) + TC;
+    Real* xhv = reinterpret_cast<Real*>(p + L.off_hv) + TC;
+    Real* xz = reinterpret_cast<Real*>(p + L.off_z) + TC;
     for (int q = tid; q < nh; q += NT) {
       const int c = hl[q];
       cp_async(xh + q, h + c);
@@ -722,6 +784,22 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       cp_async(xhv + q, hv + c);
       cp_async(xz + q, z + c);
     }
+  };
+  // Velocities of stage st's tile cells (nc of them) and, once this thread's
+  // own halo copies have landed, of the halo cells it gathered.
+  auto velocities = [&](int st, int nc) {
+    const unsigned char* p = smem + st * L.stage;
+    const Real* xh = reinterpret_cast<const Real*>(p + L.off_h);
+    const Real* xhu = reinterpret_cast<const Real*>(p + L.off_hu);
+    const Real* xhv = reinterpret_cast<const Real*>(p + L.off_hv);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int j = tid + c * NT;
+      if (j < nc) velocity(xh[j], xhu[j], xhv[j], num, eu[j], ev[j]);
+    }
+    cp_async_wait_all();
+    const int nh = s_nh[st];
+    for (int q = TC + tid; q < TC + nh; q += NT) velocity(xh[q], xhu[q], xhv[q], num, eu[q], ev[q]);
   };
 
   MassAcc<Real> mass;
@@ -738,11 +816,14 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     if (__syncthreads_or(!ok)) {
       timeout = 1;
     } else {
-      gather_halo(0, tile);
-      cp_async_wait_all();
+      gather_halo(0);
+      velocities(0, min(TC, (int)m.T - tile * TC));
       __syncthreads();
     }
   }
+  // Each iteration: face records of tile k (velocities already in shared
+  // memory), then the cell updates of tile k together with the halo gather
+  // and velocities of tile k+1. Two block barriers per tile.
   for (int k = 0; !timeout && tile < ntiles; tile += G, ++k) {
     const int st = k % NS;
     const int t_next = tile + G;
@@ -754,43 +835,44 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     const Real* xhu = reinterpret_cast<const Real*>(p + L.off_hu);
     const Real* xhv = reinterpret_cast<const Real*>(p + L.off_hv);
     const Real* xz = reinterpret_cast<const Real*>(p + L.off_z);
-    const Real* c_gn2 = reinterpret_cast<const Real*>(p + L.off_gn2);
-    const Real* c_area = reinterpret_cast<const Real*>(p + L.off_area);
-    const Real* c_irP = reinterpret_cast<const Real*>(p + L.off_irP);
-    const int32_t* rA = reinterpret_cast<const int32_t*>(p + L.off_tA);
-    const int32_t* rB = reinterpret_cast<const int32_t*>(p + L.off_tB);
-    const Real* rnx = reinterpret_cast<const Real*>(p + L.off_nx);
-    const Real* rny = reinterpret_cast<const Real*>(p + L.off_ny);
-    const Real* rlen = reinterpret_cast<const Real*>(p + L.off_len);
-    const int base = tile * NT;
-    const int nc = min(NT, (int)m.T - base);
-    const int nrec = (int)(m.toff[tile + 1] - m.toff[tile]);
-    const int nh = (int)(m.hoff[tile + 1] - m.hoff[tile]);
+    const int32_t* rS = reinterpret_cast<const int32_t*>(p + L.off_tS);
+    const Real* rg0 = reinterpret_cast<const Real*>(p + L.off_g0);
+    const Real* rg1 = reinterpret_cast<const Real*>(p + L.off_g1);
+    const Real* rg2 = reinterpret_cast<const Real*>(p + L.off_g2);
+    const int base = tile * TC;
+    const int nc = min(TC, (int)m.T - base);
+    const int nrec = s_nrec[st];
+    // this thread's cells' area, perimeter/area and g n^2 (cell arrays are
+    // padded to whole tiles, so the loads are always in bounds)
+    Real c_area[CPT], c_irP[CPT], c_gn2[CPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      c_area[cc] = m.area[base + tid + cc * NT];
+      c_irP[cc] = m.irP[base + tid + cc * NT];
+      c_gn2[cc] = s.gn2[base + tid + cc * NT];
+    }
 
-    // (1) velocities of the tile's cells and of its halo cells
-    if (tid < nc) velocity(xh[tid], xhu[tid], xhv[tid], num, eu[tid], ev[tid]);
-    for (int q = tid; q < nh; q += NT)
-      velocity(xh[NT + q], xhu[NT + q], xhv[NT + q], num, eu[NT + q], ev[NT + q]);
-    __syncthreads();
-
-    // (2) face records
+    // face records
     for (int r = tid; r < nrec; r += NT) {
-      const int32_t a = rA[r];
-      if (a == kWallSide) continue;  // padding record
-      const int32_t b = rB[r];
-      const bool wall = (b == kWallSide);
-      const int ia = a < 0 ? ((-1 - a) & (NT - 1)) : NT + a;
-      const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (NT - 1)) : NT + b);
+      const int32_t packed = rS[r];
+      const int a = packed >> 16;                       // side A code
+      if (a == kSideWall) continue;                     // padding record
+      const int b = (int)(int16_t)(packed & 0xffff);   // side B code
+      const bool wall = (b == kSideWall);
+      const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
+      const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (TC - 1)) : TC + b);
+      Real nx, ny, len;
+      Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
       Real c0, cA1, cA2, cB1, cB2;
-      face_flux<Real>(xh[ia], eu[ia], ev[ia], xz[ia], xh[ib], eu[ib], ev[ib], xz[ib], wall, rnx[r],
-                      rny[r], rlen[r], num, c0, cA1, cA2, cB1, cB2);
+      face_flux<Real>(xh[ia], eu[ia], ev[ia], xz[ia], xh[ib], eu[ib], ev[ib], xz[ib], wall, nx, ny,
+                      len, num, c0, cA1, cA2, cB1, cB2);
       if (a < 0) {
         const int sl = -1 - a;
-        slots[sl] = c0; slots[3 * NT + sl] = cA1; slots[6 * NT + sl] = cA2;
+        slots[sl] = c0; slots[3 * TC + sl] = cA1; slots[6 * TC + sl] = cA2;
       }
       if (b < 0 && !wall) {
         const int sl = -1 - b;
-        slots[sl] = -c0; slots[3 * NT + sl] = -cB1; slots[6 * NT + sl] = -cB2;
+        slots[sl] = -c0; slots[3 * TC + sl] = -cB1; slots[6 * TC + sl] = -cB2;
       }
     }
     // The next tile's copies must have landed before its halo is gathered.
@@ -799,19 +881,22 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       timeout = 1;
       break;
     }
+    if (t_next < ntiles) gather_halo((k + 1) % NS);
 
-    // (3) cells; meanwhile the next tile's halo gathers are in flight
-    if (t_next < ntiles) gather_halo((k + 1) % NS, t_next);
-    if (tid < nc) {
+    // cell updates of tile k
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      const int j = tid + cc * NT;
+      if (j >= nc) break;
       Real rhi[3], rlo[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const Real* cq = slots + q * 3 * NT + tid;  // faces kf at cq[kf * NT]
+        const Real* cq = slots + q * 3 * TC + j;  // faces kf at cq[kf * TC]
         rhi[q] = cq[0];
         rlo[q] = Real(0);
 #pragma unroll
         for (int kf = 1; kf < 3; ++kf) {
-          const Real c = cq[kf * NT];
+          const Real c = cq[kf * TC];
           if (Comp) {
             Real sum, err;
             two_sum(rhi[q], c, sum, err);
@@ -822,15 +907,16 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
           }
         }
       }
-      const int i = base + tid;
+      const int i = base + j;
       Real a1, b1, c1;
-      cell_finish<Real, Comp>(xh[tid], xhu[tid], xhv[tid], c_area[tid], c_irP[tid], c_gn2[tid], dt,
-                              rhi, rlo, num, a1, b1, c1, mass, rate, bad, neg);
+      cell_finish<Real, Comp>(xh[j], xhu[j], xhv[j], c_area[cc], c_irP[cc], c_gn2[cc], dt, rhi, rlo,
+                              num, a1, b1, c1, mass, rate, bad, neg);
       h1[i] = a1;
       hu1[i] = b1;
       hv1[i] = c1;
     }
-    cp_async_wait_all();
+    // velocities of tile k+1 (its records read them after the barrier)
+    if (t_next < ntiles) velocities((k + 1) % NS, min(TC, (int)m.T - t_next * TC));
     __syncthreads();
   }
   // After a timed-out wait, let every copy still in flight land before the

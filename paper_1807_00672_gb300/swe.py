@@ -47,6 +47,7 @@ class Params(ctypes.Structure):
         ("kernel", ctypes.c_int32),
         ("tile", ctypes.c_int32),
         ("stages", ctypes.c_int32),
+        ("cells_per_thread", ctypes.c_int32),
     ]
 
 
@@ -116,7 +117,7 @@ def _check(status: int, what: str):
 
 
 def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, courant=0.7,
-           h_eps=1e-6, stages=0) -> Params:
+           h_eps=1e-6, stages=0, cells_per_thread=0) -> Params:
     p = Params()
     lib().swe_params_default(ctypes.byref(p))
     p.g, p.courant, p.h_eps = g, courant, h_eps
@@ -125,6 +126,7 @@ def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, coura
     p.kernel = KERNEL[kernel]
     p.tile = tile
     p.stages = stages
+    p.cells_per_thread = cells_per_thread
     return p
 
 
@@ -132,10 +134,11 @@ class Mesh:
     """Device-resident mesh (swe_mesh_create)."""
 
     def __init__(self, xy, tri, *, precision="f64", order="morton", kernel="auto", tile=0,
-                 stages=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6):
+                 stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6):
         xy = _f64(xy).reshape(-1, 2)
         tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
-        self.prm = params(precision, order, kernel, tile, g, courant, h_eps, stages)
+        self.prm = params(precision, order, kernel, tile, g, courant, h_eps, stages,
+                          cells_per_thread)
         self.precision = precision
         h = ctypes.c_void_p()
         s = lib().swe_mesh_create(_p(xy), xy.shape[0], _p(tri), tri.shape[0],
