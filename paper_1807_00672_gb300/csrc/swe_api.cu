@@ -108,6 +108,7 @@ struct swe_state {
   Arena arena;
   void *h[2] = {nullptr, nullptr}, *hu[2] = {nullptr, nullptr}, *hv[2] = {nullptr, nullptr};
   void *z = nullptr, *gn2 = nullptr;
+  int stride = 1;  // 4: interleaved cells (h, hu, hv, z) for the tiled kernel
   void* fx[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double* partial = nullptr;
   double* stage = nullptr;  // T doubles in caller order
@@ -156,6 +157,7 @@ swe::DevState<Real> dev_state(const swe_state* s) {
     d.hu[b] = (Real*)s->hu[b];
     d.hv[b] = (Real*)s->hv[b];
   }
+  d.stride = s->stride;
   d.z = (const Real*)s->z;
   d.gn2 = (const Real*)s->gn2;
   for (int k = 0; k < 5; ++k) d.fx[k] = (Real*)s->fx[k];
@@ -279,13 +281,13 @@ void launch_cfl(const swe_state* s) {
 }
 
 template <typename Real>
-void launch_gather(const swe_mesh* m, const double* src, void* dst) {
-  swe::k_gather<Real><<<grid_for(m->T, 256, m->sms * 16), 256, 0, m->stream>>>(src, m->perm, (Real*)dst, m->T);
+void launch_gather(const swe_mesh* m, const double* src, void* dst, int stride) {
+  swe::k_gather<Real><<<grid_for(m->T, 256, m->sms * 16), 256, 0, m->stream>>>(src, m->perm, (Real*)dst, m->T, stride);
 }
 
 template <typename Real>
-void launch_scatter(const swe_mesh* m, const void* src, double* dst) {
-  swe::k_scatter<Real><<<grid_for(m->T, 256, m->sms * 16), 256, 0, m->stream>>>((const Real*)src, m->perm, dst, m->T);
+void launch_scatter(const swe_mesh* m, const void* src, double* dst, int stride) {
+  swe::k_scatter<Real><<<grid_for(m->T, 256, m->sms * 16), 256, 0, m->stream>>>((const Real*)src, m->perm, dst, m->T, stride);
 }
 
 size_t real_size(const swe_mesh* m) { return m->prm.precision == SWE_F64 ? 8 : 4; }
@@ -364,8 +366,8 @@ swe_status upload_state_fields(swe_state* s, const double* h, const double* hu, 
   void* dst[3] = {s->h[0], s->hu[0], s->hv[0]};
   for (int k = 0; k < 3; ++k) {
     CK(cudaMemcpyAsync(s->stage, src[k], m->T * 8, cudaMemcpyHostToDevice, m->stream));
-    if (m->prm.precision == SWE_F64) launch_gather<double>(m, s->stage, dst[k]);
-    else launch_gather<float>(m, s->stage, dst[k]);
+    if (m->prm.precision == SWE_F64) launch_gather<double>(m, s->stage, dst[k], s->stride);
+    else launch_gather<float>(m, s->stage, dst[k], s->stride);
   }
   CK(cudaGetLastError());
   return SWE_OK;
@@ -441,7 +443,7 @@ swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri
     const int nt = p.tile / p.cells_per_thread;
     if (p.tile % p.cells_per_thread != 0 || (nt != 64 && nt != 128 && nt != 256)) return SWE_EINVAL;
   }
-  if (p.stages == 0) p.stages = 3;
+  if (p.stages == 0) p.stages = 2;
   if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
   if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
   const int kernel = (p.kernel == SWE_KERNEL_EDGE) ? SWE_KERNEL_EDGE : SWE_KERNEL_TILED;
@@ -623,9 +625,15 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
   const int64_t T = m->T, E = m->E, Tp = m->Tp;
   swe_state* s = new swe_state();
   s->mesh = m;
+  const bool interleaved = (m->kernel == SWE_KERNEL_TILED);
   Layout L;
-  for (int k = 0; k < 6; ++k) L.add(w * Tp);  // h, hu, hv x 2
-  L.add(w * Tp); L.add(w * Tp);                // z, gn2
+  if (interleaved) {
+    L.add(4 * w * Tp); L.add(4 * w * Tp);     // cells (h, hu, hv, z) x 2
+  } else {
+    for (int k = 0; k < 6; ++k) L.add(w * Tp);  // h, hu, hv x 2
+    L.add(w * Tp);                              // z
+  }
+  L.add(w * Tp);                                // gn2
   if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) L.add(w * E);
   L.add(8 * (size_t)m->max_grid);
   L.add(8 * T);                              // staging
@@ -640,12 +648,23 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
     swe_state_destroy(s);
     return SWE_ECUDA;
   }
-  for (int b = 0; b < 2; ++b) {
-    s->h[b] = s->arena.take(w * Tp);
-    s->hu[b] = s->arena.take(w * Tp);
-    s->hv[b] = s->arena.take(w * Tp);
+  if (interleaved) {
+    s->stride = 4;
+    for (int b = 0; b < 2; ++b) {
+      char* c = (char*)s->arena.take(4 * w * Tp);
+      s->h[b] = c;
+      s->hu[b] = c + w;
+      s->hv[b] = c + 2 * w;
+    }
+    s->z = (char*)s->h[0] + 3 * w;  // the step carries z into the other buffer
+  } else {
+    for (int b = 0; b < 2; ++b) {
+      s->h[b] = s->arena.take(w * Tp);
+      s->hu[b] = s->arena.take(w * Tp);
+      s->hv[b] = s->arena.take(w * Tp);
+    }
+    s->z = s->arena.take(w * Tp);
   }
-  s->z = s->arena.take(w * Tp);
   s->gn2 = s->arena.take(w * Tp);
   if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) s->fx[k] = s->arena.take(w * E);
   s->partial = (double*)s->arena.take(8 * (size_t)m->max_grid);
@@ -676,8 +695,9 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
       st = SWE_ECUDA;
       break;
     }
-    if (m->prm.precision == SWE_F64) launch_gather<double>(m, s->stage, dsts[k]);
-    else launch_gather<float>(m, s->stage, dsts[k]);
+    const int sd = (k == 0) ? s->stride : 1;  // z lives in the cells, gn2 is its own array
+    if (m->prm.precision == SWE_F64) launch_gather<double>(m, s->stage, dsts[k], sd);
+    else launch_gather<float>(m, s->stage, dsts[k], sd);
   }
   if (st == SWE_OK && cuda_failed(cudaStreamSynchronize(m->stream))) st = SWE_ECUDA;
   if (st == SWE_OK) st = upload_state_fields(s, h, hu, hv);
@@ -755,8 +775,8 @@ swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, d
   const void* src[3] = {s->h[cur], s->hu[cur], s->hv[cur]};
   for (int k = 0; k < 3; ++k) {
     if (!dst[k]) continue;
-    if (m->prm.precision == SWE_F64) launch_scatter<double>(m, src[k], s->stage);
-    else launch_scatter<float>(m, src[k], s->stage);
+    if (m->prm.precision == SWE_F64) launch_scatter<double>(m, src[k], s->stage, s->stride);
+    else launch_scatter<float>(m, src[k], s->stage, s->stride);
     CK(cudaMemcpyAsync(dst[k], s->stage, m->T * 8, cudaMemcpyDeviceToHost, m->stream));
     CK(cudaStreamSynchronize(m->stream));
   }

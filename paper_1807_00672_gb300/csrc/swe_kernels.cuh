@@ -98,11 +98,16 @@ struct DevMesh {
   const Real* tg2;
 };
 
+// Cell state of one buffer b: h[b][i * stride], hu[b][i * stride],
+// hv[b][i * stride]. stride 1: separate arrays (two-launch kernels);
+// stride 4: interleaved cells (h, hu, hv, z), h[b] the cell array's base
+// (tiled kernel), z also read from h[b] + 3.
 template <typename Real>
 struct DevState {
   Real* h[2];
   Real* hu[2];
   Real* hv[2];
+  int stride;
   const Real* z;
   const Real* gn2;  // g * n^2 per cell
   // scratch
@@ -255,6 +260,28 @@ struct MassAcc<float> {
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
+
+// Four consecutive values (one interleaved cell or one face slot).
+template <typename Real>
+struct V4 {
+  Real x, y, z, w;
+};
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st4(float* p, float x, float y, float z, float w) {
+  *reinterpret_cast<float4*>(p) = make_float4(x, y, z, w);
+}
+__device__ __forceinline__ void st4(double* p, double x, double y, double z, double w) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(x, y);
+  reinterpret_cast<double2*>(p)[1] = make_double2(z, w);
+}
 
 // ---------------------------------------------------------------------------
 // HLLC flux in the face frame (Toro's shallow-water form). hA, hB are the
@@ -626,23 +653,26 @@ __device__ __forceinline__ void cp_async(float* dst, const float* src) {
 __device__ __forceinline__ void cp_async(double* dst, const double* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+// 16 bytes global -> shared (both 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Shared-memory plan of k_tiled_step, sized on the host from the mesh's
 // largest per-tile record and halo counts. Each of the NS stages holds one
-// tile: the extended state arrays (the tile's tc cells followed by its halo
-// cells) h, hu, hv, z; its packed face records and their geometry arrays;
-// its halo index list. After the stages: the face slots (3 components x
-// 3 faces x tc), the extended velocities u, v and the NS mbarriers. Every
-// offset is a multiple of 16 bytes.
+// tile: its interleaved cells (h, hu, hv, z), the tile's tc cells followed by
+// its halo cells; its packed face records and their geometry arrays; its halo
+// index list. After the stages: the face slots (c0, c1, c2, -) per face of
+// each tile cell, face-major, and the NS mbarriers. Every offset is a
+// multiple of 16 bytes.
 struct TileLayout {
   uint32_t ext, rec_cap, halo_cap;
-  uint32_t off_h, off_hu, off_hv, off_z;
-  uint32_t off_tS, off_g0, off_g1, off_g2, off_hidx;
+  uint32_t off_cells, off_tS, off_g0, off_g1, off_g2, off_hidx;
   uint32_t stage;
-  uint32_t off_slots, off_u, off_v, off_bars, total;
+  uint32_t off_slots, off_bars, total;
 };
 
 inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, uint32_t ns,
@@ -653,10 +683,7 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
   L.halo_cap = halo_cap;
   L.ext = tc + halo_cap;
   uint32_t o = 0;
-  L.off_h = o; o += a16(L.ext * w);
-  L.off_hu = o; o += a16(L.ext * w);
-  L.off_hv = o; o += a16(L.ext * w);
-  L.off_z = o; o += a16(L.ext * w);
+  L.off_cells = o; o += a16(L.ext * 4 * w);
   L.off_tS = o; o += a16(rec_cap * 4);
   L.off_g0 = o; o += a16(rec_cap * w);
   L.off_g1 = o; o += a16(rec_cap * w);
@@ -664,25 +691,22 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
   L.off_hidx = o; o += a16(halo_cap * 4);
   L.stage = o;
   o = ns * L.stage;
-  L.off_slots = o; o += a16(9 * tc * w);
-  L.off_u = o; o += a16(L.ext * w);
-  L.off_v = o; o += a16(L.ext * w);
+  L.off_slots = o; o += a16(3 * tc * 4 * w);
   L.off_bars = o; o += a16(ns * 8);
   L.total = o;
   return L;
 }
 
 // ---------------------------------------------------------------------------
-// Tiled one-launch step. A persistent block of NT threads walks tiles of
-// TC = NT * CPT consecutive cells (tile = blockIdx.x + k gridDim.x) through
-// NS shared-memory stages:
+// Tiled one-launch step on interleaved cells (h, hu, hv, z). A persistent
+// block of NT threads walks tiles of TC = NT * CPT consecutive cells
+// (tile = blockIdx.x + k gridDim.x) through NS shared-memory stages:
 //   - thread 0 queues bulk async copies (TMA) of tile k+NS-1's cell arrays,
 //     face records and halo list while the block works on tile k;
 //   - once tile k+1's copies have landed (mid-iteration k), every thread
-//     gathers its halo cells' states from global memory with cp.async, and
-//     the velocities of tile k+1's cells and halo cells are derived at the
-//     end of iteration k;
-//   (1) every face record of the tile once: interior faces of the tile fill
+//     gathers its halo cells (16 bytes each) with cp.async;
+//   (1) every face record of the tile once, velocities formed per side:
+//       interior faces of the tile fill
 //       both of their cells' slots, faces shared with another tile fill only
 //       this tile's slot (that tile computes the same face from the same
 //       inputs), walls mirror; slots are face-major (face k of tile cell j at
@@ -703,25 +727,19 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   constexpr int TC = NT * CPT;
   __shared__ int s_nrec[NS], s_nh[NS];  // record and halo counts of each stage's tile
   extern __shared__ __align__(128) unsigned char smem[];
-  Real* slots = reinterpret_cast<Real*>(smem + L.off_slots);
-  Real* eu = reinterpret_cast<Real*>(smem + L.off_u);
-  Real* ev = reinterpret_cast<Real*>(smem + L.off_v);
+  Real* slots = reinterpret_cast<Real*>(smem + L.off_slots);  // [3 TC][4], face k of cell j at k TC + j
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bars);
 
   Ctl* ctl = s.ctl;
   if (ctl->done) return;
   const int cur = ctl->cur;
   const Real dt = Real(ctl->dt);
-  const Real* __restrict__ h = cur ? s.h[1] : s.h[0];
-  const Real* __restrict__ hu = cur ? s.hu[1] : s.hu[0];
-  const Real* __restrict__ hv = cur ? s.hv[1] : s.hv[0];
-  const Real* __restrict__ z = s.z;
-  Real* __restrict__ h1 = cur ? s.h[0] : s.h[1];
-  Real* __restrict__ hu1 = cur ? s.hu[0] : s.hu[1];
-  Real* __restrict__ hv1 = cur ? s.hv[0] : s.hv[1];
+  const Real* __restrict__ U = cur ? s.h[1] : s.h[0];  // interleaved cells (h, hu, hv, z)
+  Real* __restrict__ U1 = cur ? s.h[0] : s.h[1];
   const int tid = threadIdx.x;
   const int ntiles = (int)m.ntiles;
   const int G = (int)gridDim.x;
+  const Real g = Real(num.g);
 
   if (tid == 0) {
 #pragma unroll
@@ -740,16 +758,13 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     const int64_t r0 = m.toff[t], h0 = m.hoff[t];
     const uint32_t nrec = (uint32_t)(m.toff[t + 1] - r0);
     const uint32_t nh = (uint32_t)(m.hoff[t + 1] - h0);
-    const uint32_t cell = TC * (uint32_t)sizeof(Real);
+    const uint32_t cells = TC * 4 * (uint32_t)sizeof(Real);
     s_nrec[st] = (int)nrec;
     s_nh[st] = (int)nh;
     const uint32_t rb = nrec * (uint32_t)sizeof(Real);
     fence_proxy_async();
-    mbar_expect_tx(&bar[st], 4 * cell + nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
-    bulk_g2s(p + L.off_h, h + base, cell, &bar[st]);
-    bulk_g2s(p + L.off_hu, hu + base, cell, &bar[st]);
-    bulk_g2s(p + L.off_hv, hv + base, cell, &bar[st]);
-    bulk_g2s(p + L.off_z, z + base, cell, &bar[st]);
+    mbar_expect_tx(&bar[st], cells + nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
+    bulk_g2s(p + L.off_cells, U + 4 * base, cells, &bar[st]);
     bulk_g2s(p + L.off_tS, m.tS + r0, nrec * 4, &bar[st]);
     bulk_g2s(p + L.off_g0, m.tg0 + r0, rb, &bar[st]);
     bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
@@ -766,40 +781,18 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     }
     return ok;
   };
-  // All threads: gather the halo states of stage st's tile (after its copies
-  // landed) with cp.async; the thread that gathers halo cell q later derives
-  // that cell's velocity (halo_velocities).
+  // All threads: gather the halo cells of stage st's tile (after its copies
+  // landed), one interleaved cell per cp.async group.
   auto gather_halo = [&](int st) {
     unsigned char* p = smem + st * L.stage;
     const int32_t* hl = reinterpret_cast<const int32_t*>(p + L.off_hidx);
+    Real* xc = reinterpret_cast<Real*>(p + L.off_cells) + 4 * TC;
     const int nh = s_nh[st];
-    Real* xh = reinterpret_cast<Real*>(p + L.off_h) + TC;
-    Real* xhu = reinterpret_cast<Real*>(p + L.off_hu) + TC;
-    Real* xhv = reinterpret_cast<Real*>(p + L.off_hv) + TC;
-    Real* xz = reinterpret_cast<Real*>(p + L.off_z) + TC;
     for (int q = tid; q < nh; q += NT) {
-      const int c = hl[q];
-      cp_async(xh + q, h + c);
-      cp_async(xhu + q, hu + c);
-      cp_async(xhv + q, hv + c);
-      cp_async(xz + q, z + c);
-    }
-  };
-  // Velocities of stage st's tile cells (nc of them) and, once this thread's
-  // own halo copies have landed, of the halo cells it gathered.
-  auto velocities = [&](int st, int nc) {
-    const unsigned char* p = smem + st * L.stage;
-    const Real* xh = reinterpret_cast<const Real*>(p + L.off_h);
-    const Real* xhu = reinterpret_cast<const Real*>(p + L.off_hu);
-    const Real* xhv = reinterpret_cast<const Real*>(p + L.off_hv);
+      const Real* src = U + 4 * (int64_t)hl[q];
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int j = tid + c * NT;
-      if (j < nc) velocity(xh[j], xhu[j], xhv[j], num, eu[j], ev[j]);
+      for (int b = 0; b < (int)sizeof(Real) / 4; ++b) cp_async16(xc + 4 * q + b * (16 / sizeof(Real)), src + b * (16 / sizeof(Real)));
     }
-    cp_async_wait_all();
-    const int nh = s_nh[st];
-    for (int q = TC + tid; q < TC + nh; q += NT) velocity(xh[q], xhu[q], xhv[q], num, eu[q], ev[q]);
   };
 
   MassAcc<Real> mass;
@@ -817,13 +810,12 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       timeout = 1;
     } else {
       gather_halo(0);
-      velocities(0, min(TC, (int)m.T - tile * TC));
+      cp_async_wait_all();
       __syncthreads();
     }
   }
-  // Each iteration: face records of tile k (velocities already in shared
-  // memory), then the cell updates of tile k together with the halo gather
-  // and velocities of tile k+1. Two block barriers per tile.
+  // Each iteration: the face records of tile k, then the cell updates of
+  // tile k while tile k+1's halo gather is in flight. Two block barriers.
   for (int k = 0; !timeout && tile < ntiles; tile += G, ++k) {
     const int st = k % NS;
     const int t_next = tile + G;
@@ -831,10 +823,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     // ended iteration k-1.
     if (tid == 0 && tile + (NS - 1) * G < ntiles) issue((k + NS - 1) % NS, tile + (NS - 1) * G);
     const unsigned char* p = smem + st * L.stage;
-    const Real* xh = reinterpret_cast<const Real*>(p + L.off_h);
-    const Real* xhu = reinterpret_cast<const Real*>(p + L.off_hu);
-    const Real* xhv = reinterpret_cast<const Real*>(p + L.off_hv);
-    const Real* xz = reinterpret_cast<const Real*>(p + L.off_z);
+    const Real* xc = reinterpret_cast<const Real*>(p + L.off_cells);  // [ext][4]
     const int32_t* rS = reinterpret_cast<const int32_t*>(p + L.off_tS);
     const Real* rg0 = reinterpret_cast<const Real*>(p + L.off_g0);
     const Real* rg1 = reinterpret_cast<const Real*>(p + L.off_g1);
@@ -861,19 +850,18 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       const bool wall = (b == kSideWall);
       const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
       const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (TC - 1)) : TC + b);
+      const V4<Real> A = ld4(xc + 4 * ia);
+      const V4<Real> B = ld4(xc + 4 * ib);
+      Real uA, vA, uB, vB;
+      velocity(A.x, A.y, A.z, num, uA, vA);
+      velocity(B.x, B.y, B.z, num, uB, vB);
       Real nx, ny, len;
       Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
       Real c0, cA1, cA2, cB1, cB2;
-      face_flux<Real>(xh[ia], eu[ia], ev[ia], xz[ia], xh[ib], eu[ib], ev[ib], xz[ib], wall, nx, ny,
-                      len, num, c0, cA1, cA2, cB1, cB2);
-      if (a < 0) {
-        const int sl = -1 - a;
-        slots[sl] = c0; slots[3 * TC + sl] = cA1; slots[6 * TC + sl] = cA2;
-      }
-      if (b < 0 && !wall) {
-        const int sl = -1 - b;
-        slots[sl] = -c0; slots[3 * TC + sl] = -cB1; slots[6 * TC + sl] = -cB2;
-      }
+      face_flux<Real>(A.x, uA, vA, A.w, B.x, uB, vB, B.w, wall, nx, ny, len, num, c0, cA1, cA2, cB1,
+                      cB2);
+      if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
+      if (b < 0 && !wall) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, Real(0));
     }
     // The next tile's copies must have landed before its halo is gathered.
     const bool ok = (tid == 0 && t_next < ntiles) ? wait_stage((k + 1) % NS) : true;
@@ -888,35 +876,30 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     for (int cc = 0; cc < CPT; ++cc) {
       const int j = tid + cc * NT;
       if (j >= nc) break;
-      Real rhi[3], rlo[3];
+      const V4<Real> f0 = ld4(slots + 4 * j);
+      const V4<Real> f1 = ld4(slots + 4 * (TC + j));
+      const V4<Real> f2 = ld4(slots + 4 * (2 * TC + j));
+      Real rhi[3] = {f0.x, f0.y, f0.z}, rlo[3] = {Real(0), Real(0), Real(0)};
+      const Real add1[3] = {f1.x, f1.y, f1.z}, add2[3] = {f2.x, f2.y, f2.z};
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const Real* cq = slots + q * 3 * TC + j;  // faces kf at cq[kf * TC]
-        rhi[q] = cq[0];
-        rlo[q] = Real(0);
-#pragma unroll
-        for (int kf = 1; kf < 3; ++kf) {
-          const Real c = cq[kf * TC];
-          if (Comp) {
-            Real sum, err;
-            two_sum(rhi[q], c, sum, err);
-            rhi[q] = sum;
-            rlo[q] = add_rn(rlo[q], err);
-          } else {
-            rhi[q] = rhi[q] + c;
-          }
+        if (Comp) {
+          Real s1, e1, s2, e2;
+          two_sum(rhi[q], add1[q], s1, e1);
+          two_sum(s1, add2[q], s2, e2);
+          rhi[q] = s2;
+          rlo[q] = add_rn(e1, e2);
+        } else {
+          rhi[q] = rhi[q] + add1[q] + add2[q];
         }
       }
-      const int i = base + j;
+      const V4<Real> c = ld4(xc + 4 * j);
       Real a1, b1, c1;
-      cell_finish<Real, Comp>(xh[j], xhu[j], xhv[j], c_area[cc], c_irP[cc], c_gn2[cc], dt, rhi, rlo,
-                              num, a1, b1, c1, mass, rate, bad, neg);
-      h1[i] = a1;
-      hu1[i] = b1;
-      hv1[i] = c1;
+      cell_finish<Real, Comp>(c.x, c.y, c.z, c_area[cc], c_irP[cc], c_gn2[cc], dt, rhi, rlo, num, a1,
+                              b1, c1, mass, rate, bad, neg);
+      st4(U1 + 4 * (int64_t)(base + j), a1, b1, c1, c.w);
     }
-    // velocities of tile k+1 (its records read them after the barrier)
-    if (t_next < ntiles) velocities((k + 1) % NS, min(TC, (int)m.T - t_next * TC));
+    cp_async_wait_all();
     __syncthreads();
   }
   // After a timed-out wait, let every copy still in flight land before the
@@ -942,9 +925,10 @@ __global__ void __launch_bounds__(256) k_cfl(DevMesh<Real> m, DevState<Real> s, 
   MassAcc<Real> mass;
   Real rate = Real(0);
   int bad = 0;
+  const int64_t sd = s.stride;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m.T;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const Real hh = h[i], qx = hu[i], qy = hv[i];
+    const Real hh = h[i * sd], qx = hu[i * sd], qy = hv[i * sd];
     if (O::wet(hh, num)) {
       const Real lam = O::div(O::sqrt_(qx * qx + qy * qy), hh) + O::sqrt_(Real(num.g) * hh);
       rate = fmax(rate, lam * m.irP[i]);
@@ -972,22 +956,22 @@ static __global__ void __launch_bounds__(256) k_mass_sum(Ctl* ctl, const double*
   if (threadIdx.x == 0) ctl->mass = sh[0];
 }
 
-// Caller order (double) -> internal order (Real): dst[j] = src[perm[j]].
+// Caller order (double) -> internal order (Real): dst[j * stride] = src[perm[j]].
 template <typename Real>
 __global__ void k_gather(const double* __restrict__ src, const int32_t* __restrict__ perm,
-                         Real* __restrict__ dst, int64_t n) {
+                         Real* __restrict__ dst, int64_t n, int stride) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x)
-    dst[j] = Real(src[perm[j]]);
+    dst[j * stride] = Real(src[perm[j]]);
 }
 
-// Internal order (Real) -> caller order (double): dst[perm[j]] = src[j].
+// Internal order (Real) -> caller order (double): dst[perm[j]] = src[j * stride].
 template <typename Real>
 __global__ void k_scatter(const Real* __restrict__ src, const int32_t* __restrict__ perm,
-                          double* __restrict__ dst, int64_t n) {
+                          double* __restrict__ dst, int64_t n, int stride) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x)
-    dst[perm[j]] = double(src[j]);
+    dst[perm[j]] = double(src[j * stride]);
 }
 
 }  // namespace swe

@@ -127,6 +127,7 @@ extern "C" swe_status swe_step_edges_static(
   s.h[1] = h_out;
   s.hu[1] = hu_out;
   s.hv[1] = hv_out;
+  s.stride = 1;
   s.z = z;
   s.gn2 = gn2;
   for (int k = 0; k < 5; ++k) s.fx[k] = faces + (size_t)k * n_edges;
