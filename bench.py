@@ -113,6 +113,20 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def job_rate(local_cells: int, local_seconds: float, dist=None, device=None):
+    """Whole-job rate over replicas: every rank's cell-updates over the slowest
+    rank's time (max over ranks). Without a process group, the local rate.
+    Returns (cells_per_second, slowest_seconds, total_cells)."""
+    if dist is None:
+        return local_cells / local_seconds, local_seconds, local_cells
+    import torch
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(local_cells)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return c.item() / t.item(), t.item(), int(c.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -246,11 +260,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     clocks = sampler.stop() if sampler else None
     st.sync()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * T * args.steps / (ms * 1e-3)
+    value, secs_max, _ = job_rate(T * args.steps, ms * 1e-3, dist, dev)
+    ms = secs_max * 1e3
 
     # Dominant kernel: per-launch CUDA events around single-step launches.
     per_launch = []
@@ -306,13 +317,9 @@ def main():
     st.run(e2e_steps, sync=False)
     swe_copy_ptrs(st, ho)
     t1 = time.perf_counter()
-    secs = t1 - t0
-    if dist is not None:
-        t = torch.tensor([secs], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+    e2e_value, secs, _ = job_rate(T * e2e_steps, t1 - t0, dist, dev)
     nbytes = 3 * 8 * T
-    out["e2e"] = {"value": ws * T * e2e_steps / secs, "unit": UNIT,
+    out["e2e"] = {"value": e2e_value, "unit": UNIT,
                   "h2d_bytes_per_step": nbytes / e2e_steps, "d2h_bytes_per_step": nbytes / e2e_steps,
                   "steps_per_call": e2e_steps, "h2d_bytes_per_call": nbytes,
                   "d2h_bytes_per_call": nbytes,
