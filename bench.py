@@ -202,7 +202,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=0, help="solver steps per e2e call (0 = --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the fp64 and error legs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the fp64, error and ensemble legs")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble leg")
+    ap.add_argument("--ensemble-steps", type=int, default=200)
     ap.add_argument("--ref-cells", type=int, default=25_000)
     ap.add_argument("--cpu-cells", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=150)
@@ -328,6 +331,8 @@ def main():
     if rank == 0 and not args.no_extras:
         out["fp64"] = fp64_leg(case, args, stream, ws)
         out["error"] = error_leg(args)
+    if rank == 0 and not args.no_extras and not args.no_ensemble:
+        out["ensemble"] = ensemble_leg(args, stream)
     st.close()
     mesh.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -390,6 +395,54 @@ def fp64_leg(case, args, stream, ws):
     return {"value": mesh.T / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "steps": args.fp64_steps, "hbm_frac": achieved / peak, "achieved_gbs": achieved,
             "alg_bytes_per_cell": balg}
+
+
+def ensemble_leg(args, stream):
+    """256 independent dam-break scenarios of log-uniform size (5k-500k
+    triangles, 26.6M in all) in one mesh, FP32: the kernel shape comes from
+    the autotuner (measured on every 8th scenario), then the whole ensemble
+    is timed over --ensemble-steps steps replayed from CUDA graphs."""
+    import torch
+    from paper_1807_00672_gb300 import autotune, inputs, swe
+    t0 = time.perf_counter()
+    cases = inputs.ensemble_cases()
+    total = sum(c.mesh.n_tris for c in cases)
+    tuned = autotune.tune(cases[::8], "f32", key_cells=total, key_scenarios=len(cases),
+                          use_cache=False)
+    mesh = swe.Mesh.ensemble([(c.mesh.xy, c.mesh.tri) for c in cases], precision="f32",
+                             tile=tuned["tile"], cells_per_thread=tuned["cells_per_thread"],
+                             stages=tuned["stages"], stream=ctypes_stream(stream))
+    cat = lambda name: np.concatenate([getattr(c, name) for c in cases])
+    st = swe.State(mesh, cat("h"), cat("hu"), cat("hv"), cat("z"), cat("n"))
+    setup_s = time.perf_counter() - t0
+    st.run(16)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    k = args.ensemble_steps
+    a.record(stream)
+    st.run(k, sync=False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    st.sync()
+    ms = a.elapsed_time(b) / k
+    balg = alg_bytes_per_cell(4, False)  # n is constant within a scenario
+    peak, kind = measured_peaks()
+    achieved = balg * mesh.T / (ms * 1e-3) / 1e9
+    steps = {st.scenario(i)["steps"] for i in (0, len(cases) - 1)}
+    res = {"value": mesh.T / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": k,
+           "scenarios": len(cases), "triangles": mesh.T,
+           "triangles_min_max": [min(mesh.scenario_cells), max(mesh.scenario_cells)],
+           "hbm_frac": achieved / peak, "achieved_gbs": achieved, "alg_bytes_per_cell": balg,
+           "peak_source": f"{kind} HBM copy bandwidth",
+           "shape": {"tile": tuned["tile"], "cells_per_thread": tuned["cells_per_thread"],
+                     "stages": tuned["stages"], "autotuned_on": f"{len(cases[::8])} scenarios"},
+           "autotune_trials": [(t["shape"], round(t["sec_per_step"] * 1e6, 1))
+                               for t in tuned["trials"] if "sec_per_step" in t],
+           "setup_s": setup_s, "scenario_steps": sorted(steps)}
+    st.close()
+    mesh.close()
+    return res
 
 
 def error_leg(args, cells=50_000, steps=100):

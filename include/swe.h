@@ -107,8 +107,30 @@ void swe_params_default(swe_params* p);
 swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tris,
                            const swe_params* params, void* cuda_stream, swe_mesh** out);
 
-/* counts[0..3] = nodes, triangles, edges, wall edges. */
+/* Builds one device-resident mesh holding n_scenarios independent scenarios
+ * (an ensemble): scenario i has the nodes xy[i] (n_nodes[i] of them) and the
+ * triangles tri[i] (n_tris[i]), in the formats of swe_mesh_create. The
+ * scenarios share no edge and each keeps its own time, CFL time step, step
+ * count, error word and mass; one step launch advances all of them (the
+ * paper's per-cell parallelism, Sec. 2.3, over the union of their cells).
+ * Cell arrays of every other call are the concatenation of the scenarios'
+ * cells in scenario order (scenario 0's n_tris[0] cells first). Requires
+ * SWE_KERNEL_TILED (or AUTO); SWE_KERNEL_EDGE with n_scenarios > 1 returns
+ * SWE_EINVAL. Each scenario is validated as swe_mesh_create validates a
+ * mesh; the first invalid one makes the call fail with nothing allocated.
+ * swe_mesh_create(...) is this call with n_scenarios = 1. */
+swe_status swe_mesh_create_batch(int32_t n_scenarios, const double* const* xy,
+                                 const int64_t* n_nodes, const int32_t* const* tri,
+                                 const int64_t* n_tris, const swe_params* params,
+                                 void* cuda_stream, swe_mesh** out);
+
+/* counts[0..3] = nodes, triangles, edges, wall edges (sums over scenarios). */
 swe_status swe_mesh_counts(const swe_mesh* mesh, int64_t* counts);
+
+/* *n_scenarios = scenarios in the mesh; n_tris (may be NULL, else
+ * [*n_scenarios] entries, caller-allocated: call once with NULL to size it)
+ * receives each scenario's triangle count. */
+swe_status swe_mesh_scenarios(const swe_mesh* mesh, int32_t* n_scenarios, int64_t* n_tris);
 
 /* Device bytes held by the mesh. */
 swe_status swe_mesh_device_bytes(const swe_mesh* mesh, int64_t* bytes);
@@ -128,7 +150,8 @@ swe_status swe_state_init(swe_mesh* mesh, const double* h, const double* hu, con
 swe_status swe_state_set(swe_state* state, const double* h, const double* hu, const double* hv);
 
 /* One step with the current CFL time step (no end-time clamp). Synchronises;
- * *dt_used (may be NULL) receives the step's dt. */
+ * *dt_used (may be NULL) receives the step's dt (scenario 0's on an
+ * ensemble: every scenario steps with its own CFL dt). */
 swe_status swe_step(swe_state* state, double* dt_used);
 
 /* Queues n_steps CFL steps without an end time and returns without
@@ -138,23 +161,35 @@ swe_status swe_run(swe_state* state, int64_t n_steps);
 
 /* Steps until t == t_end exactly: each step uses min(CFL dt, t_end - t), and
  * the step that reaches t_end sets t = t_end. Synchronises once per chunk of
- * graph-replayed steps. *n_steps (may be NULL) receives the steps taken. */
+ * graph-replayed steps. *n_steps (may be NULL) receives the steps taken
+ * (scenario 0's). On an ensemble every scenario stops at t_end on its own
+ * step count; launches continue until the last one gets there. */
 swe_status swe_advance(swe_state* state, double t_end, int64_t* n_steps);
 
 /* Waits for queued work and returns the latched device status. */
 swe_status swe_sync(swe_state* state);
 
 /* Copies the state to host arrays in caller order (any pointer may be NULL).
- * *t = simulated time, *mass = sum of area * h in FP64. Synchronises. */
+ * *t = simulated time (scenario 0's on an ensemble), *mass = sum of area * h
+ * in FP64 over every cell. Synchronises. */
 swe_status swe_copy_out(const swe_state* state, double* h, double* hu, double* hv, double* t,
                         double* mass);
 
-/* info[0] = steps taken, info[1] = cells whose depth went negative and was
- * clipped to 0 (expected 0 under the CFL step), info[2] = latched error bits. */
+/* info[0] = steps taken (scenario 0's), info[1] = cells whose depth went
+ * negative and was clipped to 0 (expected 0 under the CFL step), info[2] =
+ * latched error bits (both over every scenario). */
 swe_status swe_state_info(const swe_state* state, int64_t* info);
 
-/* The CFL time step the next swe_step would use (before any end-time clamp). */
+/* The CFL time step the next swe_step would use (before any end-time clamp).
+ * On an ensemble: scenario 0's (see swe_scenario_info). */
 swe_status swe_next_dt(const swe_state* state, double* dt);
+
+/* One scenario of an ensemble (0 <= scenario < n_scenarios, else
+ * SWE_EINVAL): its time, mass (sum of area * h over its cells, FP64), steps
+ * taken and next CFL time step; any output pointer may be NULL. Returns that
+ * scenario's latched status. Synchronises. */
+swe_status swe_scenario_info(const swe_state* state, int32_t scenario, double* t, double* mass,
+                             int64_t* steps, double* dt_next);
 
 void swe_state_destroy(swe_state* state);
 

@@ -56,6 +56,10 @@ def lib():
         L.oracle_advance.argtypes = [vp, pp, dbl, i64, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_advance.restype = ctypes.c_int
         L.oracle_cells_after_step.argtypes = [vp, pp, dbl, vp, vp, vp, vp, vp, vp, i64, vp]
+        L.oracle_run_tangent.argtypes = [vp, pp, i64, vp] + [vp] * 5 + [vp] * 5 + [vp, i64, vp, vp]
+        L.oracle_run_tangent.restype = i64
+        L.oracle_run_dts.argtypes = [vp, pp, i64, vp] + [vp] * 5 + [vp, i64, vp]
+        L.oracle_run_dts.restype = i64
         _lib = L
     return _lib
 
@@ -187,6 +191,40 @@ class State:
                                       _p(self.hu), _p(self.hv), _p(self.z), _p(self.n),
                                       _p(cells), cells.shape[0], _p(out))
         return out
+
+
+    def run_dts(self, dts, gauges=None):
+        """Steps with the prescribed time steps dts (state advanced in place).
+        Returns the gauge depths [len(dts), len(gauges)] after each step."""
+        dts = _f64(dts)
+        g = np.ascontiguousarray(gauges if gauges is not None else [], dtype=np.int32)
+        gh = np.zeros((dts.shape[0], g.shape[0]))
+        neg = lib().oracle_run_dts(self.mesh._h, ctypes.byref(self.prm), dts.shape[0], _p(dts),
+                                   _p(self.h), _p(self.hu), _p(self.hv), _p(self.z), _p(self.n),
+                                   _p(g), g.shape[0], _p(gh))
+        self.neg += int(neg)
+        self.t += float(dts.sum())
+        return gh
+
+    def run_tangent(self, dts, dh, dhu, dhv, dz=None, dn=None, gauges=None):
+        """Forward-mode derivative of run_dts along the direction (dh, dhu,
+        dhv, dz, dn). Advances the state; returns (tangent of (h, hu, hv) at
+        the end, gauge depths, gauge tangents)."""
+        dts = _f64(dts)
+        t = [_f64(a).copy() for a in (dh, dhu, dhv)]
+        dz = None if dz is None else _f64(dz)
+        dn = None if dn is None else _f64(dn)
+        g = np.ascontiguousarray(gauges if gauges is not None else [], dtype=np.int32)
+        gh = np.zeros((dts.shape[0], g.shape[0]))
+        gd = np.zeros((dts.shape[0], g.shape[0]))
+        neg = lib().oracle_run_tangent(
+            self.mesh._h, ctypes.byref(self.prm), dts.shape[0], _p(dts), _p(self.h), _p(self.hu),
+            _p(self.hv), _p(self.z), _p(self.n), _p(t[0]), _p(t[1]), _p(t[2]),
+            None if dz is None else _p(dz), None if dn is None else _p(dn), _p(g), g.shape[0],
+            _p(gh), _p(gd))
+        self.neg += int(neg)
+        self.t += float(dts.sum())
+        return t, gh, gd
 
 
 def hllc(hL, unL, utL, hR, unR, utR, g=G) -> np.ndarray:

@@ -565,6 +565,71 @@ int oracle_advance(const void* mp, const oracle_params* p, double t_end, int64_t
   return st;
 }
 
+// Forward-mode derivative of n_steps steps with the PRESCRIBED time steps
+// dts[0 .. n_steps) (the dt sequence is data, not a function of the state).
+// (h, hu, hv) are advanced in place; (dh, dhu, dhv) carry the tangent of the
+// initial state in and the tangent of the final state out; dz and dn are the
+// tangents of the bed and of Manning's n (NULL = zero). If gauges is given,
+// gauge_h[k * n_gauges + j] and gauge_dh[...] receive h and its tangent at
+// cell gauges[j] after step k + 1 (either may be NULL). Every step is the
+// plain step above instantiated on a one-direction dual number, so the
+// derivative follows the branch each comparison takes (Sec. 2.2 scheme,
+// differentiated piecewise).
+int64_t oracle_run_tangent(const void* mp, const oracle_params* p, int64_t n_steps,
+                           const double* dts, double* h, double* hu, double* hv, const double* z,
+                           const double* n, double* dh, double* dhu, double* dhv,
+                           const double* dz, const double* dn, const int32_t* gauges,
+                           int64_t n_gauges, double* gauge_h, double* gauge_dh) {
+  using D = Dual<1>;
+  const Mesh* m = static_cast<const Mesh*>(mp);
+  Params pp = P(p);
+  const int64_t T = m->T;
+  std::vector<D> H(T), HU(T), HV(T), Z(T), NN(T), H1(T), HU1(T), HV1(T);
+  for (int64_t i = 0; i < T; ++i) {
+    H[i] = D(h[i]); H[i].d[0] = dh[i];
+    HU[i] = D(hu[i]); HU[i].d[0] = dhu[i];
+    HV[i] = D(hv[i]); HV[i].d[0] = dhv[i];
+    Z[i] = D(z[i]); Z[i].d[0] = dz ? dz[i] : 0.0;
+    NN[i] = D(n[i]); NN[i].d[0] = dn ? dn[i] : 0.0;
+  }
+  int64_t negs = 0;
+  for (int64_t k = 0; k < n_steps; ++k) {
+    negs += step(*m, pp, D(dts[k]), H.data(), HU.data(), HV.data(), Z.data(), NN.data(),
+                 H1.data(), HU1.data(), HV1.data());
+    H.swap(H1); HU.swap(HU1); HV.swap(HV1);
+    for (int64_t j = 0; j < n_gauges; ++j) {
+      const D& v = H[gauges[j]];
+      if (gauge_h) gauge_h[k * n_gauges + j] = v.v;
+      if (gauge_dh) gauge_dh[k * n_gauges + j] = v.d[0];
+    }
+  }
+  for (int64_t i = 0; i < T; ++i) {
+    h[i] = H[i].v; hu[i] = HU[i].v; hv[i] = HV[i].v;
+    dh[i] = H[i].d[0]; dhu[i] = HU[i].d[0]; dhv[i] = HV[i].d[0];
+  }
+  return negs;
+}
+
+// n_steps steps with the prescribed time steps dts (plain values; the
+// finite-difference side of the derivative checks). Gauges as above.
+int64_t oracle_run_dts(const void* mp, const oracle_params* p, int64_t n_steps, const double* dts,
+                       double* h, double* hu, double* hv, const double* z, const double* n,
+                       const int32_t* gauges, int64_t n_gauges, double* gauge_h) {
+  const Mesh* m = static_cast<const Mesh*>(mp);
+  Params pp = P(p);
+  std::vector<double> h1(m->T), hu1(m->T), hv1(m->T);
+  int64_t negs = 0;
+  for (int64_t k = 0; k < n_steps; ++k) {
+    negs += step(*m, pp, dts[k], h, hu, hv, z, n, h1.data(), hu1.data(), hv1.data());
+    std::memcpy(h, h1.data(), sizeof(double) * m->T);
+    std::memcpy(hu, hu1.data(), sizeof(double) * m->T);
+    std::memcpy(hv, hv1.data(), sizeof(double) * m->T);
+    for (int64_t j = 0; j < n_gauges; ++j)
+      if (gauge_h) gauge_h[k * n_gauges + j] = h[gauges[j]];
+  }
+  return negs;
+}
+
 // Updated state of selected cells only, for one step of length dt from the
 // given state (used to check full-size runs cell by cell). out is 3 x m.
 void oracle_cells_after_step(const void* mp, const oracle_params* p, double dt, const double* h,

@@ -1,15 +1,22 @@
 // C ABI of the shallow-water step library (declared in include/swe.h).
 //
-// Handles own one device arena each (mesh: geometry and connectivity; state:
-// two state buffers, bed, friction, scratch and the control word). Steps are
-// queued on the mesh's stream; repeated steps replay a captured CUDA graph of
-// kStepsPerGraph steps. Kernels pick the current buffer, dt and the stop flag
-// from the control word, so one graph serves any step count and end time
-// (the host crosses PCIe/C2C only at set-up and copy-out, Sec. 2.3).
+// A mesh handle holds one or more independent scenarios (an ensemble), each
+// with its own triangles, state, time step and clock; a single mesh is an
+// ensemble of one. Handles own one device arena each (mesh: geometry,
+// connectivity and the tiled kernel's work chunks; state: two state buffers,
+// friction coefficients, scratch and one control word per scenario). Steps
+// are queued on the mesh's stream; repeated steps replay a captured CUDA
+// graph of kStepsPerGraph launches. Kernels read each scenario's current
+// buffer, dt and stop flag from its control word, so one graph serves any
+// step count and end time (the host crosses to the device only at set-up and
+// copy-out, Sec. 2.3).
+#include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <limits>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/swe.h"
@@ -18,15 +25,17 @@
 
 namespace swe {
 
-// Sets the end time and re-clamps the next dt (one thread).
-__global__ void k_set_end(Ctl* ctl, double t_end) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  ctl->t_end = t_end;
-  if (ctl->err) { ctl->done = 1; return; }
-  const double rest = t_end - ctl->t;
-  ctl->done = (ctl->t >= t_end) ? 1 : 0;
-  if (ctl->dt_cfl >= rest) { ctl->dt = rest; ctl->clamped = 1; }
-  else { ctl->dt = ctl->dt_cfl; ctl->clamped = 0; }
+// Sets the end time of every scenario and re-clamps its next dt.
+__global__ void k_set_end(Ctl* ctls, int n, double t_end) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    Ctl* ctl = ctls + i;
+    ctl->t_end = t_end;
+    if (ctl->err) { ctl->done = 1; continue; }
+    const double rest = t_end - ctl->t;
+    ctl->done = (ctl->t >= t_end) ? 1 : 0;
+    if (ctl->dt_cfl >= rest) { ctl->dt = rest; ctl->clamped = 1; }
+    else { ctl->dt = ctl->dt_cfl; ctl->clamped = 0; }
+  }
 }
 
 }  // namespace swe
@@ -75,6 +84,15 @@ struct Layout {
   void add(size_t bytes) { total += align_up(bytes); }
 };
 
+// Where one scenario lives inside the mesh.
+struct Scenario {
+  int64_t caller0 = 0;  // first caller cell index (scenarios are concatenated)
+  int64_t ncells = 0;
+  int64_t cell0 = 0;    // first internal cell (tile-aligned in the tiled layout)
+  int64_t tile0 = 0, ntiles = 0;
+  int64_t chunk0 = 0, nchunks = 0;  // work chunks (= mass partial slots) of the tiled kernel
+};
+
 }  // namespace
 
 struct swe_mesh {
@@ -88,11 +106,13 @@ struct swe_mesh {
   int tile = kDefaultTile;
   int64_t ntiles = 0, records = 0, halos = 0;
   int stages = 2;
-  int cpt = 1;  // cells per thread of the tiled kernel (threads = tile / cpt)
+  int cpt = 2;  // cells per thread of the tiled kernel (threads = tile / cpt)
   swe::TileLayout layout{};
-  int64_t Tp = 0;  // cell arrays' length (padded to whole tiles for the tiled kernel)
+  int64_t Tp = 0;  // internal cell slots (tiled: scenarios padded to whole tiles)
+  std::vector<Scenario> scen;
+  int64_t nchunks = 0;
   Arena arena;
-  int32_t* perm = nullptr;
+  int32_t* perm = nullptr;  // internal cell -> caller cell (-1 for padding)
   void* area = nullptr;
   void* irP = nullptr;
   int32_t *eL = nullptr, *eR = nullptr, *cf[3] = {nullptr, nullptr, nullptr};
@@ -100,7 +120,10 @@ struct swe_mesh {
   int64_t *toff = nullptr, *hoff = nullptr;
   int32_t *tS = nullptr, *hidx = nullptr;
   void *tg0 = nullptr, *tg1 = nullptr, *tg2 = nullptr;
-  int grid_edge = 1, grid_cell = 1, grid_tiled = 1, grid_cfl = 1, max_grid = 1;
+  int32_t *chunk_scen = nullptr, *chunk_tile0 = nullptr, *chunk_ntiles = nullptr;
+  int32_t* chunk_stride = nullptr;
+  int32_t* scen_cell_end = nullptr;
+  int grid_edge = 1, grid_cell = 1, grid_cfl = 1, max_grid = 1;
 };
 
 struct swe_state {
@@ -111,15 +134,17 @@ struct swe_state {
   int stride = 1;  // 4: interleaved cells (h, hu, hv, z) for the tiled kernel
   void* fx[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double* partial = nullptr;
-  double* stage = nullptr;  // T doubles in caller order
-  swe::Ctl* ctl = nullptr;
+  double* stage = nullptr;       // T doubles in caller order
+  swe::Ctl* ctl = nullptr;       // one per scenario
   swe::Ctl* host_ctl = nullptr;  // pinned mirror
   cudaStream_t capture = nullptr;
   cudaGraphExec_t graph = nullptr;
-  bool open_ended = true;  // the device t_end is +inf
+  bool open_ended = true;  // the device t_end is +inf for every scenario
 };
 
 namespace {
+
+int nscen(const swe_mesh* m) { return (int)m->scen.size(); }
 
 swe::Num num_of(const swe_mesh* m) { return swe::make_num(m->prm.g, m->prm.courant, m->prm.h_eps); }
 
@@ -138,6 +163,11 @@ swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
   d.cf0 = m->cf[0];
   d.cf1 = m->cf[1];
   d.cf2 = m->cf[2];
+  d.chunk_scen = m->chunk_scen;
+  d.chunk_tile0 = m->chunk_tile0;
+  d.chunk_ntiles = m->chunk_ntiles;
+  d.chunk_stride = m->chunk_stride;
+  d.scen_cell_end = m->scen_cell_end;
   d.ntiles = m->ntiles;
   d.toff = m->toff;
   d.hoff = m->hoff;
@@ -215,10 +245,11 @@ template <typename Real, bool Comp, int NT, int CPT>
 void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::DevState<Real>& ds,
                      const swe::Num& num, cudaStream_t st) {
   const swe::TileLayout& L = m->layout;
+  const int g = (int)m->nchunks;
   if (m->stages == 3)
-    swe::k_tiled_step<Real, Comp, NT, 3, CPT><<<m->grid_tiled, NT, L.total, st>>>(dm, ds, num, L);
+    swe::k_tiled_step<Real, Comp, NT, 3, CPT><<<g, NT, L.total, st>>>(dm, ds, num, L);
   else
-    swe::k_tiled_step<Real, Comp, NT, 2, CPT><<<m->grid_tiled, NT, L.total, st>>>(dm, ds, num, L);
+    swe::k_tiled_step<Real, Comp, NT, 2, CPT><<<g, NT, L.total, st>>>(dm, ds, num, L);
 }
 
 template <typename Real, bool Comp, int CPT>
@@ -232,7 +263,7 @@ void launch_tiled_cpt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe
 }
 
 template <typename Real>
-void set_grids(swe_mesh* m) {
+void set_edge_grids(swe_mesh* m) {
   int occ_cell = 0, occ_edge = 0, occ_cfl = 0;
   constexpr bool comp = sizeof(Real) == 4;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cell, swe::k_cell_update<Real, comp>, 256, 0);
@@ -244,12 +275,6 @@ void set_grids(swe_mesh* m) {
   m->grid_edge = grid_for(m->E, 256, m->sms * occ_edge * 4);
   m->grid_cell = grid_for(m->T, 256, m->sms * occ_cell);
   m->grid_cfl = grid_for(m->T, 256, m->sms * occ_cfl);
-  if (m->kernel == SWE_KERNEL_TILED) {
-    int64_t g = (int64_t)m->sms * blocks_per_sm_tiled<Real>(m);
-    m->grid_tiled = (int)(m->ntiles < g ? m->ntiles : g);
-    if (m->grid_tiled < 1) m->grid_tiled = 0;  // the layout does not fit: reported by mesh_create
-  }
-  m->max_grid = std::max(std::max(m->grid_cell, m->grid_cfl), m->grid_tiled);
 }
 
 template <typename Real>
@@ -277,31 +302,39 @@ void launch_one_step(const swe_state* s, cudaStream_t st) {
 template <typename Real>
 void launch_cfl(const swe_state* s) {
   const swe_mesh* m = s->mesh;
-  swe::k_cfl<Real><<<m->grid_cfl, 256, 0, m->stream>>>(dev_mesh<Real>(m), dev_state<Real>(s), num_of(m));
+  if (m->kernel == SWE_KERNEL_EDGE)
+    swe::k_cfl<Real><<<m->grid_cfl, 256, 0, m->stream>>>(dev_mesh<Real>(m), dev_state<Real>(s), num_of(m));
+  else
+    swe::k_cfl_tiled<Real><<<(int)m->nchunks, 256, 0, m->stream>>>(dev_mesh<Real>(m), dev_state<Real>(s),
+                                                                  num_of(m), m->tile);
 }
 
 template <typename Real>
 void launch_gather(const swe_mesh* m, const double* src, void* dst, int stride) {
-  swe::k_gather<Real><<<grid_for(m->T, 256, m->sms * 16), 256, 0, m->stream>>>(src, m->perm, (Real*)dst, m->T, stride);
+  swe::k_gather<Real><<<grid_for(m->Tp, 256, m->sms * 16), 256, 0, m->stream>>>(src, m->perm, (Real*)dst,
+                                                                               m->Tp, stride);
 }
 
 template <typename Real>
 void launch_scatter(const swe_mesh* m, const void* src, double* dst, int stride) {
-  swe::k_scatter<Real><<<grid_for(m->T, 256, m->sms * 16), 256, 0, m->stream>>>((const Real*)src, m->perm, dst, m->T, stride);
+  swe::k_scatter<Real><<<grid_for(m->Tp, 256, m->sms * 16), 256, 0, m->stream>>>((const Real*)src, m->perm,
+                                                                                dst, m->Tp, stride);
 }
 
 size_t real_size(const swe_mesh* m) { return m->prm.precision == SWE_F64 ? 8 : 4; }
 
-// Host FP64 vector -> device array of the mesh precision.
+// Host FP64 vector -> device array of the mesh precision. Synchronous: the
+// host vector may go out of scope on return.
 swe_status upload_real(const swe_mesh* m, const std::vector<double>& v, void* dst) {
   if (v.empty()) return SWE_OK;
   if (m->prm.precision == SWE_F64) {
     CK(cudaMemcpyAsync(dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
   } else {
     std::vector<float> f(v.size());
     for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
     CK(cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, m->stream));
-    CK(cudaStreamSynchronize(m->stream));  // f goes out of scope
+    CK(cudaStreamSynchronize(m->stream));
   }
   return SWE_OK;
 }
@@ -310,18 +343,33 @@ template <typename T>
 swe_status upload(const swe_mesh* m, const std::vector<T>& v, void* dst) {
   if (v.empty()) return SWE_OK;
   CK(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
   return SWE_OK;
 }
 
-swe_status status_from_ctl(const swe::Ctl& c) {
-  if (c.err & swe::kErrTimeout) return SWE_ETIMEOUT;
-  if (c.err & swe::kErrNan) return SWE_ENAN;
-  if (c.err & swe::kErrDry) return SWE_EDRY;
+swe_status status_from_err(int err) {
+  if (err & swe::kErrTimeout) return SWE_ETIMEOUT;
+  if (err & swe::kErrNan) return SWE_ENAN;
+  if (err & swe::kErrDry) return SWE_EDRY;
   return SWE_OK;
+}
+
+// Status over every scenario (the most severe error any of them raised).
+swe_status status_all(const swe_state* s) {
+  int err = 0;
+  for (int i = 0; i < nscen(s->mesh); ++i) err |= s->host_ctl[i].err;
+  return status_from_err(err);
+}
+
+bool all_done(const swe_state* s) {
+  for (int i = 0; i < nscen(s->mesh); ++i)
+    if (!s->host_ctl[i].done) return false;
+  return true;
 }
 
 swe_status read_ctl(const swe_state* s) {
-  CK(cudaMemcpyAsync(s->host_ctl, s->ctl, sizeof(swe::Ctl), cudaMemcpyDeviceToHost, s->mesh->stream));
+  CK(cudaMemcpyAsync(s->host_ctl, s->ctl, sizeof(swe::Ctl) * nscen(s->mesh), cudaMemcpyDeviceToHost,
+                     s->mesh->stream));
   CK(cudaStreamSynchronize(s->mesh->stream));
   return SWE_OK;
 }
@@ -353,10 +401,15 @@ swe_status queue_steps(swe_state* s, int64_t n) {
   return SWE_OK;
 }
 
-// Makes the device end time +inf (no clamp) unless it already is.
+void set_end(swe_state* s, double t_end) {
+  const int n = nscen(s->mesh);
+  swe::k_set_end<<<(n + 127) / 128, 128, 0, s->mesh->stream>>>(s->ctl, n, t_end);
+}
+
+// Makes every device end time +inf (no clamp) unless it already is.
 void open_end(swe_state* s) {
   if (s->open_ended) return;
-  swe::k_set_end<<<1, 1, 0, s->mesh->stream>>>(s->ctl, std::numeric_limits<double>::infinity());
+  set_end(s, std::numeric_limits<double>::infinity());
   s->open_ended = true;
 }
 
@@ -373,21 +426,341 @@ swe_status upload_state_fields(swe_state* s, const double* h, const double* hu, 
   return SWE_OK;
 }
 
-// Resets the control word to t = 0 in buffer 0 and computes dt and mass.
+// Resets every scenario's control word to t = 0 in buffer 0 and computes
+// its dt and mass.
 swe_status reset_and_cfl(swe_state* s) {
   const swe_mesh* m = s->mesh;
-  swe::Ctl c{};
-  c.t = 0.0;
-  c.t_end = std::numeric_limits<double>::infinity();
+  for (int i = 0; i < nscen(m); ++i) {
+    swe::Ctl c{};
+    c.t = 0.0;
+    c.t_end = std::numeric_limits<double>::infinity();
+    c.part0 = m->scen[i].chunk0;
+    c.nparts = m->scen[i].nchunks;
+    s->host_ctl[i] = c;
+  }
   s->open_ended = true;
-  *s->host_ctl = c;
-  CK(cudaMemcpyAsync(s->ctl, s->host_ctl, sizeof(swe::Ctl), cudaMemcpyHostToDevice, m->stream));
+  CK(cudaMemcpyAsync(s->ctl, s->host_ctl, sizeof(swe::Ctl) * nscen(m), cudaMemcpyHostToDevice,
+                     m->stream));
   if (m->prm.precision == SWE_F64) launch_cfl<double>(s);
   else launch_cfl<float>(s);
   CK(cudaGetLastError());
   swe_status r = read_ctl(s);
   if (r != SWE_OK) return r;
-  return status_from_ctl(*s->host_ctl);
+  return status_all(s);
+}
+
+swe_status resolve_params(const swe_params* params, swe_params& p) {
+  swe_params_default(&p);
+  if (params) p = *params;
+  if (p.precision != SWE_F64 && p.precision != SWE_F32) return SWE_EINVAL;
+  if (p.order != SWE_ORDER_NONE && p.order != SWE_ORDER_MORTON) return SWE_EINVAL;
+  if (p.kernel < SWE_KERNEL_AUTO || p.kernel > SWE_KERNEL_TILED) return SWE_EINVAL;
+  if (p.tile == 0) p.tile = kDefaultTile;
+  if (p.cells_per_thread == 0) p.cells_per_thread = 2;
+  if (p.cells_per_thread != 1 && p.cells_per_thread != 2) return SWE_EINVAL;
+  const int nt = p.tile / p.cells_per_thread;
+  if (p.tile % p.cells_per_thread != 0 || (nt != 64 && nt != 128 && nt != 256)) return SWE_EINVAL;
+  if (p.stages == 0) p.stages = 2;
+  if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
+  if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
+  if (p.kernel == SWE_KERNEL_AUTO) p.kernel = SWE_KERNEL_TILED;
+  return SWE_OK;
+}
+
+// Builds a mesh of n scenarios (swe_mesh_create_batch).
+swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nodes,
+                        const int32_t* const* tri, const int64_t* n_tris, const swe_params* params,
+                        void* cuda_stream, swe_mesh** out) {
+  if (!out) return SWE_EINVAL;
+  *out = nullptr;
+  if (n <= 0 || !xy || !n_nodes || !tri || !n_tris) return SWE_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (n_tris[i] == 0) return SWE_EMESH;
+    if (!xy[i] || !tri[i] || n_nodes[i] <= 0 || n_tris[i] < 0) return SWE_EINVAL;
+  }
+  swe_params p;
+  swe_status st = resolve_params(params, p);
+  if (st != SWE_OK) return st;
+  const int kernel = p.kernel;
+  if (kernel == SWE_KERNEL_EDGE && n > 1) return SWE_EINVAL;
+  const int tile = p.tile;
+
+  // Host-side construction and validation first (scenarios on parallel host
+  // threads): no device is touched for an invalid mesh.
+  std::vector<swe::HostMesh> hm(n);
+  std::vector<int> rc(n, 0);
+  {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nthr = (int)std::min<unsigned>((unsigned)n, std::min(16u, hw));
+    std::atomic<int> next{0};
+    auto work = [&]() {
+      for (int i = next++; i < n; i = next++)
+        rc[i] = swe::build_host_mesh(xy[i], n_nodes[i], tri[i], n_tris[i], p.order,
+                                     kernel == SWE_KERNEL_TILED ? tile : 0,
+                                     kernel == SWE_KERNEL_EDGE, hm[i]);
+    };
+    std::vector<std::thread> pool;
+    for (int k = 1; k < nthr; ++k) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+  }
+  for (int i = 0; i < n; ++i) {
+    if (rc[i] == -2) return SWE_EMESH;
+    if (rc[i] != 0) return SWE_EINVAL;
+  }
+
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+  swe_mesh* m = new swe_mesh();
+  m->prm = p;
+  m->device = dev;
+  m->sms = sms;
+  m->kernel = kernel;
+  m->tile = tile;
+  m->stages = p.stages;
+  m->cpt = p.cells_per_thread;
+  m->scen.resize(n);
+  int64_t caller = 0, cells = 0, tiles = 0, recs = 0, halos = 0, rec_cap = 0, halo_cap = 0;
+  for (int i = 0; i < n; ++i) {
+    Scenario& sc = m->scen[i];
+    sc.caller0 = caller;
+    sc.ncells = hm[i].T;
+    sc.cell0 = cells;
+    sc.tile0 = tiles;
+    sc.ntiles = hm[i].ntiles;
+    caller += hm[i].T;
+    cells += (kernel == SWE_KERNEL_TILED) ? hm[i].ntiles * tile : hm[i].T;
+    tiles += hm[i].ntiles;
+    recs += (int64_t)hm[i].tA.size();
+    halos += (int64_t)hm[i].hidx.size();
+    rec_cap = std::max(rec_cap, hm[i].rec_cap);
+    halo_cap = std::max(halo_cap, hm[i].halo_cap);
+    m->V += hm[i].V;
+    m->E += hm[i].E;
+    m->Eb += hm[i].Eb;
+  }
+  m->T = caller;
+  m->Tp = cells;
+  m->ntiles = tiles;
+  m->records = recs;
+  m->halos = halos;
+  if (m->Tp >= INT32_MAX || recs >= INT32_MAX) {
+    delete m;
+    return SWE_EINVAL;
+  }
+  if (cuda_stream) {
+    m->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cuda_failed(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking))) {
+      delete m;
+      return SWE_ECUDA;
+    }
+    m->own_stream = true;
+  }
+  const size_t w = real_size(m);
+  const int geo_arrays = (p.precision == SWE_F64) ? 3 : 2;
+
+  // Work chunks of the tiled kernel, about one per resident block: scenario
+  // s gets ceil(ntiles_s / per) chunks, and its chunk r walks the tiles
+  // r, r + nchunks_s, r + 2 nchunks_s, ... of the scenario.
+  std::vector<int32_t> ch_scen, ch_tile0, ch_ntiles, ch_stride, cell_end;
+  if (kernel == SWE_KERNEL_TILED) {
+    m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)geo_arrays, (uint32_t)tile,
+                                      (uint32_t)m->stages, (uint32_t)rec_cap, (uint32_t)halo_cap);
+    const int occ = (p.precision == SWE_F64) ? blocks_per_sm_tiled<double>(m)
+                                             : blocks_per_sm_tiled<float>(m);
+    if (occ < 1) {
+      g_cuda_msg = "tiled kernel layout does not fit in shared memory";
+      swe_mesh_destroy(m);
+      return SWE_ECUDA;
+    }
+    // Smallest tile count per chunk for which all chunks fit in one wave of
+    // resident blocks (sum over scenarios of ceil(ntiles_s / per) <= resident);
+    // one scenario gives per = ceil(ntiles / resident). With more scenarios
+    // than resident blocks no per fits: one chunk per scenario.
+    const int64_t resident = (int64_t)sms * occ;
+    int64_t max_nt = 1;
+    for (int i = 0; i < n; ++i) max_nt = std::max(max_nt, m->scen[i].ntiles);
+    auto fits = [&](int64_t per) {
+      if (per >= max_nt) return true;
+      int64_t c = 0;
+      for (int i = 0; i < n; ++i) c += (m->scen[i].ntiles + per - 1) / per;
+      return c <= resident;
+    };
+    int64_t lo = std::max<int64_t>(1, (tiles + resident - 1) / resident), hi = max_nt;
+    lo = std::min(lo, hi);
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (fits(mid)) hi = mid;
+      else lo = mid + 1;
+    }
+    const int64_t per = lo;
+    for (int i = 0; i < n; ++i) {
+      Scenario& sc = m->scen[i];
+      sc.chunk0 = (int64_t)ch_scen.size();
+      sc.nchunks = (sc.ntiles + per - 1) / per;
+      for (int64_t r = 0; r < sc.nchunks; ++r) {
+        ch_scen.push_back(i);
+        ch_tile0.push_back((int32_t)(sc.tile0 + r));
+        ch_ntiles.push_back((int32_t)((sc.ntiles - r + sc.nchunks - 1) / sc.nchunks));
+        ch_stride.push_back((int32_t)sc.nchunks);
+      }
+      cell_end.push_back((int32_t)(sc.cell0 + sc.ncells));
+    }
+    m->nchunks = (int64_t)ch_scen.size();
+  } else {
+    if (p.precision == SWE_F64) set_edge_grids<double>(m);
+    else set_edge_grids<float>(m);
+  }
+  m->max_grid = (int)std::max<int64_t>(std::max(m->grid_cell, m->grid_cfl), m->nchunks);
+
+  // Device layout.
+  const int64_t T = m->T, Tp = m->Tp, E = m->E, R = recs, H = halos;
+  const int64_t C = m->nchunks;
+  Layout L;
+  L.add(4 * Tp);  // perm
+  L.add(w * Tp);  // area
+  L.add(w * Tp);  // irP
+  if (kernel == SWE_KERNEL_EDGE) {
+    L.add(4 * E); L.add(4 * E);
+    L.add(w * E); L.add(w * E); L.add(w * E);
+    L.add(4 * T); L.add(4 * T); L.add(4 * T);
+  } else {
+    L.add(8 * (tiles + 1)); L.add(8 * (tiles + 1));
+    L.add(4 * R);
+    for (int g = 0; g < geo_arrays; ++g) L.add(w * R);
+    L.add(4 * H);
+    L.add(4 * C); L.add(4 * C); L.add(4 * C); L.add(4 * C);
+    L.add(4 * (int64_t)n);
+  }
+  if (cudaMalloc((void**)&m->arena.base, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    swe_mesh_destroy(m);
+    return SWE_ENOMEM;
+  }
+  m->arena.size = L.total;
+  st = SWE_OK;
+  auto chk = [&](swe_status r) { if (st == SWE_OK) st = r; };
+  if (cuda_failed(cudaMemsetAsync(m->arena.base, 0, L.total, m->stream))) chk(SWE_ECUDA);
+  m->perm = (int32_t*)m->arena.take(4 * Tp);
+  m->area = m->arena.take(w * Tp);
+  m->irP = m->arena.take(w * Tp);
+  if (kernel == SWE_KERNEL_EDGE) {
+    m->eL = (int32_t*)m->arena.take(4 * E);
+    m->eR = (int32_t*)m->arena.take(4 * E);
+    m->nx = m->arena.take(w * E);
+    m->ny = m->arena.take(w * E);
+    m->len = m->arena.take(w * E);
+    for (int k = 0; k < 3; ++k) m->cf[k] = (int32_t*)m->arena.take(4 * T);
+  } else {
+    m->toff = (int64_t*)m->arena.take(8 * (tiles + 1));
+    m->hoff = (int64_t*)m->arena.take(8 * (tiles + 1));
+    m->tS = (int32_t*)m->arena.take(4 * R);
+    m->tg0 = m->arena.take(w * R);
+    m->tg1 = m->arena.take(w * R);
+    if (geo_arrays > 2) m->tg2 = m->arena.take(w * R);
+    m->hidx = (int32_t*)m->arena.take(4 * H);
+    m->chunk_scen = (int32_t*)m->arena.take(4 * C);
+    m->chunk_tile0 = (int32_t*)m->arena.take(4 * C);
+    m->chunk_ntiles = (int32_t*)m->arena.take(4 * C);
+    m->chunk_stride = (int32_t*)m->arena.take(4 * C);
+    m->scen_cell_end = (int32_t*)m->arena.take(4 * (int64_t)n);
+  }
+  if (m->arena.overflow) {
+    g_cuda_msg = "mesh arena layout";
+    chk(SWE_ECUDA);
+  }
+
+  // Concatenated host arrays, uploaded one at a time.
+  if (st == SWE_OK) {
+    std::vector<int32_t> perm(Tp, -1);
+    std::vector<double> area(Tp, 0.0), irp(Tp, 0.0);
+    for (int i = 0; i < n; ++i) {
+      const Scenario& sc = m->scen[i];
+      for (int64_t j = 0; j < sc.ncells; ++j) {
+        perm[sc.cell0 + j] = (int32_t)(sc.caller0 + hm[i].perm[j]);
+        area[sc.cell0 + j] = hm[i].area[j];
+        irp[sc.cell0 + j] = hm[i].perim[j] / hm[i].area[j];
+      }
+    }
+    chk(upload(m, perm, m->perm));
+    chk(upload_real(m, area, m->area));
+    chk(upload_real(m, irp, m->irP));
+  }
+  if (st == SWE_OK && kernel == SWE_KERNEL_EDGE) {
+    const swe::HostMesh& h0 = hm[0];
+    chk(upload(m, h0.eL, m->eL));
+    chk(upload(m, h0.eR, m->eR));
+    chk(upload_real(m, h0.nx, m->nx));
+    chk(upload_real(m, h0.ny, m->ny));
+    chk(upload_real(m, h0.len, m->len));
+    for (int k = 0; k < 3; ++k) chk(upload(m, h0.cface[k], m->cf[k]));
+  } else if (st == SWE_OK) {
+    std::vector<int64_t> toff(tiles + 1, 0), hoff(tiles + 1, 0);
+    std::vector<int32_t> packed(R), hidx(H);
+    std::vector<double> g0(R), g1(R), g2(geo_arrays > 2 ? R : 0);
+    auto code = [](int32_t v) { return v == swe::kWall ? (int32_t)swe::kSideWall : v; };
+    bool fits = true;
+    int64_t r_at = 0, h_at = 0;
+    for (int i = 0; i < n; ++i) {
+      const swe::HostMesh& hmi = hm[i];
+      const Scenario& sc = m->scen[i];
+      for (int64_t t = 0; t < hmi.ntiles; ++t) {
+        toff[sc.tile0 + t] = r_at + hmi.toff[t];
+        hoff[sc.tile0 + t] = h_at + hmi.hoff[t];
+      }
+      // Sides as int16 codes packed in one word (A high, B low). Local and
+      // halo codes are relative to the tile, so they need no offset.
+      for (size_t r = 0; r < hmi.tA.size(); ++r) {
+        const int32_t a = code(hmi.tA[r]), b = code(hmi.tB[r]);
+        fits = fits && a >= -32768 && a <= 32767 && b >= -32768 && b <= 32767;
+        packed[r_at + r] = (int32_t)(((uint32_t)(uint16_t)a << 16) | (uint32_t)(uint16_t)b);
+        if (geo_arrays > 2) {
+          g0[r_at + r] = hmi.tnx[r];
+          g1[r_at + r] = hmi.tny[r];
+          g2[r_at + r] = hmi.tlen[r];
+        } else {  // scaled normal l n
+          g0[r_at + r] = hmi.tlen[r] * hmi.tnx[r];
+          g1[r_at + r] = hmi.tlen[r] * hmi.tny[r];
+        }
+      }
+      for (size_t q = 0; q < hmi.hidx.size(); ++q) hidx[h_at + q] = (int32_t)(sc.cell0 + hmi.hidx[q]);
+      r_at += (int64_t)hmi.tA.size();
+      h_at += (int64_t)hmi.hidx.size();
+    }
+    toff[tiles] = r_at;
+    hoff[tiles] = h_at;
+    if (!fits) chk(SWE_EINVAL);
+    chk(upload(m, toff, m->toff));
+    chk(upload(m, hoff, m->hoff));
+    chk(upload(m, packed, m->tS));
+    chk(upload_real(m, g0, m->tg0));
+    chk(upload_real(m, g1, m->tg1));
+    if (geo_arrays > 2) chk(upload_real(m, g2, m->tg2));
+    chk(upload(m, hidx, m->hidx));
+    chk(upload(m, ch_scen, m->chunk_scen));
+    chk(upload(m, ch_tile0, m->chunk_tile0));
+    chk(upload(m, ch_ntiles, m->chunk_ntiles));
+    chk(upload(m, ch_stride, m->chunk_stride));
+    chk(upload(m, cell_end, m->scen_cell_end));
+  }
+  if (st != SWE_OK) {
+    swe_mesh_destroy(m);
+    return st;
+  }
+  *out = m;
+  return SWE_OK;
+}
+
+// Scatters buffer b of field k (0 h, 1 hu, 2 hv) to caller order in stage.
+void scatter_field(const swe_state* s, int k, int b) {
+  const swe_mesh* m = s->mesh;
+  const void* src = (k == 0) ? s->h[b] : (k == 1) ? s->hu[b] : s->hv[b];
+  if (m->prm.precision == SWE_F64) launch_scatter<double>(m, src, s->stage, s->stride);
+  else launch_scatter<float>(m, src, s->stage, s->stride);
 }
 
 }  // namespace
@@ -426,178 +799,27 @@ const char* swe_last_cuda_error(void) { return g_cuda_msg.c_str(); }
 
 swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tris,
                            const swe_params* params, void* cuda_stream, swe_mesh** out) {
-  if (!out) return SWE_EINVAL;
-  *out = nullptr;
-  if (n_tris == 0) return SWE_EMESH;
-  if (!xy || !tri || n_nodes <= 0 || n_tris < 0) return SWE_EINVAL;
-  swe_params p;
-  swe_params_default(&p);
-  if (params) p = *params;
-  if (p.precision != SWE_F64 && p.precision != SWE_F32) return SWE_EINVAL;
-  if (p.order != SWE_ORDER_NONE && p.order != SWE_ORDER_MORTON) return SWE_EINVAL;
-  if (p.kernel < SWE_KERNEL_AUTO || p.kernel > SWE_KERNEL_TILED) return SWE_EINVAL;
-  if (p.tile == 0) p.tile = kDefaultTile;
-  if (p.cells_per_thread == 0) p.cells_per_thread = 2;
-  if (p.cells_per_thread != 1 && p.cells_per_thread != 2) return SWE_EINVAL;
-  {
-    const int nt = p.tile / p.cells_per_thread;
-    if (p.tile % p.cells_per_thread != 0 || (nt != 64 && nt != 128 && nt != 256)) return SWE_EINVAL;
-  }
-  if (p.stages == 0) p.stages = 2;
-  if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
-  if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
-  const int kernel = (p.kernel == SWE_KERNEL_EDGE) ? SWE_KERNEL_EDGE : SWE_KERNEL_TILED;
+  return create_batch(1, &xy, &n_nodes, &tri, &n_tris, params, cuda_stream, out);
+}
 
-  // Host-side construction and validation first: no device is touched for
-  // an invalid mesh.
-  swe::HostMesh hm;
-  int rc = swe::build_host_mesh(xy, n_nodes, tri, n_tris, p.order,
-                                kernel == SWE_KERNEL_TILED ? p.tile : 0,
-                                kernel == SWE_KERNEL_EDGE, hm);
-  if (rc == -2) return SWE_EMESH;
-  if (rc != 0) return SWE_EINVAL;
-
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  int sms = 0;
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-
-  swe_mesh* m = new swe_mesh();
-  m->prm = p;
-  m->device = dev;
-  m->sms = sms;
-  m->V = hm.V; m->T = hm.T; m->E = hm.E; m->Eb = hm.Eb;
-  m->kernel = kernel;
-  m->tile = p.tile;
-  m->stages = p.stages;
-  m->cpt = p.cells_per_thread;
-  m->ntiles = hm.ntiles;
-  m->records = (int64_t)hm.tA.size();
-  const int geo_arrays = (p.precision == SWE_F64) ? 3 : 2;
-  m->halos = (int64_t)hm.hidx.size();
-  if (cuda_stream) {
-    m->stream = (cudaStream_t)cuda_stream;
-  } else {
-    if (cuda_failed(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking))) {
-      delete m;
-      return SWE_ECUDA;
-    }
-    m->own_stream = true;
-  }
-  const size_t w = real_size(m);
-  const int64_t T = m->T, E = m->E, R = m->records;
-  m->Tp = (kernel == SWE_KERNEL_TILED) ? m->ntiles * m->tile : T;
-  const int64_t Tp = m->Tp;
-  Layout L;
-  L.add(4 * T);   // perm
-  L.add(w * Tp);  // area
-  L.add(w * Tp);  // irP
-  if (kernel == SWE_KERNEL_EDGE) {
-    L.add(4 * E); L.add(4 * E);
-    L.add(w * E); L.add(w * E); L.add(w * E);
-    L.add(4 * T); L.add(4 * T); L.add(4 * T);
-  } else {
-    L.add(8 * (m->ntiles + 1)); L.add(8 * (m->ntiles + 1));
-    L.add(4 * R);
-    for (int g = 0; g < geo_arrays; ++g) L.add(w * R);
-    L.add(4 * m->halos);
-    m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)geo_arrays, (uint32_t)m->tile,
-                                      (uint32_t)m->stages, (uint32_t)hm.rec_cap,
-                                      (uint32_t)hm.halo_cap);
-  }
-  if (cudaMalloc((void**)&m->arena.base, L.total) != cudaSuccess) {
-    cudaGetLastError();
-    swe_mesh_destroy(m);
-    return SWE_ENOMEM;
-  }
-  m->arena.size = L.total;
-  if (cuda_failed(cudaMemsetAsync(m->arena.base, 0, L.total, m->stream))) {
-    swe_mesh_destroy(m);
-    return SWE_ECUDA;
-  }
-  m->perm = (int32_t*)m->arena.take(4 * T);
-  m->area = m->arena.take(w * Tp);
-  m->irP = m->arena.take(w * Tp);
-  std::vector<double> irp(T);
-  for (int64_t j = 0; j < T; ++j) irp[j] = hm.perim[j] / hm.area[j];
-  swe_status st = SWE_OK;
-  auto chk = [&](swe_status s) { if (st == SWE_OK) st = s; };
-  auto carved = [&]() { if (m->arena.overflow && st == SWE_OK) { g_cuda_msg = "mesh arena layout"; st = SWE_ECUDA; } return st == SWE_OK; };
-  if (!carved()) { swe_mesh_destroy(m); return st; }
-  chk(upload(m, hm.perm, m->perm));
-  chk(upload_real(m, hm.area, m->area));
-  chk(upload_real(m, irp, m->irP));
-  if (kernel == SWE_KERNEL_EDGE) {
-    m->eL = (int32_t*)m->arena.take(4 * E);
-    m->eR = (int32_t*)m->arena.take(4 * E);
-    m->nx = m->arena.take(w * E);
-    m->ny = m->arena.take(w * E);
-    m->len = m->arena.take(w * E);
-    for (int k = 0; k < 3; ++k) m->cf[k] = (int32_t*)m->arena.take(4 * T);
-    if (!carved()) { swe_mesh_destroy(m); return st; }
-    chk(upload(m, hm.eL, m->eL));
-    chk(upload(m, hm.eR, m->eR));
-    chk(upload_real(m, hm.nx, m->nx));
-    chk(upload_real(m, hm.ny, m->ny));
-    chk(upload_real(m, hm.len, m->len));
-    for (int k = 0; k < 3; ++k) chk(upload(m, hm.cface[k], m->cf[k]));
-  } else {
-    m->toff = (int64_t*)m->arena.take(8 * (m->ntiles + 1));
-    m->hoff = (int64_t*)m->arena.take(8 * (m->ntiles + 1));
-    m->tS = (int32_t*)m->arena.take(4 * R);
-    m->tg0 = m->arena.take(w * R);
-    m->tg1 = m->arena.take(w * R);
-    if (geo_arrays > 2) m->tg2 = m->arena.take(w * R);
-    m->hidx = (int32_t*)m->arena.take(4 * m->halos);
-    if (!carved()) { swe_mesh_destroy(m); return st; }
-    chk(upload(m, hm.toff, m->toff));
-    chk(upload(m, hm.hoff, m->hoff));
-    chk(upload(m, hm.hidx, m->hidx));
-    // Sides as int16 codes packed in one word (A high, B low).
-    std::vector<int32_t> packed(R);
-    auto code = [](int32_t v) { return v == swe::kWall ? (int32_t)swe::kSideWall : v; };
-    bool fits = true;
-    for (int64_t r = 0; r < R; ++r) {
-      const int32_t a = code(hm.tA[r]), b = code(hm.tB[r]);
-      fits = fits && a >= -32768 && a <= 32767 && b >= -32768 && b <= 32767;
-      packed[r] = (int32_t)(((uint32_t)(uint16_t)a << 16) | (uint32_t)(uint16_t)b);
-    }
-    if (!fits) chk(SWE_EINVAL);
-    chk(upload(m, packed, m->tS));
-    if (geo_arrays > 2) {
-      chk(upload_real(m, hm.tnx, m->tg0));
-      chk(upload_real(m, hm.tny, m->tg1));
-      chk(upload_real(m, hm.tlen, m->tg2));
-    } else {  // scaled normal l n
-      std::vector<double> gx(R), gy(R);
-      for (int64_t r = 0; r < R; ++r) {
-        gx[r] = hm.tlen[r] * hm.tnx[r];
-        gy[r] = hm.tlen[r] * hm.tny[r];
-      }
-      chk(upload_real(m, gx, m->tg0));
-      chk(upload_real(m, gy, m->tg1));
-    }
-    chk(cuda_failed(cudaStreamSynchronize(m->stream)) ? SWE_ECUDA : SWE_OK);  // host vectors end here
-  }
-  if (st == SWE_OK && cuda_failed(cudaStreamSynchronize(m->stream))) st = SWE_ECUDA;
-  if (st != SWE_OK) {
-    swe_mesh_destroy(m);
-    return st;
-  }
-  if (p.precision == SWE_F64) set_grids<double>(m);
-  else set_grids<float>(m);
-  if (m->kernel == SWE_KERNEL_TILED && m->grid_tiled < 1) {
-    g_cuda_msg = "tiled kernel layout does not fit in shared memory";
-    swe_mesh_destroy(m);
-    return SWE_ECUDA;
-  }
-  *out = m;
-  return SWE_OK;
+swe_status swe_mesh_create_batch(int32_t n_scenarios, const double* const* xy,
+                                 const int64_t* n_nodes, const int32_t* const* tri,
+                                 const int64_t* n_tris, const swe_params* params,
+                                 void* cuda_stream, swe_mesh** out) {
+  return create_batch(n_scenarios, xy, n_nodes, tri, n_tris, params, cuda_stream, out);
 }
 
 swe_status swe_mesh_counts(const swe_mesh* m, int64_t* counts) {
   if (!m || !counts) return SWE_EINVAL;
   counts[0] = m->V; counts[1] = m->T; counts[2] = m->E; counts[3] = m->Eb;
+  return SWE_OK;
+}
+
+swe_status swe_mesh_scenarios(const swe_mesh* m, int32_t* n_scenarios, int64_t* n_tris) {
+  if (!m || !n_scenarios) return SWE_EINVAL;
+  *n_scenarios = nscen(m);
+  if (n_tris)
+    for (int i = 0; i < nscen(m); ++i) n_tris[i] = m->scen[i].ncells;
   return SWE_OK;
 }
 
@@ -623,6 +845,7 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
   if (!manning && !(manning_const >= 0.0)) return SWE_EINVAL;
   const size_t w = real_size(m);
   const int64_t T = m->T, E = m->E, Tp = m->Tp;
+  const int n = nscen(m);
   swe_state* s = new swe_state();
   s->mesh = m;
   const bool interleaved = (m->kernel == SWE_KERNEL_TILED);
@@ -636,8 +859,8 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
   L.add(w * Tp);                                // gn2
   if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) L.add(w * E);
   L.add(8 * (size_t)m->max_grid);
-  L.add(8 * T);                              // staging
-  L.add(sizeof(swe::Ctl));
+  L.add(8 * T);                                 // staging
+  L.add(sizeof(swe::Ctl) * n);
   if (cudaMalloc((void**)&s->arena.base, L.total) != cudaSuccess) {
     cudaGetLastError();
     delete s;
@@ -669,14 +892,14 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
   if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) s->fx[k] = s->arena.take(w * E);
   s->partial = (double*)s->arena.take(8 * (size_t)m->max_grid);
   s->stage = (double*)s->arena.take(8 * T);
-  s->ctl = (swe::Ctl*)s->arena.take(sizeof(swe::Ctl));
+  s->ctl = (swe::Ctl*)s->arena.take(sizeof(swe::Ctl) * n);
   swe_status st = SWE_OK;
   if (s->arena.overflow) {
     g_cuda_msg = "state arena layout";
     swe_state_destroy(s);
     return SWE_ECUDA;
   }
-  if (cudaMallocHost((void**)&s->host_ctl, sizeof(swe::Ctl)) != cudaSuccess ||
+  if (cudaMallocHost((void**)&s->host_ctl, sizeof(swe::Ctl) * n) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     swe_state_destroy(s);
@@ -685,8 +908,8 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
   // Bed and friction coefficient g n^2 (FP64 on the host, caller order).
   std::vector<double> gn2(T);
   for (int64_t i = 0; i < T; ++i) {
-    const double n = manning ? manning[i] : manning_const;
-    gn2[i] = m->prm.g * (n * n);
+    const double nn = manning ? manning[i] : manning_const;
+    gn2[i] = m->prm.g * (nn * nn);
   }
   const double* fields[2] = {z, gn2.data()};
   void* dsts[2] = {s->z, s->gn2};
@@ -727,8 +950,8 @@ swe_status swe_step(swe_state* s, double* dt_used) {
   CK(cudaGetLastError());
   st = read_ctl(s);
   if (st != SWE_OK) return st;
-  if (dt_used) *dt_used = s->host_ctl->dt_last;
-  return status_from_ctl(*s->host_ctl);
+  if (dt_used) *dt_used = s->host_ctl[0].dt_last;
+  return status_all(s);
 }
 
 swe_status swe_run(swe_state* s, int64_t n_steps) {
@@ -741,66 +964,104 @@ swe_status swe_advance(swe_state* s, double t_end, int64_t* n_steps) {
   if (!s || !(t_end == t_end)) return SWE_EINVAL;
   swe_status st = read_ctl(s);
   if (st != SWE_OK) return st;
-  const long long start = s->host_ctl->steps;
-  swe::k_set_end<<<1, 1, 0, s->mesh->stream>>>(s->ctl, t_end);
+  const long long start = s->host_ctl[0].steps;
+  set_end(s, t_end);
   s->open_ended = false;
   CK(cudaGetLastError());
   for (;;) {
     st = read_ctl(s);
     if (st != SWE_OK) return st;
-    if (s->host_ctl->done) break;
+    if (all_done(s)) break;
     st = queue_steps(s, kStepsPerGraph);
     if (st != SWE_OK) return st;
   }
-  if (n_steps) *n_steps = s->host_ctl->steps - start;
-  return status_from_ctl(*s->host_ctl);
+  if (n_steps) *n_steps = s->host_ctl[0].steps - start;
+  return status_all(s);
 }
 
 swe_status swe_sync(swe_state* s) {
   if (!s) return SWE_EINVAL;
   swe_status st = read_ctl(s);
   if (st != SWE_OK) return st;
-  return status_from_ctl(*s->host_ctl);
+  return status_all(s);
 }
 
 swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, double* t,
                         double* mass) {
   if (!s) return SWE_EINVAL;
   const swe_mesh* m = s->mesh;
-  if (mass) swe::k_mass_sum<<<1, 256, 0, m->stream>>>(s->ctl, s->partial);
+  const int n = nscen(m);
+  if (mass) swe::k_mass_sum<<<n, 256, 0, m->stream>>>(s->ctl, s->partial);
   swe_status st = read_ctl(s);
   if (st != SWE_OK) return st;
-  const int cur = s->host_ctl->cur;
+  bool same = true;
+  for (int i = 1; i < n; ++i) same = same && s->host_ctl[i].cur == s->host_ctl[0].cur;
   double* dst[3] = {h, hu, hv};
-  const void* src[3] = {s->h[cur], s->hu[cur], s->hv[cur]};
   for (int k = 0; k < 3; ++k) {
     if (!dst[k]) continue;
-    if (m->prm.precision == SWE_F64) launch_scatter<double>(m, src[k], s->stage, s->stride);
-    else launch_scatter<float>(m, src[k], s->stage, s->stride);
-    CK(cudaMemcpyAsync(dst[k], s->stage, m->T * 8, cudaMemcpyDeviceToHost, m->stream));
+    if (same) {
+      scatter_field(s, k, s->host_ctl[0].cur);
+      CK(cudaMemcpyAsync(dst[k], s->stage, m->T * 8, cudaMemcpyDeviceToHost, m->stream));
+    } else {
+      // Scenarios that stopped at different step counts sit in different
+      // buffers: copy each one's range from the buffer it is in.
+      for (int b = 0; b < 2; ++b) {
+        scatter_field(s, k, b);
+        for (int i = 0; i < n; ++i) {
+          if (s->host_ctl[i].cur != b) continue;
+          const Scenario& sc = m->scen[i];
+          CK(cudaMemcpyAsync(dst[k] + sc.caller0, s->stage + sc.caller0, sc.ncells * 8,
+                             cudaMemcpyDeviceToHost, m->stream));
+        }
+      }
+    }
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(m->stream));
   }
-  if (t) *t = s->host_ctl->t;
-  if (mass) *mass = s->host_ctl->mass;
-  return status_from_ctl(*s->host_ctl);
+  if (t) *t = s->host_ctl[0].t;
+  if (mass) {
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) sum += s->host_ctl[i].mass;
+    *mass = sum;
+  }
+  return status_all(s);
 }
 
 swe_status swe_state_info(const swe_state* s, int64_t* info) {
   if (!s || !info) return SWE_EINVAL;
   swe_status st = read_ctl(s);
   if (st != SWE_OK) return st;
-  info[0] = s->host_ctl->steps;
-  info[1] = s->host_ctl->neg;
-  info[2] = s->host_ctl->err;
+  info[0] = s->host_ctl[0].steps;
+  info[1] = 0;
+  info[2] = 0;
+  for (int i = 0; i < nscen(s->mesh); ++i) {
+    info[1] += s->host_ctl[i].neg;
+    info[2] |= s->host_ctl[i].err;
+  }
   return SWE_OK;
+}
+
+swe_status swe_scenario_info(const swe_state* s, int32_t scenario, double* t, double* mass,
+                             int64_t* steps, double* dt_next) {
+  if (!s || scenario < 0 || scenario >= nscen(s->mesh)) return SWE_EINVAL;
+  const swe_mesh* m = s->mesh;
+  if (mass) swe::k_mass_sum<<<nscen(m), 256, 0, m->stream>>>(s->ctl, s->partial);
+  swe_status st = read_ctl(s);
+  if (st != SWE_OK) return st;
+  const swe::Ctl& c = s->host_ctl[scenario];
+  if (t) *t = c.t;
+  if (mass) *mass = c.mass;
+  if (steps) *steps = c.steps;
+  if (dt_next) *dt_next = c.dt_cfl;
+  return status_from_err(c.err);
 }
 
 swe_status swe_next_dt(const swe_state* s, double* dt) {
   if (!s || !dt) return SWE_EINVAL;
   swe_status st = read_ctl(s);
   if (st != SWE_OK) return st;
-  *dt = s->host_ctl->dt_cfl;
-  return status_from_ctl(*s->host_ctl);
+  *dt = s->host_ctl[0].dt_cfl;
+  return status_all(s);
 }
 
 void swe_state_destroy(swe_state* s) {

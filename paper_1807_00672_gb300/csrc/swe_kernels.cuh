@@ -35,6 +35,7 @@ struct Ctl {
   double dt_cfl;     // unclamped CFL dt of the current state
   double mass;       // sum of area * h of the current state (FP64)
   double dt_last;    // dt of the last step taken
+  long long part0;   // first mass partial sum of this scenario
   long long nparts;  // mass partial sums written by the last launch (one per block)
   unsigned long long rate_bits;  // running max of the CFL rate (bits of a double >= 0)
   long long steps;   // steps taken
@@ -43,9 +44,11 @@ struct Ctl {
   int done;          // no more steps: t reached t_end or an error latched
   int clamped;       // dt == t_end - t
   int err;           // latched error bits
-  unsigned int ticket;  // blocks finished in the current launch
+  unsigned int ticket;  // blocks of this scenario finished in the current launch
   int pad_;
 };
+// A mesh holds one or more independent scenarios (an ensemble); each has its
+// own control word, and a launch's blocks each work for one scenario.
 
 constexpr int kErrNan = 1;
 constexpr int kErrDry = 2;
@@ -84,7 +87,17 @@ struct DevMesh {
   const int32_t* cf0;
   const int32_t* cf1;
   const int32_t* cf2;
-  // tiled layout
+  // tiled layout; work chunks: chunk b walks the chunk_ntiles[b] tiles
+  // chunk_tile0[b] + k chunk_stride[b] (k = 0, 1, ...) of scenario
+  // chunk_scen[b]; the cells of scenario s end at scen_cell_end[s]. The
+  // chunks of one scenario interleave (stride = their count), so the
+  // blocks resident at any moment sweep neighbouring tiles together and a
+  // tile's halo cells are mostly still in L2 from the neighbours' copies.
+  const int32_t* chunk_scen;
+  const int32_t* chunk_tile0;
+  const int32_t* chunk_ntiles;
+  const int32_t* chunk_stride;
+  const int32_t* scen_cell_end;
   int64_t ntiles;
   const int64_t* toff;
   const int64_t* hoff;
@@ -440,11 +453,14 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // Every thread of the block calls this once at the end of an update launch.
-// stepped: the launch advanced the state by ctl->dt (false: CFL/mass only).
-// err: kErr* bits seen by this thread.
+// The block is one of `nblocks` working for the scenario of `ctl`; its mass
+// partial sum goes to partial[part], the scenario's partials being
+// partial[part0 .. part0 + nblocks). stepped: the launch advanced the state
+// by ctl->dt (false: CFL/mass only). err: kErr* bits seen by this thread.
 template <int NT>
-__device__ void finish_launch(Ctl* ctl, double* partial, double mass, double rate, int err_bits,
-                              int neg, bool stepped, double courant) {
+__device__ void finish_launch(Ctl* ctl, double* partial, long long part, long long part0,
+                              int nblocks, double mass, double rate, int err_bits, int neg,
+                              bool stepped, double courant) {
   __shared__ double s_mass[NT / 32];
   __shared__ double s_rate[NT / 32];
   __shared__ int s_bad[NT / 32];
@@ -468,10 +484,10 @@ __device__ void finish_launch(Ctl* ctl, double* partial, double mass, double rat
     atomicMax(&ctl->rate_bits, (unsigned long long)__double_as_longlong(r));
     if (b) atomicOr(&ctl->err, b);
     if (n) atomicAdd((unsigned long long*)&ctl->neg, (unsigned long long)n);
-    partial[blockIdx.x] = m;
+    partial[part] = m;
     __threadfence();
     const unsigned int ticket = atomicAdd(&ctl->ticket, 1u);
-    s_last = (ticket == gridDim.x - 1);
+    s_last = (ticket == (unsigned int)nblocks - 1u);
   }
   __syncthreads();
   if (!s_last) return;
@@ -479,7 +495,8 @@ __device__ void finish_launch(Ctl* ctl, double* partial, double mass, double rat
   // Last block: the step's control update. The mass partial sums stay in
   // `partial` and are added up by k_mass_sum when the host asks for them.
   if (threadIdx.x == 0) {
-    ctl->nparts = gridDim.x;
+    ctl->part0 = part0;
+    ctl->nparts = nblocks;
     const unsigned long long bits = atomicExch(&ctl->rate_bits, 0ull);
     ctl->ticket = 0u;
     double t = ctl->t;
@@ -592,8 +609,8 @@ __global__ void __launch_bounds__(256) k_cell_update(DevMesh<Real> m, DevState<R
     hu1[i] = b1;
     hv1[i] = c1;
   }
-  finish_launch<256>(ctl, s.partial, mass.value(), (double)rate, bad ? kErrNan : 0, neg, true,
-                     num.courant);
+  finish_launch<256>(ctl, s.partial, blockIdx.x, 0, gridDim.x, mass.value(), (double)rate,
+                     bad ? kErrNan : 0, neg, true, num.courant);
 }
 
 // ---------------------------------------------------------------------------
@@ -730,16 +747,19 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   Real* slots = reinterpret_cast<Real*>(smem + L.off_slots);  // [3 TC][4], face k of cell j at k TC + j
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bars);
 
-  Ctl* ctl = s.ctl;
+  // This block's work: tiles t_first + k t_step (k < n_tiles) of one scenario.
+  const int scen = m.chunk_scen[blockIdx.x];
+  const int t_first = m.chunk_tile0[blockIdx.x];
+  const int n_tiles = m.chunk_ntiles[blockIdx.x];
+  const int t_step = m.chunk_stride[blockIdx.x];
+  const int cell_end = m.scen_cell_end[scen];
+  Ctl* ctl = s.ctl + scen;
   if (ctl->done) return;
   const int cur = ctl->cur;
   const Real dt = Real(ctl->dt);
   const Real* __restrict__ U = cur ? s.h[1] : s.h[0];  // interleaved cells (h, hu, hv, z)
   Real* __restrict__ U1 = cur ? s.h[0] : s.h[1];
   const int tid = threadIdx.x;
-  const int ntiles = (int)m.ntiles;
-  const int G = (int)gridDim.x;
-  const Real g = Real(num.g);
 
   if (tid == 0) {
 #pragma unroll
@@ -798,13 +818,12 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   MassAcc<Real> mass;
   Real rate = Real(0);
   int bad = 0, neg = 0, timeout = 0;
-  int tile = blockIdx.x;
   if (tid == 0) {
 #pragma unroll
     for (int i = 0; i < NS - 1; ++i)
-      if (tile + i * G < ntiles) issue(i, tile + i * G);
+      if (i < n_tiles) issue(i, t_first + i * t_step);
   }
-  if (tile < ntiles) {
+  if (n_tiles > 0) {
     const bool ok = (tid == 0) ? wait_stage(0) : true;
     if (__syncthreads_or(!ok)) {
       timeout = 1;
@@ -816,12 +835,13 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   }
   // Each iteration: the face records of tile k, then the cell updates of
   // tile k while tile k+1's halo gather is in flight. Two block barriers.
-  for (int k = 0; !timeout && tile < ntiles; tile += G, ++k) {
+  for (int k = 0; !timeout && k < n_tiles; ++k) {
     const int st = k % NS;
-    const int t_next = tile + G;
+    const int tile = t_first + k * t_step;
+    const bool has_next = k + 1 < n_tiles;
     // The stage that receives tile k+NS-1 was released by the barrier that
     // ended iteration k-1.
-    if (tid == 0 && tile + (NS - 1) * G < ntiles) issue((k + NS - 1) % NS, tile + (NS - 1) * G);
+    if (tid == 0 && k + NS - 1 < n_tiles) issue((k + NS - 1) % NS, tile + (NS - 1) * t_step);
     const unsigned char* p = smem + st * L.stage;
     const Real* xc = reinterpret_cast<const Real*>(p + L.off_cells);  // [ext][4]
     const int32_t* rS = reinterpret_cast<const int32_t*>(p + L.off_tS);
@@ -829,7 +849,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     const Real* rg1 = reinterpret_cast<const Real*>(p + L.off_g1);
     const Real* rg2 = reinterpret_cast<const Real*>(p + L.off_g2);
     const int base = tile * TC;
-    const int nc = min(TC, (int)m.T - base);
+    const int nc = min(TC, cell_end - base);
     const int nrec = s_nrec[st];
     // this thread's cells' area, perimeter/area and g n^2 (cell arrays are
     // padded to whole tiles, so the loads are always in bounds)
@@ -864,12 +884,12 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       if (b < 0 && !wall) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, Real(0));
     }
     // The next tile's copies must have landed before its halo is gathered.
-    const bool ok = (tid == 0 && t_next < ntiles) ? wait_stage((k + 1) % NS) : true;
+    const bool ok = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
     if (__syncthreads_or(!ok)) {
       timeout = 1;
       break;
     }
-    if (t_next < ntiles) gather_halo((k + 1) % NS);
+    if (has_next) gather_halo((k + 1) % NS);
 
     // cell updates of tile k
 #pragma unroll
@@ -909,11 +929,13 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     for (int i = 0; i < NS; ++i)
       if ((pending >> i) & 1u) mbar_wait(&bar[i], (parity_bits >> i) & 1u);
   }
-  finish_launch<NT>(ctl, s.partial, mass.value(), (double)rate,
-                    (bad ? kErrNan : 0) | (timeout ? kErrTimeout : 0), neg, true, num.courant);
+  finish_launch<NT>(ctl, s.partial, blockIdx.x, ctl->part0, (int)ctl->nparts, mass.value(),
+                    (double)rate, (bad ? kErrNan : 0) | (timeout ? kErrTimeout : 0), neg, true,
+                    num.courant);
 }
 
-// CFL rate and mass of the current state, no step (initialisation).
+// CFL rate and mass of the current state, no step (initialisation), one
+// scenario in separate arrays (two-launch layout).
 template <typename Real>
 __global__ void __launch_bounds__(256) k_cfl(DevMesh<Real> m, DevState<Real> s, Num num) {
   using O = Ops<Real>;
@@ -936,17 +958,50 @@ __global__ void __launch_bounds__(256) k_cfl(DevMesh<Real> m, DevState<Real> s, 
     if (!isfinite(hh + qx + qy)) bad = 1;
     mass.add(m.area[i], hh);
   }
-  finish_launch<256>(ctl, s.partial, mass.value(), (double)rate, bad ? kErrNan : 0, 0, false,
-                     num.courant);
+  finish_launch<256>(ctl, s.partial, blockIdx.x, 0, gridDim.x, mass.value(), (double)rate,
+                     bad ? kErrNan : 0, 0, false, num.courant);
 }
 
-// Mass integral of the latest launch: the sum of its per-block partial sums,
-// in a fixed order (one block of 256 threads).
-static __global__ void __launch_bounds__(256) k_mass_sum(Ctl* ctl, const double* __restrict__ partial) {
+// The same on interleaved cells, over the tiled layout's work chunks (every
+// scenario of the mesh). TC: cells per tile.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_cfl_tiled(DevMesh<Real> m, DevState<Real> s, Num num,
+                                                   int TC) {
+  using O = Ops<Real>;
+  const int scen = m.chunk_scen[blockIdx.x];
+  Ctl* ctl = s.ctl + scen;
+  const int cur = ctl->cur;
+  const Real* __restrict__ U = cur ? s.h[1] : s.h[0];
+  const int64_t cell_end = m.scen_cell_end[scen];
+  const int n_tiles = m.chunk_ntiles[blockIdx.x];
+  MassAcc<Real> mass;
+  Real rate = Real(0);
+  int bad = 0;
+  for (int k = 0; k < n_tiles; ++k) {
+    const int64_t c0 = (int64_t)(m.chunk_tile0[blockIdx.x] + k * m.chunk_stride[blockIdx.x]) * TC;
+    const int64_t c1 = min(c0 + (int64_t)TC, cell_end);
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+      const Real hh = U[4 * i], qx = U[4 * i + 1], qy = U[4 * i + 2];
+      if (O::wet(hh, num)) {
+        const Real lam = O::div(O::sqrt_(qx * qx + qy * qy), hh) + O::sqrt_(Real(num.g) * hh);
+        rate = fmax(rate, lam * m.irP[i]);
+      }
+      if (!isfinite(hh + qx + qy)) bad = 1;
+      mass.add(m.area[i], hh);
+    }
+  }
+  finish_launch<256>(ctl, s.partial, blockIdx.x, ctl->part0, (int)ctl->nparts, mass.value(),
+                     (double)rate, bad ? kErrNan : 0, 0, false, num.courant);
+}
+
+// Mass integral of each scenario's latest launch: the sum of its per-block
+// partial sums, in a fixed order (block s of 256 threads for scenario s).
+static __global__ void __launch_bounds__(256) k_mass_sum(Ctl* ctls, const double* __restrict__ partial) {
   __shared__ double sh[256];
-  const long long n = ctl->nparts;
+  Ctl* ctl = ctls + blockIdx.x;
+  const long long n = ctl->nparts, p0 = ctl->part0;
   double acc = 0.0;
-  for (long long j = threadIdx.x; j < n; j += 256) acc += partial[j];
+  for (long long j = threadIdx.x; j < n; j += 256) acc += partial[p0 + j];
   sh[threadIdx.x] = acc;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
@@ -956,13 +1011,16 @@ static __global__ void __launch_bounds__(256) k_mass_sum(Ctl* ctl, const double*
   if (threadIdx.x == 0) ctl->mass = sh[0];
 }
 
-// Caller order (double) -> internal order (Real): dst[j * stride] = src[perm[j]].
+// Caller order (double) -> internal order (Real): dst[j * stride] = src[perm[j]]
+// for every internal cell j < n (perm[j] < 0 marks tile padding: skipped).
 template <typename Real>
 __global__ void k_gather(const double* __restrict__ src, const int32_t* __restrict__ perm,
                          Real* __restrict__ dst, int64_t n, int stride) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x)
-    dst[j * stride] = Real(src[perm[j]]);
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = perm[j];
+    if (c >= 0) dst[j * stride] = Real(src[c]);
+  }
 }
 
 // Internal order (Real) -> caller order (double): dst[perm[j]] = src[j * stride].
@@ -970,8 +1028,10 @@ template <typename Real>
 __global__ void k_scatter(const Real* __restrict__ src, const int32_t* __restrict__ perm,
                           double* __restrict__ dst, int64_t n, int stride) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x)
-    dst[perm[j]] = double(src[j * stride]);
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = perm[j];
+    if (c >= 0) dst[c] = double(src[j * stride]);
+  }
 }
 
 }  // namespace swe

@@ -30,10 +30,11 @@ KERNEL = {"auto": 0, "edge": 1, "tiled": 2}
 
 # Every symbol include/swe.h declares.
 EXPORTS = (
-    "swe_params_default", "swe_mesh_create", "swe_mesh_counts", "swe_mesh_device_bytes",
-    "swe_mesh_destroy", "swe_state_init", "swe_state_set", "swe_step", "swe_run",
-    "swe_advance", "swe_sync", "swe_copy_out", "swe_state_info", "swe_next_dt",
-    "swe_state_destroy", "swe_strerror", "swe_last_cuda_error", "swe_step_edges_static",
+    "swe_params_default", "swe_mesh_create", "swe_mesh_create_batch", "swe_mesh_counts",
+    "swe_mesh_scenarios", "swe_mesh_device_bytes", "swe_mesh_destroy", "swe_state_init",
+    "swe_state_set", "swe_step", "swe_run", "swe_advance", "swe_sync", "swe_copy_out",
+    "swe_state_info", "swe_next_dt", "swe_scenario_info", "swe_state_destroy", "swe_strerror",
+    "swe_last_cuda_error", "swe_step_edges_static",
 )
 
 
@@ -77,7 +78,9 @@ def lib():
     sig = {
         "swe_params_default": (None, [P]),
         "swe_mesh_create": (st, [vp, i64, vp, i64, P, vp, pp]),
+        "swe_mesh_create_batch": (st, [ctypes.c_int32, vp, vp, vp, vp, P, vp, pp]),
         "swe_mesh_counts": (st, [vp, vp]),
+        "swe_mesh_scenarios": (st, [vp, vp, vp]),
         "swe_mesh_device_bytes": (st, [vp, vp]),
         "swe_mesh_destroy": (None, [vp]),
         "swe_state_init": (st, [vp, vp, vp, vp, vp, vp, dbl, pp]),
@@ -89,6 +92,7 @@ def lib():
         "swe_copy_out": (st, [vp, vp, vp, vp, vp, vp]),
         "swe_state_info": (st, [vp, vp]),
         "swe_next_dt": (st, [vp, vp]),
+        "swe_scenario_info": (st, [vp, ctypes.c_int32, vp, vp, vp, vp]),
         "swe_state_destroy": (None, [vp]),
         "swe_strerror": (ctypes.c_char_p, [st]),
         "swe_last_cuda_error": (ctypes.c_char_p, []),
@@ -131,23 +135,60 @@ def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, coura
 
 
 class Mesh:
-    """Device-resident mesh (swe_mesh_create)."""
+    """Device-resident mesh (swe_mesh_create), or an ensemble of independent
+    scenario meshes (``Mesh.ensemble``, swe_mesh_create_batch)."""
 
     def __init__(self, xy, tri, *, precision="f64", order="morton", kernel="auto", tile=0,
                  stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6):
-        xy = _f64(xy).reshape(-1, 2)
-        tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
-        self.prm = params(precision, order, kernel, tile, g, courant, h_eps, stages,
-                          cells_per_thread)
+        self._build([(xy, tri)], precision, order, kernel, tile, stages, cells_per_thread,
+                    stream, g, courant, h_eps, batch=False)
+
+    @classmethod
+    def ensemble(cls, meshes, *, precision="f64", order="morton", kernel="auto", tile=0,
+                 stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6):
+        """One mesh holding the scenarios ``meshes`` = [(xy, tri), ...]; cell
+        arrays are the scenarios' cells concatenated in this order."""
+        self = cls.__new__(cls)
+        self._build(list(meshes), precision, order, kernel, tile, stages, cells_per_thread,
+                    stream, g, courant, h_eps, batch=True)
+        return self
+
+    def _build(self, meshes, precision, order, kernel, tile, stages, cpt, stream, g, courant,
+               h_eps, batch):
+        xys = [_f64(xy).reshape(-1, 2) for xy, _ in meshes]
+        tris = [np.ascontiguousarray(t, dtype=np.int32).reshape(-1, 3) for _, t in meshes]
+        self.prm = params(precision, order, kernel, tile, g, courant, h_eps, stages, cpt)
         self.precision = precision
         h = ctypes.c_void_p()
-        s = lib().swe_mesh_create(_p(xy), xy.shape[0], _p(tri), tri.shape[0],
-                                  ctypes.byref(self.prm), stream, ctypes.byref(h))
-        _check(s, "swe_mesh_create")
+        if batch:
+            n = len(meshes)
+            xp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in xys])
+            tp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in tris])
+            nn = np.array([a.shape[0] for a in xys], dtype=np.int64)
+            nt = np.array([a.shape[0] for a in tris], dtype=np.int64)
+            s = lib().swe_mesh_create_batch(n, xp, _p(nn), tp, _p(nt), ctypes.byref(self.prm),
+                                            stream, ctypes.byref(h))
+            _check(s, "swe_mesh_create_batch")
+        else:
+            xy, tri = xys[0], tris[0]
+            s = lib().swe_mesh_create(_p(xy), xy.shape[0], _p(tri), tri.shape[0],
+                                      ctypes.byref(self.prm), stream, ctypes.byref(h))
+            _check(s, "swe_mesh_create")
         self._h = h
         c = np.zeros(4, dtype=np.int64)
         lib().swe_mesh_counts(self._h, _p(c))
         self.V, self.T, self.E, self.Eb = (int(x) for x in c)
+        ns = ctypes.c_int32()
+        _check(lib().swe_mesh_scenarios(self._h, ctypes.byref(ns), None), "swe_mesh_scenarios")
+        counts = np.zeros(ns.value, dtype=np.int64)
+        _check(lib().swe_mesh_scenarios(self._h, ctypes.byref(ns), _p(counts)),
+               "swe_mesh_scenarios")
+        self.scenario_cells = [int(x) for x in counts]
+        self.scenario_offsets = [0] + list(np.cumsum(counts)[:-1].astype(int))
+
+    @property
+    def n_scenarios(self) -> int:
+        return len(self.scenario_cells)
 
     def device_bytes(self) -> int:
         b = ctypes.c_int64()
@@ -236,6 +277,14 @@ class State:
         dt = ctypes.c_double()
         _check(lib().swe_next_dt(self._h, ctypes.byref(dt)), "swe_next_dt")
         return dt.value
+
+    def scenario(self, i: int):
+        """(t, mass, steps, next dt) of scenario i of an ensemble."""
+        t, m, dt = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        k = ctypes.c_int64()
+        _check(lib().swe_scenario_info(self._h, int(i), ctypes.byref(t), ctypes.byref(m),
+                                       ctypes.byref(k), ctypes.byref(dt)), "swe_scenario_info")
+        return dict(t=t.value, mass=m.value, steps=k.value, dt=dt.value)
 
     def close(self):
         if getattr(self, "_h", None):

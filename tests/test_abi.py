@@ -101,3 +101,49 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(swe, "LIB_PATH", str(tmp_path / "libswe.so"))
     with pytest.raises(RuntimeError, match="missing"):
         swe.lib()
+
+
+def _create_batch(meshes, prm=None, n=None):
+    k = len(meshes)
+    xys = [np.ascontiguousarray(xy, dtype=np.float64) for xy, _ in meshes]
+    tris = [np.ascontiguousarray(t, dtype=np.int32) for _, t in meshes]
+    xp = (ctypes.c_void_p * max(k, 1))(*[a.ctypes.data for a in xys])
+    tp = (ctypes.c_void_p * max(k, 1))(*[a.ctypes.data for a in tris])
+    nn = np.array([a.shape[0] for a in xys] or [0], dtype=np.int64)
+    nt = np.array([a.shape[0] for a in tris] or [0], dtype=np.int64)
+    h = ctypes.c_void_p()
+    st = swe.lib().swe_mesh_create_batch(k if n is None else n, xp,
+                                         nn.ctypes.data_as(ctypes.c_void_p), tp,
+                                         nt.ctypes.data_as(ctypes.c_void_p),
+                                         None if prm is None else ctypes.byref(prm), None,
+                                         ctypes.byref(h))
+    return st, h
+
+
+def test_batch_rejects_bad_counts_and_an_invalid_scenario(L):
+    a = inputs.jittered_grid(3, 3, 3.0, 3.0)
+    b = inputs.jittered_grid(4, 2, 4.0, 2.0, seed=3)
+    st, _ = _create_batch([(a.xy, a.tri)], n=0)
+    assert st == swe.SWE_EINVAL
+    st, _ = _create_batch([(a.xy, a.tri)], n=-3)
+    assert st == swe.SWE_EINVAL
+    bad = b.tri.copy()
+    bad[0, 0] = b.n_nodes  # the second scenario has a node index out of range
+    st, _ = _create_batch([(a.xy, a.tri), (b.xy, bad)])
+    assert st == swe.SWE_EMESH
+    st, _ = _create_batch([(a.xy, a.tri), (b.xy, b.tri[:0])])
+    assert st == swe.SWE_EMESH
+    h = ctypes.c_void_p()
+    assert L.swe_mesh_create_batch(2, None, None, None, None, None, None, ctypes.byref(h)) == swe.SWE_EINVAL
+
+
+def test_batch_needs_the_tiled_kernel(L):
+    a = inputs.jittered_grid(3, 3, 3.0, 3.0)
+    st, _ = _create_batch([(a.xy, a.tri), (a.xy, a.tri)], swe.params(kernel="edge"))
+    assert st == swe.SWE_EINVAL
+
+
+def test_scenario_queries_reject_null_handles(L):
+    n = ctypes.c_int32()
+    assert L.swe_mesh_scenarios(None, ctypes.byref(n), None) == swe.SWE_EINVAL
+    assert L.swe_scenario_info(None, 0, None, None, None, None) == swe.SWE_EINVAL

@@ -1,0 +1,148 @@
+"""Ensembles (swe_mesh_create_batch): several independent scenarios in one
+mesh, advanced by the same launches.
+
+A scenario's result must not depend on the company it keeps: its cells go
+through the same per-cell arithmetic whether it runs alone or in a batch, so
+the fields must be bitwise identical to a run of that scenario on its own
+mesh, and its FP64 fields must match the oracle like any single mesh.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_00672_gb300 import inputs, swe
+
+from gpu_util import ensure_built, momentum_scale, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+
+def scenario_mix():
+    """Six scenarios: dam breaks of several sizes (ragged tails), wet/dry
+    random flows (one smaller than a tile) and bumps over a dry bed top."""
+    cases = inputs.ensemble_cases(3, t_min=300, t_max=9_000, seed=11)
+    cases.append(inputs.random_flow_case(nx=21, ny=13, seed=5))
+    cases.append(inputs.humps_case(nx=30, ny=20))
+    cases.append(inputs.random_flow_case(nx=7, ny=5, seed=6))
+    return cases
+
+
+def areas(case):
+    xy, tri = case.mesh.xy, case.mesh.tri
+    p0, p1, p2 = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    return 0.5 * np.abs((p1[:, 0] - p0[:, 0]) * (p2[:, 1] - p0[:, 1])
+                        - (p2[:, 0] - p0[:, 0]) * (p1[:, 1] - p0[:, 1]))
+
+
+def ensemble_state(cases, **kw):
+    ensure_built()
+    mesh = swe.Mesh.ensemble([(c.mesh.xy, c.mesh.tri) for c in cases], **kw)
+    cat = lambda name: np.concatenate([getattr(c, name) for c in cases])
+    st = swe.State(mesh, cat("h"), cat("hu"), cat("hv"), cat("z"), cat("n"))
+    return mesh, st
+
+
+def single_state(case, **kw):
+    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, **kw)
+    return mesh, swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+
+
+def split(mesh, a):
+    return [a[o:o + n] for o, n in zip(mesh.scenario_offsets, mesh.scenario_cells)]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_ensemble_equals_scenarios_run_alone_bitwise(precision):
+    cases = scenario_mix()
+    mesh, st = ensemble_state(cases, precision=precision)
+    assert mesh.n_scenarios == len(cases)
+    assert mesh.scenario_cells == [c.mesh.n_tris for c in cases]
+    assert mesh.T == sum(c.mesh.n_tris for c in cases)
+    st.run(37)  # two graph replays and five single launches
+    got = [split(mesh, f) for f in st.fields()]
+    for i, c in enumerate(cases):
+        m1, s1 = single_state(c, precision=precision)
+        s1.run(37)
+        ref = s1.fields()
+        for k in range(3):
+            assert np.array_equal(got[k][i], ref[k]), (i, k)
+        info = st.scenario(i)
+        assert info["steps"] == 37
+        assert info["t"] == s1.t
+        assert info["dt"] == s1.next_dt()
+        assert info["mass"] == pytest.approx(s1.mass, rel=1e-13)
+
+
+def test_ensemble_fp64_matches_oracle_per_scenario():
+    cases = scenario_mix()
+    mesh, st = ensemble_state(cases, precision="f64")
+    st.run(100)
+    h, hu, hv = (split(mesh, f) for f in st.fields())
+    for i, c in enumerate(cases):
+        ref = oracle.state_from_case(c)
+        ref.run(100)
+        qs = momentum_scale(ref.h, ref.hu, ref.hv)
+        assert rel_err(h[i], ref.h) <= TOL64, i
+        assert np.abs(hu[i] - ref.hu).max() / qs <= TOL64, i
+        assert np.abs(hv[i] - ref.hv).max() / qs <= TOL64, i
+        assert st.scenario(i)["t"] == pytest.approx(ref.t, rel=1e-13)
+
+
+def test_ensemble_advance_stops_every_scenario_at_the_end_time():
+    """Scenarios take different step counts to reach t_end, so they end in
+    different state buffers; each must stop exactly at t_end and equal its
+    own advance bitwise."""
+    cases = scenario_mix()
+    mesh, st = ensemble_state(cases, precision="f64")
+    t_end = 2.0  # the oracle takes 43, 26, 28, 32, 1 and 5 steps
+    st.advance(t_end)
+    steps = [st.scenario(i)["steps"] for i in range(len(cases))]
+    assert len(set(steps)) > 1 and len({s % 2 for s in steps}) == 2
+    got = [split(mesh, f) for f in st.fields()]
+    for i, c in enumerate(cases):
+        info = st.scenario(i)
+        assert info["t"] == t_end
+        m1, s1 = single_state(c, precision="f64")
+        n1 = s1.advance(t_end)
+        assert info["steps"] == n1
+        ref = s1.fields()
+        for k in range(3):
+            assert np.array_equal(got[k][i], ref[k]), (i, k)
+
+
+def test_ensemble_total_mass_is_the_sum_of_scenario_masses():
+    cases = scenario_mix()
+    mesh, st = ensemble_state(cases, precision="f64")
+    st.run(20)
+    parts = [st.scenario(i)["mass"] for i in range(len(cases))]
+    assert st.mass == pytest.approx(sum(parts), rel=1e-15)
+    exact = sum(float((areas(c) * c.h).sum()) for c in cases)
+    assert st.mass == pytest.approx(exact, rel=1e-12)
+
+
+def test_ensemble_of_one_equals_a_plain_mesh():
+    case = inputs.random_flow_case(nx=33, ny=17, seed=9)
+    mesh, st = ensemble_state([case], precision="f32")
+    m1, s1 = single_state(case, precision="f32")
+    st.run(25)
+    s1.run(25)
+    for a, b in zip(st.fields(), s1.fields()):
+        assert np.array_equal(a, b)
+
+
+def test_ensemble_reports_a_dry_scenario_at_init():
+    cases = scenario_mix()[:2]
+    dry = cases[1]
+    dry.h[:] = 0.0
+    with pytest.raises(swe.SweError) as e:
+        ensemble_state(cases, precision="f64")
+    assert e.value.status == swe.SWE_EDRY
+
+
+def test_scenario_index_is_checked():
+    mesh, st = ensemble_state(scenario_mix()[:2], precision="f64")
+    with pytest.raises(swe.SweError) as e:
+        st.scenario(2)
+    assert e.value.status == swe.SWE_EINVAL
