@@ -26,7 +26,8 @@
  *     Device-side conditions (NaN, all-dry) latch an error word that the next
  *     synchronising call reports.
  *   - Handles are owned by the caller and freed with the matching destroy.
- *     A state must be destroyed before its mesh. Handles are not thread-safe.
+ *     Destroying a mesh that states still use is allowed: the mesh is freed
+ *     when the last of them is destroyed. Handles are not thread-safe.
  */
 #ifndef SWE_H
 #define SWE_H
@@ -192,6 +193,55 @@ swe_status swe_scenario_info(const swe_state* state, int32_t scenario, double* t
                              int64_t* steps, double* dt_next);
 
 void swe_state_destroy(swe_state* state);
+
+/* ---------------------------------------------------------------------------
+ * Gradients through many steps (reverse mode; no counterpart in the paper).
+ *
+ * The derivative is that of the step of Sec. 2.2 with the time steps held
+ * fixed at the values the recorded run used (dt is data, not a function of
+ * the state), differentiated piecewise: each wet/dry test, HLLC case and
+ * min/max takes the branch the forward step took. A depth clipped at zero
+ * (never under the CFL step) is differentiated as if unclipped.
+ *
+ * Usage: swe_grad_record runs the steps and keeps a tape; swe_grad then
+ * computes, for a loss L given by its derivatives with respect to the final
+ * state and to the gauge depths, the gradient of L with respect to the
+ * initial state, the bed z and Manning's n. swe_grad can be called any
+ * number of times on one tape (different seeds). Requires a single-scenario
+ * mesh built with SWE_KERNEL_TILED (SWE_ESTATE otherwise). Results are in
+ * the mesh precision; FP64 is the reference for accuracy.
+ * ------------------------------------------------------------------------- */
+typedef struct swe_tape swe_tape;
+
+/* Advances `state` by n_steps CFL steps (as swe_run does, with no end time)
+ * and records: every step's dt, the depth at each of the n_gauges cells
+ * gauge_cells[j] (caller indices, repeats allowed) after every step into
+ * gauge_h[k * n_gauges + j] for step k = 0 .. n_steps-1 (host, may be NULL),
+ * and the state every checkpoint_every steps (device memory: about
+ * (ceil(n_steps / K) + K + 2) states, K = checkpoint_every). The state is
+ * left at step n_steps. Synchronises. Returns SWE_ENAN / SWE_EDRY if a step
+ * fails (no tape is made). The tape holds the mesh (not the state). */
+swe_status swe_grad_record(swe_state* state, int64_t n_steps, int64_t checkpoint_every,
+                           const int32_t* gauge_cells, int32_t n_gauges, double* gauge_h,
+                           swe_tape** out);
+
+/* Reverse sweep over the recorded steps. Seeds (host, caller order, any may
+ * be NULL = zero): g_h, g_hu, g_hv = dL/d(h, hu, hv) of the final state
+ * [n_tris each]; g_gauge = dL/d gauge_h [n_steps * n_gauges]. Outputs (host,
+ * caller order, any may be NULL): dL/dh, dL/dhu, dL/dhv of the initial state,
+ * dL/dz, dL/dn (n >= 0 assumed). Recomputes each segment of checkpoint_every
+ * steps from its checkpoint; returns SWE_ESTATE if a recomputed step did not
+ * reproduce the recorded dt. Synchronises. */
+swe_status swe_grad(swe_tape* tape, const double* g_h, const double* g_hu, const double* g_hv,
+                    const double* g_gauge, double* d_h0, double* d_hu0, double* d_hv0, double* d_z,
+                    double* d_n);
+
+/* info[0] = steps, info[1] = checkpoint interval, info[2] = device time of
+ * the recorded forward steps (ms, CUDA events), info[3] = device time of the
+ * last swe_grad's recompute and adjoint steps (ms), info[4] = tape bytes. */
+swe_status swe_tape_info(const swe_tape* tape, double* info);
+
+void swe_tape_destroy(swe_tape* tape);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free step (no counterpart in the paper).

@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["swe_api.cu", "mesh_build.cpp", "swe_noalloc.cu"]
-HEADERS = ["swe_kernels.cuh", "mesh_build.h"]
+SOURCES = ["swe_api.cu", "mesh_build.cpp", "swe_noalloc.cu", "swe_grad.cu"]
+HEADERS = ["swe_kernels.cuh", "swe_adjoint.cuh", "swe_handles.cuh", "mesh_build.h"]
 
 
 def nvcc() -> str:

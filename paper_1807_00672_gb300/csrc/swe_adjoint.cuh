@@ -1,0 +1,490 @@
+// Reverse mode (adjoint) of one explicit step, for gradients of a loss with
+// respect to the initial state, the bed z and Manning's n (through g n^2).
+//
+// One step maps U^n to U^{n+1} with a fixed dt (Sec. 2.2, Eq. 4 and the
+// semi-implicit friction):
+//   U*_i     = U^n_i - (dt / Omega_i) R_i,  R_i = sum over faces of s l (F + P n)
+//   U^{n+1}_i = friction(U*_i)              (clip of h at 0, momentum / d)
+// Given lambda = dL/dU^{n+1}, the adjoint step forms, per cell,
+//   mu_i  = dL/dU*_i          (friction transposed; needs only U^{n+1}, g n^2, dt)
+//   rho_i = dL/dR_i = -(dt / Omega_i) mu_i
+// and per face the vector-Jacobian product of its two residual contributions
+// with (rho_A, rho_B), giving dL/d(h, hu, hv, z) of both sides. Then
+//   dL/dU^n_i = mu_i + sum over the cell's faces of its side's part,
+//   dL/dz_i  += sum of the z parts,  dL/d(g n^2)_i += friction part.
+// Every branch (wet/dry tests, the HLLC case, the min/max of the wave-speed
+// estimates and of the reconstruction) is taken as the forward step takes
+// it; where the forward picks between two equal values (a tie of max(zA, zB)
+// or of the speed estimates) the derivative follows the first argument, the
+// convention of the FP64 reference the gradients are checked against.
+//
+// The friction factor d is recovered from U^{n+1}: with c = dt g n^2 h^{-7/3}
+// and q1 = |q^{n+1}|, d = 1 + c |q*| = 1 / (1 - c q1) exactly, so the adjoint
+// needs no per-step copy of U* (relative error about eps * d).
+// A depth clipped at 0 (never under the CFL step; the forward counts it) is
+// differentiated as if it were not clipped.
+#pragma once
+
+#include "swe_kernels.cuh"
+
+namespace swe {
+
+// dL/dU* of one cell from its post-step state (h1, q1x, q1y) and lambda:
+// mu (3 values) and the derivative with respect to its g n^2.
+template <typename Real>
+__device__ __forceinline__ void cell_vjp(Real h1, Real q1x, Real q1y, Real lh, Real lx, Real ly,
+                                         Real gn2, Real dt, const Num& num, Real& mh, Real& mx,
+                                         Real& my, Real& bgn2) {
+  using O = Ops<Real>;
+  const Real zero = Real(0);
+  if (O::wet(h1, num)) {
+    const Real q1n = O::sqrt_(q1x * q1x + q1y * q1y);
+    const Real ch = O::friction(dt, Real(1), Real(1), h1);  // dt h^{-7/3}
+    const Real c = ch * gn2;
+    const Real cq = c * q1n;        // (d - 1) / d
+    const Real rd = Real(1) - cq;   // 1 / d
+    const Real ql = q1x * lx + q1y * ly;
+    const Real k = q1n > zero ? O::div(c * ql, q1n) : zero;
+    mx = rd * (lx - k * q1x);
+    my = rd * (ly - k * q1y);
+    mh = lh + Real(7.0 / 3.0) * O::div(cq, h1) * ql;
+    bgn2 = -q1n * ch * ql;
+  } else {
+    mh = lh;
+    mx = zero;
+    my = zero;
+    bgn2 = zero;
+  }
+}
+
+// Vector-Jacobian product of one face. Inputs: both sides' cell states
+// (h, hu, hv, z) as the forward step read them, the wall flag, the geometry,
+// and rho = dL/dR of side A (the face adds c_A to R_A) and side B (the face
+// subtracts c_B from R_B). Outputs gA, gB = dL/d(h, hu, hv, z) of each side
+// through this face (gB = 0 for a wall: the mirror folds into A).
+template <typename Real>
+__device__ __forceinline__ void face_vjp(Real hA, Real huA, Real hvA, Real zA, Real hB, Real huB,
+                                         Real hvB, Real zB, bool wall, Real nx, Real ny, Real len,
+                                         const Num& num, Real rA0, Real rA1, Real rA2, Real rB0,
+                                         Real rB1, Real rB2, Real gA[4], Real gB[4]) {
+  using O = Ops<Real>;
+  const Real zero = Real(0), half = Real(0.5);
+  const Real g = Real(num.g);
+  // ---- forward, keeping what the reverse sweep needs
+  Real uA, vA, uB, vB;
+  velocity(hA, huA, hvA, num, uA, vA);
+  const bool wetcA = O::wet(hA, num);
+  const Real unA = uA * nx + vA * ny;
+  const Real utA = vA * nx - uA * ny;
+  Real unB, utB;
+  bool wetcB = false;
+  if (wall) {
+    hB = hA; zB = zA; unB = -unA; utB = utA;
+  } else {
+    velocity(hB, huB, hvB, num, uB, vB);
+    wetcB = O::wet(hB, num);
+    unB = uB * nx + vB * ny;
+    utB = vB * nx - uB * ny;
+  }
+  const bool zsA = zA >= zB;  // max(zA, zB) taken from A on a tie
+  const Real zs = zsA ? zA : zB;
+  Real hAs = fmax(zero, hA + zA - zs);
+  Real hBs = fmax(zero, hB + zB - zs);
+  const bool actA = O::wet(hAs, num), actB = O::wet(hBs, num);
+  if (!actA) hAs = zero;
+  if (!actB) hBs = zero;
+  // HLLC (same case analysis as the forward)
+  const bool wetA = hAs > zero, wetB = hBs > zero;
+  const Real cA = O::sqrt_(g * hAs);
+  const Real cB = O::sqrt_(g * hBs);
+  const Real us = (unA + unB) * half + cA - cB;
+  const Real cs = (cA + cB) * half + (unA - unB) * Real(0.25);
+  const bool firstA = (unA - cA) <= (us - cs);
+  const bool firstB = (unB + cB) >= (us + cs);
+  const Real SA = wetA ? (wetB ? (firstA ? unA - cA : us - cs) : unA - cA) : unB - Real(2) * cB;
+  const Real SB = wetA ? (wetB ? (firstB ? unB + cB : us + cs) : unA + Real(2) * cA) : unB + cB;
+  const Real qA = hAs * unA, qB = hBs * unB;
+  const Real FA1 = qA * unA + half * g * hAs * hAs;
+  const Real FB1 = qB * unB + half * g * hBs * hBs;
+  const Real inv = O::div(Real(1), SB - SA);
+  const Real N0 = SB * qA - SA * qB + SA * SB * (hBs - hAs);
+  const Real N1 = SB * FA1 - SA * FB1 + SA * SB * (qB - qA);
+  const Real H0 = N0 * inv;
+  const Real numS = SA * hBs * (unB - SB) - SB * hAs * (unA - SA);
+  const bool selA = numS <= zero;  // contact speed >= 0: transverse momentum from A
+  const bool left = SA >= zero, right = SB <= zero, dry = !wetA && !wetB;
+
+  // ---- reverse sweep
+  // residual contributions: A gets +l (F0, Fx + PA nx, Fy + PA ny), B gets -l (F0, Fx + PB nx, ...)
+  const Real bF0 = wall ? zero : len * (rA0 - rB0);
+  const Real bFx = len * (rA1 - rB1);
+  const Real bFy = len * (rA2 - rB2);
+  const Real bPA = len * (rA1 * nx + rA2 * ny);
+  const Real bPB = wall ? zero : -len * (rB1 * nx + rB2 * ny);
+  const Real bF1 = bFx * nx + bFy * ny;
+  const Real bF2 = wall ? zero : bFy * nx - bFx * ny;
+  Real bhAs = -g * hAs * bPA, bhBs = -g * hBs * bPB;
+  Real bhA = g * hA * bPA, bhB = g * hB * bPB;
+  Real bunA = zero, butA = zero, bunB = zero, butB = zero;
+  if (!dry) {
+    if (left) {
+      const Real bqA = bF0 + bF1 * unA + bF2 * utA;
+      bunA += bF1 * qA + bqA * hAs;
+      butA += bF2 * qA;
+      bhAs += bF1 * g * hAs + bqA * unA;
+    } else if (right) {
+      const Real bqB = bF0 + bF1 * unB + bF2 * utB;
+      bunB += bF1 * qB + bqB * hBs;
+      butB += bF2 * qB;
+      bhBs += bF1 * g * hBs + bqB * unB;
+    } else {
+      const Real ut = selA ? utA : utB;
+      if (selA) butA += bF2 * H0; else butB += bF2 * H0;
+      const Real bH0 = bF0 + bF2 * ut;
+      const Real bN0 = bH0 * inv, bN1 = bF1 * inv;
+      const Real binv = bH0 * N0 + bF1 * N1;
+      const Real bD = -binv * inv * inv;  // D = SB - SA
+      Real bSB = bD, bSA = -bD;
+      const Real dh = hBs - hAs, dq = qB - qA, SS = SA * SB;
+      bSB += bN0 * (qA + SA * dh) + bN1 * (FA1 + SA * dq);
+      bSA += bN0 * (SB * dh - qB) + bN1 * (SB * dq - FB1);
+      Real bqA = bN0 * SB - bN1 * SS;
+      Real bqB = bN1 * SS - bN0 * SA;
+      bhBs += bN0 * SS;
+      bhAs -= bN0 * SS;
+      const Real bFA1 = bN1 * SB, bFB1 = -bN1 * SA;
+      bqA += bFA1 * unA;
+      bunA += bFA1 * qA;
+      bhAs += bFA1 * g * hAs;
+      bqB += bFB1 * unB;
+      bunB += bFB1 * qB;
+      bhBs += bFB1 * g * hBs;
+      bhAs += bqA * unA;
+      bunA += bqA * hAs;
+      bhBs += bqB * unB;
+      bunB += bqB * hBs;
+      Real bcA = zero, bcB = zero;
+      if (wetA && wetB) {
+        Real bus = zero, bcs = zero;
+        if (firstA) { bunA += bSA; bcA -= bSA; } else { bus += bSA; bcs -= bSA; }
+        if (firstB) { bunB += bSB; bcB += bSB; } else { bus += bSB; bcs += bSB; }
+        bunA += half * bus + Real(0.25) * bcs;
+        bunB += half * bus - Real(0.25) * bcs;
+        bcA += bus + half * bcs;
+        bcB += half * bcs - bus;
+      } else if (wetA) {  // B dry: SA = unA - cA, SB = unA + 2 cA
+        bunA += bSA + bSB;
+        bcA += Real(2) * bSB - bSA;
+      } else {            // A dry: SA = unB - 2 cB, SB = unB + cB
+        bunB += bSA + bSB;
+        bcB += bSB - Real(2) * bSA;
+      }
+      if (wetA) bhAs += bcA * O::div(half * g, cA);
+      if (wetB) bhBs += bcB * O::div(half * g, cB);
+    }
+  }
+  // reconstruction h* = h + z - max(zA, zB) where it stays wet
+  Real bzA = zero, bzB = zero, bzs = zero;
+  if (actA) { bhA += bhAs; bzA += bhAs; bzs -= bhAs; }
+  if (actB) { bhB += bhBs; bzB += bhBs; bzs -= bhBs; }
+  if (zsA) bzA += bzs; else bzB += bzs;
+  if (wall) {  // B mirrors A: hB = hA, zB = zA, unB = -unA, utB = utA
+    bhA += bhB;
+    bzA += bzB;
+    bunA -= bunB;
+    butA += butB;
+  }
+  // face frame -> x, y velocities -> conserved variables
+  const Real buA = bunA * nx - butA * ny;
+  const Real bvA = bunA * ny + butA * nx;
+  gA[0] = bhA;
+  gA[1] = zero;
+  gA[2] = zero;
+  gA[3] = bzA;
+  if (wetcA) {
+    const Real r = O::div(Real(1), hA);
+    gA[1] = buA * r;
+    gA[2] = bvA * r;
+    gA[0] -= (buA * uA + bvA * vA) * r;
+  }
+  gB[0] = zero; gB[1] = zero; gB[2] = zero; gB[3] = zero;
+  if (!wall) {
+    const Real buB = bunB * nx - butB * ny;
+    const Real bvB = bunB * ny + butB * nx;
+    gB[0] = bhB;
+    gB[3] = bzB;
+    if (wetcB) {
+      const Real r = O::div(Real(1), hB);
+      gB[1] = buB * r;
+      gB[2] = bvB * r;
+      gB[0] -= (buB * uB + bvB * vB) * r;
+    }
+  }
+}
+
+// Inputs and outputs of one adjoint launch (interleaved cells, internal
+// order, padded to whole tiles).
+template <typename Real>
+struct AdjArgs {
+  const Real* un;      // U^n (h, hu, hv, z)
+  const Real* u1;      // U^{n+1} (h, hu, hv, z)
+  const Real* lam_in;  // dL/dU^{n+1} (h, hu, hv, accumulated dL/dz)
+  Real* lam_out;       // dL/dU^n, same layout
+  const Real* gn2;     // g n^2 per cell
+  Real* dgn2;          // accumulated dL/d(g n^2) per cell (read-modify-write)
+  Real dt;
+  int* err;            // kErr* bits (timeouts)
+};
+
+// Shared-memory plan of k_tiled_adjoint. Per stage: the tile's (and its
+// halo's) cells of U^n, U^{n+1} and lambda, the halo cells' areas and g n^2,
+// the face records with their geometry, the halo list. After the stages:
+// rho per tile and halo cell, the face slots (dh, dhu, dhv, dz) per face of
+// each tile cell, face-major, and the NS mbarriers.
+struct AdjLayout {
+  uint32_t ext, rec_cap, halo_cap;
+  uint32_t off_un, off_u1, off_lam, off_harea, off_hgn2, off_tS, off_g0, off_g1, off_g2, off_hidx;
+  uint32_t stage;
+  uint32_t off_rho, off_slots, off_bars, total;
+};
+
+inline AdjLayout make_adj_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, uint32_t ns,
+                                 uint32_t rec_cap, uint32_t halo_cap) {
+  auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+  AdjLayout L{};
+  L.rec_cap = rec_cap;
+  L.halo_cap = halo_cap;
+  L.ext = tc + halo_cap;
+  uint32_t o = 0;
+  L.off_un = o; o += a16(L.ext * 4 * w);
+  L.off_u1 = o; o += a16(L.ext * 4 * w);
+  L.off_lam = o; o += a16(L.ext * 4 * w);
+  L.off_harea = o; o += a16(halo_cap * w);
+  L.off_hgn2 = o; o += a16(halo_cap * w);
+  L.off_tS = o; o += a16(rec_cap * 4);
+  L.off_g0 = o; o += a16(rec_cap * w);
+  L.off_g1 = o; o += a16(rec_cap * w);
+  L.off_g2 = o; o += geo_arrays > 2 ? a16(rec_cap * w) : 0u;
+  L.off_hidx = o; o += a16(halo_cap * 4);
+  L.stage = o;
+  o = ns * L.stage;
+  L.off_rho = o; o += a16(L.ext * 4 * w);
+  L.off_slots = o; o += a16(3 * tc * 4 * w);
+  L.off_bars = o; o += a16(ns * 8);
+  L.total = o;
+  return L;
+}
+
+// Tiled adjoint of one step over the same tiles, records and work chunks as
+// k_tiled_step (scenario of each chunk, interleaved tile walk, NS-stage TMA
+// pipeline with the halo gathered by cp.async). Per tile:
+//   (A) mu and rho of every tile and halo cell (rho to shared memory, mu of
+//       the thread's own cells kept in registers);
+//   (B) the vector-Jacobian product of every face record into the slots of
+//       the tile's cells (a face shared with another tile gives only this
+//       tile's side, as in the forward);
+//   (C) each cell: dL/dU^n = mu + its three slots in face order, the z parts
+//       added to the running dL/dz, and its dL/d(g n^2) accumulated.
+// Three block barriers per tile.
+template <typename Real, int NT, int NS, int CPT>
+__global__ void __launch_bounds__(NT)
+    k_tiled_adjoint(DevMesh<Real> m, AdjArgs<Real> A, Num num, AdjLayout L) {
+  using O = Ops<Real>;
+  constexpr int TC = NT * CPT;
+  __shared__ int s_nrec[NS], s_nh[NS];
+  extern __shared__ __align__(128) unsigned char smem[];
+  Real* rho = reinterpret_cast<Real*>(smem + L.off_rho);      // [ext][4]
+  Real* slots = reinterpret_cast<Real*>(smem + L.off_slots);  // [3 TC][4]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bars);
+
+  const int scen = m.chunk_scen[blockIdx.x];
+  const int t_first = m.chunk_tile0[blockIdx.x];
+  const int n_tiles = m.chunk_ntiles[blockIdx.x];
+  const int t_step = m.chunk_stride[blockIdx.x];
+  const int cell_end = m.scen_cell_end[scen];
+  const Real dt = A.dt;
+  const int tid = threadIdx.x;
+
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  uint32_t parity_bits = 0, pending = 0;
+  auto issue = [&](int st, int t) {
+    unsigned char* p = smem + st * L.stage;
+    const int64_t base = (int64_t)t * TC;
+    const int64_t r0 = m.toff[t], h0 = m.hoff[t];
+    const uint32_t nrec = (uint32_t)(m.toff[t + 1] - r0);
+    const uint32_t nh = (uint32_t)(m.hoff[t + 1] - h0);
+    const uint32_t cells = TC * 4 * (uint32_t)sizeof(Real);
+    s_nrec[st] = (int)nrec;
+    s_nh[st] = (int)nh;
+    const uint32_t rb = nrec * (uint32_t)sizeof(Real);
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], 3 * cells + nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
+    bulk_g2s(p + L.off_un, A.un + 4 * base, cells, &bar[st]);
+    bulk_g2s(p + L.off_u1, A.u1 + 4 * base, cells, &bar[st]);
+    bulk_g2s(p + L.off_lam, A.lam_in + 4 * base, cells, &bar[st]);
+    bulk_g2s(p + L.off_tS, m.tS + r0, nrec * 4, &bar[st]);
+    bulk_g2s(p + L.off_g0, m.tg0 + r0, rb, &bar[st]);
+    bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
+    if (Geo<Real>::kArrays > 2) bulk_g2s(p + L.off_g2, m.tg2 + r0, rb, &bar[st]);
+    if (nh > 0) bulk_g2s(p + L.off_hidx, m.hidx + h0, nh * 4, &bar[st]);
+    pending |= 1u << st;
+  };
+  auto wait_stage = [&](int st) -> bool {
+    const bool ok = mbar_wait(&bar[st], (parity_bits >> st) & 1u);
+    if (ok) {
+      parity_bits ^= 1u << st;
+      pending &= ~(1u << st);
+    }
+    return ok;
+  };
+  // halo cells of stage st: three interleaved cells and two scalars each
+  auto gather_halo = [&](int st) {
+    unsigned char* p = smem + st * L.stage;
+    const int32_t* hl = reinterpret_cast<const int32_t*>(p + L.off_hidx);
+    Real* dun = reinterpret_cast<Real*>(p + L.off_un) + 4 * TC;
+    Real* du1 = reinterpret_cast<Real*>(p + L.off_u1) + 4 * TC;
+    Real* dla = reinterpret_cast<Real*>(p + L.off_lam) + 4 * TC;
+    Real* dar = reinterpret_cast<Real*>(p + L.off_harea);
+    Real* dgn = reinterpret_cast<Real*>(p + L.off_hgn2);
+    const int nh = s_nh[st];
+    constexpr int kV = 16 / (int)sizeof(Real);  // values per 16-byte copy
+    for (int q = tid; q < nh; q += NT) {
+      const int64_t c = hl[q];
+#pragma unroll
+      for (int b = 0; b < 4 / kV; ++b) {
+        cp_async16(dun + 4 * q + b * kV, A.un + 4 * c + b * kV);
+        cp_async16(du1 + 4 * q + b * kV, A.u1 + 4 * c + b * kV);
+        cp_async16(dla + 4 * q + b * kV, A.lam_in + 4 * c + b * kV);
+      }
+      cp_async(dar + q, m.area + c);
+      cp_async(dgn + q, A.gn2 + c);
+    }
+  };
+
+  int timeout = 0;
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NS - 1; ++i)
+      if (i < n_tiles) issue(i, t_first + i * t_step);
+  }
+  if (n_tiles > 0) {
+    const bool ok = (tid == 0) ? wait_stage(0) : true;
+    if (__syncthreads_or(!ok)) {
+      timeout = 1;
+    } else {
+      gather_halo(0);
+      cp_async_wait_all();
+      __syncthreads();
+    }
+  }
+  for (int k = 0; !timeout && k < n_tiles; ++k) {
+    const int st = k % NS;
+    const int tile = t_first + k * t_step;
+    const bool has_next = k + 1 < n_tiles;
+    if (tid == 0 && k + NS - 1 < n_tiles) issue((k + NS - 1) % NS, tile + (NS - 1) * t_step);
+    const unsigned char* p = smem + st * L.stage;
+    const Real* sun = reinterpret_cast<const Real*>(p + L.off_un);
+    const Real* su1 = reinterpret_cast<const Real*>(p + L.off_u1);
+    const Real* sla = reinterpret_cast<const Real*>(p + L.off_lam);
+    const Real* har = reinterpret_cast<const Real*>(p + L.off_harea);
+    const Real* hgn = reinterpret_cast<const Real*>(p + L.off_hgn2);
+    const int32_t* rS = reinterpret_cast<const int32_t*>(p + L.off_tS);
+    const Real* rg0 = reinterpret_cast<const Real*>(p + L.off_g0);
+    const Real* rg1 = reinterpret_cast<const Real*>(p + L.off_g1);
+    const Real* rg2 = reinterpret_cast<const Real*>(p + L.off_g2);
+    const int base = tile * TC;
+    const int nc = min(TC, cell_end - base);
+    const int nrec = s_nrec[st];
+    const int nh = s_nh[st];
+
+    // (A) mu, rho
+    Real mu[CPT][3], bg[CPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      const int j = tid + cc * NT;
+      const V4<Real> c1 = ld4(su1 + 4 * j);
+      const V4<Real> la = ld4(sla + 4 * j);
+      cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, A.gn2[base + j], dt, num, mu[cc][0],
+                     mu[cc][1], mu[cc][2], bg[cc]);
+      const Real a = j < nc ? -O::div(dt, m.area[base + j]) : Real(0);  // padding: area 0
+      st4(rho + 4 * j, a * mu[cc][0], a * mu[cc][1], a * mu[cc][2], Real(0));
+    }
+    for (int q = tid; q < nh; q += NT) {
+      const int j = TC + q;
+      const V4<Real> c1 = ld4(su1 + 4 * j);
+      const V4<Real> la = ld4(sla + 4 * j);
+      Real mh, mx, my, b;
+      cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, hgn[q], dt, num, mh, mx, my, b);
+      const Real a = -O::div(dt, har[q]);
+      st4(rho + 4 * j, a * mh, a * mx, a * my, Real(0));
+    }
+    __syncthreads();
+
+    // (B) face records
+    for (int r = tid; r < nrec; r += NT) {
+      const int32_t packed = rS[r];
+      const int a = packed >> 16;
+      if (a == kSideWall) continue;  // padding record
+      const int b = (int)(int16_t)(packed & 0xffff);
+      const bool wall = (b == kSideWall);
+      const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
+      const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (TC - 1)) : TC + b);
+      const V4<Real> UA = ld4(sun + 4 * ia);
+      const V4<Real> UB = ld4(sun + 4 * ib);
+      const V4<Real> RA = ld4(rho + 4 * ia);
+      const V4<Real> RB = ld4(rho + 4 * ib);
+      Real nx, ny, len;
+      Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
+      Real gA[4], gB[4];
+      const Real zero = Real(0);
+      face_vjp<Real>(UA.x, UA.y, UA.z, UA.w, UB.x, UB.y, UB.z, UB.w, wall, nx, ny, len, num, RA.x,
+                     RA.y, RA.z, wall ? zero : RB.x, wall ? zero : RB.y, wall ? zero : RB.z, gA, gB);
+      if (a < 0) st4(slots + 4 * (-1 - a), gA[0], gA[1], gA[2], gA[3]);
+      if (b < 0 && !wall) st4(slots + 4 * (-1 - b), gB[0], gB[1], gB[2], gB[3]);
+    }
+    const bool ok = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
+    if (__syncthreads_or(!ok)) {
+      timeout = 1;
+      break;
+    }
+    if (has_next) gather_halo((k + 1) % NS);
+
+    // (C) cells
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      const int j = tid + cc * NT;
+      if (j >= nc) break;
+      const V4<Real> f0 = ld4(slots + 4 * j);
+      const V4<Real> f1 = ld4(slots + 4 * (TC + j));
+      const V4<Real> f2 = ld4(slots + 4 * (2 * TC + j));
+      const Real dzr = sla[4 * j + 3];
+      st4(A.lam_out + 4 * (int64_t)(base + j), mu[cc][0] + f0.x + f1.x + f2.x,
+          mu[cc][1] + f0.y + f1.y + f2.y, mu[cc][2] + f0.z + f1.z + f2.z, dzr + f0.w + f1.w + f2.w);
+      A.dgn2[base + j] += bg[cc];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  if (timeout && tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+      if ((pending >> i) & 1u) mbar_wait(&bar[i], (parity_bits >> i) & 1u);
+    atomicOr(A.err, kErrTimeout);
+  }
+}
+
+// Adds g[k * G + j] to the depth adjoint of cell cells[j] for j < G (one
+// thread, so repeated gauge cells add up in a fixed order).
+template <typename Real>
+__global__ void k_inject_gauges(Real* lam, const int32_t* cells, const double* g, int64_t k, int G) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int j = 0; j < G; ++j) lam[4 * (int64_t)cells[j]] += Real(g[k * (int64_t)G + j]);
+}
+
+}  // namespace swe

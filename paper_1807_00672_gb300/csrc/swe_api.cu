@@ -21,6 +21,7 @@
 
 #include "../../include/swe.h"
 #include "mesh_build.h"
+#include "swe_handles.cuh"
 #include "swe_kernels.cuh"
 
 namespace swe {
@@ -40,161 +41,40 @@ __global__ void k_set_end(Ctl* ctls, int n, double t_end) {
 
 }  // namespace swe
 
+namespace swe_host {
+
+thread_local std::string g_cuda_msg;
+
+bool cuda_failed_at(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return false;
+  const char* base = file;
+  for (const char* c = file; *c; ++c)
+    if (*c == '/') base = c + 1;
+  g_cuda_msg = std::string(cudaGetErrorString(e)) + " in " + what + " (" + base + ":" +
+               std::to_string(line) + ")";
+  return true;
+}
+
+}  // namespace swe_host
+
+using namespace swe_host;
+
 namespace {
 
 constexpr int kStepsPerGraph = 16;
 constexpr int kDefaultTile = 256;
 
-thread_local std::string g_cuda_msg;
-
-bool cuda_failed_at(cudaError_t e, const char* what, int line) {
-  if (e == cudaSuccess) return false;
-  g_cuda_msg = std::string(cudaGetErrorString(e)) + " in " + what + " (swe_api.cu:" +
-               std::to_string(line) + ")";
-  return true;
-}
-#define cuda_failed(call) cuda_failed_at((call), #call, __LINE__)
+#define cuda_failed(call) swe_host::cuda_failed_at((call), #call, __FILE__, __LINE__)
 
 #define CK(call)                                  \
   do {                                            \
     if (cuda_failed(call)) return SWE_ECUDA;      \
   } while (0)
 
-size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
-
-// Bump allocator over one cudaMalloc. take() returns nullptr (and sets
-// overflow) instead of handing out memory past the allocation.
-struct Arena {
-  char* base = nullptr;
-  size_t size = 0, used = 0;
-  bool overflow = false;
-  void* take(size_t bytes) {
-    if (used + align_up(bytes) > size) {
-      overflow = true;
-      return nullptr;
-    }
-    void* p = base + used;
-    used += align_up(bytes);
-    return p;
-  }
-};
-
-struct Layout {
-  size_t total = 0;
-  void add(size_t bytes) { total += align_up(bytes); }
-};
-
-// Where one scenario lives inside the mesh.
-struct Scenario {
-  int64_t caller0 = 0;  // first caller cell index (scenarios are concatenated)
-  int64_t ncells = 0;
-  int64_t cell0 = 0;    // first internal cell (tile-aligned in the tiled layout)
-  int64_t tile0 = 0, ntiles = 0;
-  int64_t chunk0 = 0, nchunks = 0;  // work chunks (= mass partial slots) of the tiled kernel
-};
-
 }  // namespace
 
-struct swe_mesh {
-  swe_params prm{};
-  int device = 0;
-  int sms = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int64_t V = 0, T = 0, E = 0, Eb = 0;
-  int kernel = SWE_KERNEL_TILED;
-  int tile = kDefaultTile;
-  int64_t ntiles = 0, records = 0, halos = 0;
-  int stages = 2;
-  int cpt = 2;  // cells per thread of the tiled kernel (threads = tile / cpt)
-  swe::TileLayout layout{};
-  int64_t Tp = 0;  // internal cell slots (tiled: scenarios padded to whole tiles)
-  std::vector<Scenario> scen;
-  int64_t nchunks = 0;
-  Arena arena;
-  int32_t* perm = nullptr;  // internal cell -> caller cell (-1 for padding)
-  void* area = nullptr;
-  void* irP = nullptr;
-  int32_t *eL = nullptr, *eR = nullptr, *cf[3] = {nullptr, nullptr, nullptr};
-  void *nx = nullptr, *ny = nullptr, *len = nullptr;
-  int64_t *toff = nullptr, *hoff = nullptr;
-  int32_t *tS = nullptr, *hidx = nullptr;
-  void *tg0 = nullptr, *tg1 = nullptr, *tg2 = nullptr;
-  int32_t *chunk_scen = nullptr, *chunk_tile0 = nullptr, *chunk_ntiles = nullptr;
-  int32_t* chunk_stride = nullptr;
-  int32_t* scen_cell_end = nullptr;
-  int grid_edge = 1, grid_cell = 1, grid_cfl = 1, max_grid = 1;
-};
-
-struct swe_state {
-  swe_mesh* mesh = nullptr;
-  Arena arena;
-  void *h[2] = {nullptr, nullptr}, *hu[2] = {nullptr, nullptr}, *hv[2] = {nullptr, nullptr};
-  void *z = nullptr, *gn2 = nullptr;
-  int stride = 1;  // 4: interleaved cells (h, hu, hv, z) for the tiled kernel
-  void* fx[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  double* partial = nullptr;
-  double* stage = nullptr;       // T doubles in caller order
-  swe::Ctl* ctl = nullptr;       // one per scenario
-  swe::Ctl* host_ctl = nullptr;  // pinned mirror
-  cudaStream_t capture = nullptr;
-  cudaGraphExec_t graph = nullptr;
-  bool open_ended = true;  // the device t_end is +inf for every scenario
-};
 
 namespace {
-
-int nscen(const swe_mesh* m) { return (int)m->scen.size(); }
-
-swe::Num num_of(const swe_mesh* m) { return swe::make_num(m->prm.g, m->prm.courant, m->prm.h_eps); }
-
-template <typename Real>
-swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
-  swe::DevMesh<Real> d{};
-  d.T = m->T;
-  d.E = m->E;
-  d.area = (const Real*)m->area;
-  d.irP = (const Real*)m->irP;
-  d.eL = m->eL;
-  d.eR = m->eR;
-  d.nx = (const Real*)m->nx;
-  d.ny = (const Real*)m->ny;
-  d.len = (const Real*)m->len;
-  d.cf0 = m->cf[0];
-  d.cf1 = m->cf[1];
-  d.cf2 = m->cf[2];
-  d.chunk_scen = m->chunk_scen;
-  d.chunk_tile0 = m->chunk_tile0;
-  d.chunk_ntiles = m->chunk_ntiles;
-  d.chunk_stride = m->chunk_stride;
-  d.scen_cell_end = m->scen_cell_end;
-  d.ntiles = m->ntiles;
-  d.toff = m->toff;
-  d.hoff = m->hoff;
-  d.hidx = m->hidx;
-  d.tS = m->tS;
-  d.tg0 = (const Real*)m->tg0;
-  d.tg1 = (const Real*)m->tg1;
-  d.tg2 = (const Real*)m->tg2;
-  return d;
-}
-
-template <typename Real>
-swe::DevState<Real> dev_state(const swe_state* s) {
-  swe::DevState<Real> d{};
-  for (int b = 0; b < 2; ++b) {
-    d.h[b] = (Real*)s->h[b];
-    d.hu[b] = (Real*)s->hu[b];
-    d.hv[b] = (Real*)s->hv[b];
-  }
-  d.stride = s->stride;
-  d.z = (const Real*)s->z;
-  d.gn2 = (const Real*)s->gn2;
-  for (int k = 0; k < 5; ++k) d.fx[k] = (Real*)s->fx[k];
-  d.partial = s->partial;
-  d.ctl = s->ctl;
-  return d;
-}
 
 int grid_for(int64_t n, int threads, int cap) {
   int64_t g = (n + threads - 1) / threads;
@@ -277,26 +157,9 @@ void set_edge_grids(swe_mesh* m) {
   m->grid_cfl = grid_for(m->T, 256, m->sms * occ_cfl);
 }
 
-template <typename Real>
-void launch_step(const swe_state* s, cudaStream_t st) {
-  const swe_mesh* m = s->mesh;
-  constexpr bool comp = sizeof(Real) == 4;
-  swe::DevMesh<Real> dm = dev_mesh<Real>(m);
-  swe::DevState<Real> ds = dev_state<Real>(s);
-  swe::Num num = num_of(m);
-  if (m->kernel == SWE_KERNEL_EDGE) {
-    swe::k_edge_flux<Real><<<m->grid_edge, 256, 0, st>>>(dm, ds, num);
-    swe::k_cell_update<Real, comp><<<m->grid_cell, 256, 0, st>>>(dm, ds, num);
-  } else if (m->cpt == 2) {
-    launch_tiled_cpt<Real, comp, 2>(m, dm, ds, num, st);
-  } else {
-    launch_tiled_cpt<Real, comp, 1>(m, dm, ds, num, st);
-  }
-}
-
 void launch_one_step(const swe_state* s, cudaStream_t st) {
-  if (s->mesh->prm.precision == SWE_F64) launch_step<double>(s, st);
-  else launch_step<float>(s, st);
+  if (s->mesh->prm.precision == SWE_F64) launch_forward(s->mesh, dev_state<double>(s), st);
+  else launch_forward(s->mesh, dev_state<float>(s), st);
 }
 
 template <typename Real>
@@ -367,12 +230,6 @@ bool all_done(const swe_state* s) {
   return true;
 }
 
-swe_status read_ctl(const swe_state* s) {
-  CK(cudaMemcpyAsync(s->host_ctl, s->ctl, sizeof(swe::Ctl) * nscen(s->mesh), cudaMemcpyDeviceToHost,
-                     s->mesh->stream));
-  CK(cudaStreamSynchronize(s->mesh->stream));
-  return SWE_OK;
-}
 
 swe_status ensure_graph(swe_state* s) {
   if (s->graph) return SWE_OK;
@@ -765,6 +622,62 @@ void scatter_field(const swe_state* s, int k, int b) {
 
 }  // namespace
 
+namespace swe_host {
+
+swe_status read_ctl(const swe_state* s) {
+  CK(cudaMemcpyAsync(s->host_ctl, s->ctl, sizeof(swe::Ctl) * nscen(s->mesh), cudaMemcpyDeviceToHost,
+                     s->mesh->stream));
+  CK(cudaStreamSynchronize(s->mesh->stream));
+  return SWE_OK;
+}
+
+static void free_mesh(swe_mesh* m) {
+  if (m->arena.base) cudaFree(m->arena.base);
+  if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+  delete m;
+}
+
+void retain_mesh(swe_mesh* m) { m->refs += 1; }
+
+void release_mesh(swe_mesh* m) {
+  m->refs -= 1;
+  if (m->dead && m->refs == 0) free_mesh(m);
+}
+
+template <typename Real>
+static void launch_forward_t(const swe_mesh* m, const swe::DevState<Real>& ds, cudaStream_t st) {
+  constexpr bool comp = sizeof(Real) == 4;
+  const swe::DevMesh<Real> dm = dev_mesh<Real>(m);
+  const swe::Num num = num_of(m);
+  if (m->kernel == SWE_KERNEL_EDGE) {
+    swe::k_edge_flux<Real><<<m->grid_edge, 256, 0, st>>>(dm, ds, num);
+    swe::k_cell_update<Real, comp><<<m->grid_cell, 256, 0, st>>>(dm, ds, num);
+  } else if (m->cpt == 2) {
+    launch_tiled_cpt<Real, comp, 2>(m, dm, ds, num, st);
+  } else {
+    launch_tiled_cpt<Real, comp, 1>(m, dm, ds, num, st);
+  }
+}
+
+void launch_forward(const swe_mesh* m, const swe::DevState<float>& ds, cudaStream_t st) {
+  launch_forward_t<float>(m, ds, st);
+}
+void launch_forward(const swe_mesh* m, const swe::DevState<double>& ds, cudaStream_t st) {
+  launch_forward_t<double>(m, ds, st);
+}
+
+void gather_any(const swe_mesh* m, const double* src, void* dst, int stride) {
+  if (m->prm.precision == SWE_F64) launch_gather<double>(m, src, dst, stride);
+  else launch_gather<float>(m, src, dst, stride);
+}
+
+void scatter_any(const swe_mesh* m, const void* src, double* dst, int stride) {
+  if (m->prm.precision == SWE_F64) launch_scatter<double>(m, src, dst, stride);
+  else launch_scatter<float>(m, src, dst, stride);
+}
+
+}  // namespace swe_host
+
 extern "C" {
 
 void swe_params_default(swe_params* p) {
@@ -831,9 +744,9 @@ swe_status swe_mesh_device_bytes(const swe_mesh* m, int64_t* bytes) {
 
 void swe_mesh_destroy(swe_mesh* m) {
   if (!m) return;
-  if (m->arena.base) cudaFree(m->arena.base);
-  if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
-  delete m;
+  m->dead = true;
+  m->refs += 1;  // the caller's own use, dropped at once
+  release_mesh(m);
 }
 
 swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const double* hv,
@@ -848,6 +761,7 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
   const int n = nscen(m);
   swe_state* s = new swe_state();
   s->mesh = m;
+  retain_mesh(m);
   const bool interleaved = (m->kernel == SWE_KERNEL_TILED);
   Layout L;
   if (interleaved) {
@@ -863,7 +777,7 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
   L.add(sizeof(swe::Ctl) * n);
   if (cudaMalloc((void**)&s->arena.base, L.total) != cudaSuccess) {
     cudaGetLastError();
-    delete s;
+    swe_state_destroy(s);
     return SWE_ENOMEM;
   }
   s->arena.size = L.total;
@@ -1066,12 +980,14 @@ swe_status swe_next_dt(const swe_state* s, double* dt) {
 
 void swe_state_destroy(swe_state* s) {
   if (!s) return;
-  if (s->mesh && s->mesh->stream) cudaStreamSynchronize(s->mesh->stream);
+  swe_mesh* m = s->mesh;
+  if (m && m->stream) cudaStreamSynchronize(m->stream);
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->capture) cudaStreamDestroy(s->capture);
   if (s->host_ctl) cudaFreeHost(s->host_ctl);
   if (s->arena.base) cudaFree(s->arena.base);
   delete s;
+  if (m) release_mesh(m);
 }
 
 }  // extern "C"

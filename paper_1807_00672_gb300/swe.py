@@ -34,7 +34,8 @@ EXPORTS = (
     "swe_mesh_scenarios", "swe_mesh_device_bytes", "swe_mesh_destroy", "swe_state_init",
     "swe_state_set", "swe_step", "swe_run", "swe_advance", "swe_sync", "swe_copy_out",
     "swe_state_info", "swe_next_dt", "swe_scenario_info", "swe_state_destroy", "swe_strerror",
-    "swe_last_cuda_error", "swe_step_edges_static",
+    "swe_last_cuda_error", "swe_step_edges_static", "swe_grad_record", "swe_grad",
+    "swe_tape_info", "swe_tape_destroy",
 )
 
 
@@ -96,6 +97,10 @@ def lib():
         "swe_state_destroy": (None, [vp]),
         "swe_strerror": (ctypes.c_char_p, [st]),
         "swe_last_cuda_error": (ctypes.c_char_p, []),
+        "swe_grad_record": (st, [vp, i64, i64, vp, ctypes.c_int32, vp, pp]),
+        "swe_grad": (st, [vp] + [vp] * 9),
+        "swe_tape_info": (st, [vp, vp]),
+        "swe_tape_destroy": (None, [vp]),
         "swe_step_edges_static": (st, [i64, i64] + [vp] * 13 + [dbl] * 4 + [vp] * 3
                                   + [vp, vp, vp]),
     }
@@ -289,6 +294,58 @@ class State:
     def close(self):
         if getattr(self, "_h", None):
             lib().swe_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tape:
+    """Steps recorded for gradients (swe_grad_record): advances ``state`` by
+    ``n_steps`` CFL steps, keeping every dt, the depths at ``gauges`` (caller
+    cell indices) after every step, and checkpoints every
+    ``checkpoint_every`` steps. ``gauge_h`` is [n_steps, len(gauges)]."""
+
+    def __init__(self, state: State, n_steps: int, checkpoint_every: int = 50, gauges=None):
+        g = np.ascontiguousarray(gauges if gauges is not None else [], dtype=np.int32).reshape(-1)
+        self.gauges = g
+        self.n_steps = int(n_steps)
+        self.gauge_h = np.zeros((self.n_steps, g.shape[0]))
+        self.mesh = state.mesh
+        h = ctypes.c_void_p()
+        s = lib().swe_grad_record(state._h, self.n_steps, int(checkpoint_every),
+                                  _p(g) if g.size else None, g.shape[0],
+                                  _p(self.gauge_h) if g.size else None, ctypes.byref(h))
+        _check(s, "swe_grad_record")
+        self._h = h
+
+    def grad(self, g_h=None, g_hu=None, g_hv=None, g_gauge=None):
+        """Gradient of a loss given by dL/d(final h, hu, hv) and dL/d gauge_h.
+        Returns dict(h, hu, hv, z, n) of dL/d(initial h, hu, hv), dL/dz, dL/dn."""
+        T = self.mesh.T
+        seeds = [None if a is None else _f64(a).reshape(T) for a in (g_h, g_hu, g_hv)]
+        gg = None
+        if g_gauge is not None and self.gauges.size:
+            gg = _f64(g_gauge).reshape(self.n_steps, self.gauges.shape[0])
+        out = {k: np.empty(T) for k in ("h", "hu", "hv", "z", "n")}
+        s = lib().swe_grad(self._h, *[None if a is None else _p(a) for a in seeds],
+                           None if gg is None else _p(gg),
+                           *[_p(out[k]) for k in ("h", "hu", "hv", "z", "n")])
+        _check(s, "swe_grad")
+        return out
+
+    def info(self):
+        a = np.zeros(5)
+        _check(lib().swe_tape_info(self._h, _p(a)), "swe_tape_info")
+        return dict(steps=int(a[0]), checkpoint_every=int(a[1]), record_ms=float(a[2]),
+                    grad_ms=float(a[3]), bytes=int(a[4]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().swe_tape_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -146,3 +146,18 @@ def test_scenario_index_is_checked():
     with pytest.raises(swe.SweError) as e:
         st.scenario(2)
     assert e.value.status == swe.SWE_EINVAL
+
+
+def test_mesh_closed_before_its_state_stays_alive_until_the_state_goes():
+    """Destroying a mesh that a state still uses only marks it; the state
+    keeps working and frees the mesh when it is destroyed itself (garbage
+    collection may finalise the two in either order)."""
+    cases = scenario_mix()[:3]
+    mesh, st = ensemble_state(cases, precision="f32")
+    ref_mesh, ref = ensemble_state(cases, precision="f32")
+    mesh.close()
+    st.run(5)
+    ref.run(5)
+    for a, b in zip(st.fields(), ref.fields()):
+        assert np.array_equal(a, b)
+    st.close()
