@@ -206,6 +206,9 @@ def main():
                     help="skip the fp64, error and ensemble legs")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble leg")
     ap.add_argument("--ensemble-steps", type=int, default=200)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--adjoint-steps", type=int, default=500)
+    ap.add_argument("--adjoint-checkpoint", type=int, default=50)
     ap.add_argument("--ref-cells", type=int, default=25_000)
     ap.add_argument("--cpu-cells", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=150)
@@ -333,6 +336,8 @@ def main():
         out["error"] = error_leg(args)
     if rank == 0 and not args.no_extras and not args.no_ensemble:
         out["ensemble"] = ensemble_leg(args, stream)
+    if rank == 0 and not args.no_extras and not args.no_adjoint:
+        out["adjoint"] = adjoint_leg(args, stream)
     st.close()
     mesh.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -442,6 +447,85 @@ def ensemble_leg(args, stream):
            "setup_s": setup_s, "scenario_steps": sorted(steps)}
     st.close()
     mesh.close()
+    return res
+
+
+# Algorithmic bytes per cell of one adjoint step: reads U^n (h, hu, hv, z),
+# U^{n+1} (h, hu, hv), lambda^{n+1} (4 words), area, g n^2 and the running
+# dL/d(g n^2), the edge geometry and endpoints once (1.5 edges per cell);
+# writes lambda^n (4 words) and dL/d(g n^2): 23.5 words + 12 bytes.
+def adjoint_bytes_per_cell(word: int) -> float:
+    return 23.5 * word + 12.0
+
+
+def adjoint_leg(args, stream):
+    """Gradient of the calibration loss (1,000,000 triangles fully wet, 64
+    gauges, L = sum over steps and gauges of (h - h_obs)^2, observations from
+    the same run with a perturbed Manning n) with respect to n, z and the
+    initial state, through --adjoint-steps steps with checkpoints every
+    --adjoint-checkpoint steps. Reports the device times of the plain forward
+    run, the recorded forward and the backward (recompute + adjoint), their
+    ratio, and the FP32 gradient's distance to the FP64 one."""
+    import torch
+    from paper_1807_00672_gb300 import inputs, swe
+    N, K = args.adjoint_steps, args.adjoint_checkpoint
+    case = inputs.make_config("calibration_1m")
+    gauges = inputs.gauge_cells(case, 64, seed=5)
+    n_obs = inputs.perturbed_manning(case, seed=5)
+    res = {"workload": "calibration_1m", "triangles": case.mesh.n_tris, "steps": N,
+           "checkpoint_every": K, "gauges": int(gauges.shape[0])}
+    grads = {}
+    for prec in ("f32", "f64"):
+        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=prec, stream=ctypes_stream(stream))
+        obs_st = swe.State(mesh, case.h, case.hu, case.hv, case.z, n_obs)
+        obs_tape = swe.Tape(obs_st, N, K, gauges)
+        obs = obs_tape.gauge_h.copy()
+        obs_tape.close()
+        obs_st.close()
+        # plain forward: N steps replayed from graphs
+        st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+        st.run(16)
+        st.set(case.h, case.hu, case.hv)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.run(N, sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        st.sync()
+        fwd_ms = a.elapsed_time(b)
+        st.set(case.h, case.hu, case.hv)
+        tape = swe.Tape(st, N, K, gauges)
+        resid = tape.gauge_h - obs
+        g = 2.0 * resid
+        tape.grad(g_gauge=g)  # warm-up
+        r = tape.grad(g_gauge=g)
+        info = tape.info()
+        grads[prec] = r
+        word = 4 if prec == "f32" else 8
+        bwd = info["grad_ms"]
+        adj_step = max(bwd - (N - (N + K - 1) // K) * fwd_ms / N, 1e-9) / N
+        peak, kind = measured_peaks()
+        res[prec] = {
+            "loss": float((resid ** 2).sum()), "forward_ms": fwd_ms,
+            "recorded_forward_ms": info["record_ms"], "backward_ms": bwd,
+            "backward_over_forward": bwd / fwd_ms,
+            "adjoint_step_ms_est": adj_step,
+            "adjoint_hbm_frac_est": adjoint_bytes_per_cell(word) * mesh.T / (adj_step * 1e-3) / 1e9 / peak,
+            "tape_bytes": info["bytes"],
+            "finite": bool(all(np.isfinite(v).all() for v in r.values()))}
+        tape.close()
+        st.close()
+        mesh.close()
+    for k in ("n", "z", "h"):
+        ref = grads["f64"][k]
+        res[f"f32_vs_f64_rel_{k}"] = float(np.abs(grads["f32"][k] - ref).max() / np.abs(ref).max())
+    res["adjoint_alg_bytes_per_cell"] = {"f32": adjoint_bytes_per_cell(4), "f64": adjoint_bytes_per_cell(8)}
+    res["peak_source"] = f"{kind} HBM copy bandwidth"
+    res["note"] = ("backward = recompute of each checkpoint segment's inner steps with the forward "
+                   "kernel + one adjoint launch per step; adjoint step time estimated as (backward - "
+                   "recomputed steps x forward step) / steps")
     return res
 
 

@@ -236,9 +236,10 @@ struct AdjArgs {
   int* err;            // kErr* bits (timeouts)
 };
 
-// Shared-memory plan of k_tiled_adjoint. Per stage: the tile's (and its
-// halo's) cells of U^n, U^{n+1} and lambda, the halo cells' areas and g n^2,
-// the face records with their geometry, the halo list. After the stages:
+// Shared-memory plan of k_tiled_adjoint. Per stage: the tile's and its
+// halo's cells of U^n; the halo cells' U^{n+1}, lambda, areas and g n^2 (a
+// tile's own cells read theirs straight from global memory into registers);
+// the face records with their geometry; the halo list. After the stages:
 // rho per tile and halo cell, the face slots (dh, dhu, dhv, dz) per face of
 // each tile cell, face-major, and the NS mbarriers.
 struct AdjLayout {
@@ -257,8 +258,8 @@ inline AdjLayout make_adj_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, u
   L.ext = tc + halo_cap;
   uint32_t o = 0;
   L.off_un = o; o += a16(L.ext * 4 * w);
-  L.off_u1 = o; o += a16(L.ext * 4 * w);
-  L.off_lam = o; o += a16(L.ext * 4 * w);
+  L.off_u1 = o; o += a16(halo_cap * 4 * w);
+  L.off_lam = o; o += a16(halo_cap * 4 * w);
   L.off_harea = o; o += a16(halo_cap * w);
   L.off_hgn2 = o; o += a16(halo_cap * w);
   L.off_tS = o; o += a16(rec_cap * 4);
@@ -297,11 +298,9 @@ __global__ void __launch_bounds__(NT)
   Real* slots = reinterpret_cast<Real*>(smem + L.off_slots);  // [3 TC][4]
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bars);
 
-  const int scen = m.chunk_scen[blockIdx.x];
-  const int t_first = m.chunk_tile0[blockIdx.x];
-  const int n_tiles = m.chunk_ntiles[blockIdx.x];
-  const int t_step = m.chunk_stride[blockIdx.x];
-  const int cell_end = m.scen_cell_end[scen];
+  const Chunk ch = m.chunks[blockIdx.x];
+  const int t_first = ch.tile0, n_tiles = ch.ntiles, t_step = ch.stride;
+  const int cell_end = ch.cell_end;
   const Real dt = A.dt;
   const int tid = threadIdx.x;
 
@@ -324,10 +323,8 @@ __global__ void __launch_bounds__(NT)
     s_nh[st] = (int)nh;
     const uint32_t rb = nrec * (uint32_t)sizeof(Real);
     fence_proxy_async();
-    mbar_expect_tx(&bar[st], 3 * cells + nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
+    mbar_expect_tx(&bar[st], cells + nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
     bulk_g2s(p + L.off_un, A.un + 4 * base, cells, &bar[st]);
-    bulk_g2s(p + L.off_u1, A.u1 + 4 * base, cells, &bar[st]);
-    bulk_g2s(p + L.off_lam, A.lam_in + 4 * base, cells, &bar[st]);
     bulk_g2s(p + L.off_tS, m.tS + r0, nrec * 4, &bar[st]);
     bulk_g2s(p + L.off_g0, m.tg0 + r0, rb, &bar[st]);
     bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
@@ -348,8 +345,8 @@ __global__ void __launch_bounds__(NT)
     unsigned char* p = smem + st * L.stage;
     const int32_t* hl = reinterpret_cast<const int32_t*>(p + L.off_hidx);
     Real* dun = reinterpret_cast<Real*>(p + L.off_un) + 4 * TC;
-    Real* du1 = reinterpret_cast<Real*>(p + L.off_u1) + 4 * TC;
-    Real* dla = reinterpret_cast<Real*>(p + L.off_lam) + 4 * TC;
+    Real* du1 = reinterpret_cast<Real*>(p + L.off_u1);
+    Real* dla = reinterpret_cast<Real*>(p + L.off_lam);
     Real* dar = reinterpret_cast<Real*>(p + L.off_harea);
     Real* dgn = reinterpret_cast<Real*>(p + L.off_hgn2);
     const int nh = s_nh[st];
@@ -404,12 +401,13 @@ __global__ void __launch_bounds__(NT)
     const int nh = s_nh[st];
 
     // (A) mu, rho
-    Real mu[CPT][3], bg[CPT];
+    Real mu[CPT][3], bg[CPT], dzr[CPT];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) {
       const int j = tid + cc * NT;
-      const V4<Real> c1 = ld4(su1 + 4 * j);
-      const V4<Real> la = ld4(sla + 4 * j);
+      const V4<Real> c1 = ld4(A.u1 + 4 * (int64_t)(base + j));
+      const V4<Real> la = ld4(A.lam_in + 4 * (int64_t)(base + j));
+      dzr[cc] = la.w;
       cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, A.gn2[base + j], dt, num, mu[cc][0],
                      mu[cc][1], mu[cc][2], bg[cc]);
       const Real a = j < nc ? -O::div(dt, m.area[base + j]) : Real(0);  // padding: area 0
@@ -417,8 +415,8 @@ __global__ void __launch_bounds__(NT)
     }
     for (int q = tid; q < nh; q += NT) {
       const int j = TC + q;
-      const V4<Real> c1 = ld4(su1 + 4 * j);
-      const V4<Real> la = ld4(sla + 4 * j);
+      const V4<Real> c1 = ld4(su1 + 4 * q);
+      const V4<Real> la = ld4(sla + 4 * q);
       Real mh, mx, my, b;
       cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, hgn[q], dt, num, mh, mx, my, b);
       const Real a = -O::div(dt, har[q]);
@@ -463,9 +461,9 @@ __global__ void __launch_bounds__(NT)
       const V4<Real> f0 = ld4(slots + 4 * j);
       const V4<Real> f1 = ld4(slots + 4 * (TC + j));
       const V4<Real> f2 = ld4(slots + 4 * (2 * TC + j));
-      const Real dzr = sla[4 * j + 3];
       st4(A.lam_out + 4 * (int64_t)(base + j), mu[cc][0] + f0.x + f1.x + f2.x,
-          mu[cc][1] + f0.y + f1.y + f2.y, mu[cc][2] + f0.z + f1.z + f2.z, dzr + f0.w + f1.w + f2.w);
+          mu[cc][1] + f0.y + f1.y + f2.y, mu[cc][2] + f0.z + f1.z + f2.z,
+          dzr[cc] + f0.w + f1.w + f2.w);
       A.dgn2[base + j] += bg[cc];
     }
     cp_async_wait_all();

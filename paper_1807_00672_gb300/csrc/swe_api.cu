@@ -63,6 +63,7 @@ namespace {
 
 constexpr int kStepsPerGraph = 16;
 constexpr int kDefaultTile = 256;
+constexpr int64_t kEnsembleWaves = 3;  // waves of work chunks for several scenarios
 
 #define cuda_failed(call) swe_host::cuda_failed_at((call), #call, __FILE__, __LINE__)
 
@@ -420,10 +421,13 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   const size_t w = real_size(m);
   const int geo_arrays = (p.precision == SWE_F64) ? 3 : 2;
 
-  // Work chunks of the tiled kernel, about one per resident block: scenario
-  // s gets ceil(ntiles_s / per) chunks, and its chunk r walks the tiles
-  // r, r + nchunks_s, r + 2 nchunks_s, ... of the scenario.
-  std::vector<int32_t> ch_scen, ch_tile0, ch_ntiles, ch_stride, cell_end;
+  // Work chunks of the tiled kernels (see swe::Chunk). One scenario: one
+  // wave of resident blocks with ceil(ntiles / resident) tiles each. Several
+  // scenarios: about kEnsembleWaves waves; scenario s is split into
+  // ceil(ntiles_s / per) interleaved chunks, and the chunks are launched
+  // largest first so that the block scheduler, which starts blocks in index
+  // order as slots free up, balances the SMs (longest-processing-time order).
+  std::vector<swe::Chunk> chunks;
   if (kernel == SWE_KERNEL_TILED) {
     m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)geo_arrays, (uint32_t)tile,
                                       (uint32_t)m->stages, (uint32_t)rec_cap, (uint32_t)halo_cap);
@@ -434,40 +438,28 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
       swe_mesh_destroy(m);
       return SWE_ECUDA;
     }
-    // Smallest tile count per chunk for which all chunks fit in one wave of
-    // resident blocks (sum over scenarios of ceil(ntiles_s / per) <= resident);
-    // one scenario gives per = ceil(ntiles / resident). With more scenarios
-    // than resident blocks no per fits: one chunk per scenario.
     const int64_t resident = (int64_t)sms * occ;
-    int64_t max_nt = 1;
-    for (int i = 0; i < n; ++i) max_nt = std::max(max_nt, m->scen[i].ntiles);
-    auto fits = [&](int64_t per) {
-      if (per >= max_nt) return true;
-      int64_t c = 0;
-      for (int i = 0; i < n; ++i) c += (m->scen[i].ntiles + per - 1) / per;
-      return c <= resident;
-    };
-    int64_t lo = std::max<int64_t>(1, (tiles + resident - 1) / resident), hi = max_nt;
-    lo = std::min(lo, hi);
-    while (lo < hi) {
-      const int64_t mid = lo + (hi - lo) / 2;
-      if (fits(mid)) hi = mid;
-      else lo = mid + 1;
-    }
-    const int64_t per = lo;
+    const int64_t waves = (n == 1) ? 1 : kEnsembleWaves;
+    const int64_t per = std::max<int64_t>(1, (tiles + resident * waves - 1) / (resident * waves));
     for (int i = 0; i < n; ++i) {
       Scenario& sc = m->scen[i];
-      sc.chunk0 = (int64_t)ch_scen.size();
+      sc.chunk0 = (int64_t)chunks.size();
       sc.nchunks = (sc.ntiles + per - 1) / per;
       for (int64_t r = 0; r < sc.nchunks; ++r) {
-        ch_scen.push_back(i);
-        ch_tile0.push_back((int32_t)(sc.tile0 + r));
-        ch_ntiles.push_back((int32_t)((sc.ntiles - r + sc.nchunks - 1) / sc.nchunks));
-        ch_stride.push_back((int32_t)sc.nchunks);
+        swe::Chunk c{};
+        c.scen = i;
+        c.tile0 = (int32_t)(sc.tile0 + r);
+        c.ntiles = (int32_t)((sc.ntiles - r + sc.nchunks - 1) / sc.nchunks);
+        c.stride = (int32_t)sc.nchunks;
+        c.part = (int32_t)(sc.chunk0 + r);
+        c.cell_end = (int32_t)(sc.cell0 + sc.ncells);
+        chunks.push_back(c);
       }
-      cell_end.push_back((int32_t)(sc.cell0 + sc.ncells));
     }
-    m->nchunks = (int64_t)ch_scen.size();
+    if (n > 1)
+      std::stable_sort(chunks.begin(), chunks.end(),
+                       [](const swe::Chunk& a, const swe::Chunk& b) { return a.ntiles > b.ntiles; });
+    m->nchunks = (int64_t)chunks.size();
   } else {
     if (p.precision == SWE_F64) set_edge_grids<double>(m);
     else set_edge_grids<float>(m);
@@ -490,8 +482,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     L.add(4 * R);
     for (int g = 0; g < geo_arrays; ++g) L.add(w * R);
     L.add(4 * H);
-    L.add(4 * C); L.add(4 * C); L.add(4 * C); L.add(4 * C);
-    L.add(4 * (int64_t)n);
+    L.add(sizeof(swe::Chunk) * C);
   }
   if (cudaMalloc((void**)&m->arena.base, L.total) != cudaSuccess) {
     cudaGetLastError();
@@ -520,11 +511,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     m->tg1 = m->arena.take(w * R);
     if (geo_arrays > 2) m->tg2 = m->arena.take(w * R);
     m->hidx = (int32_t*)m->arena.take(4 * H);
-    m->chunk_scen = (int32_t*)m->arena.take(4 * C);
-    m->chunk_tile0 = (int32_t*)m->arena.take(4 * C);
-    m->chunk_ntiles = (int32_t*)m->arena.take(4 * C);
-    m->chunk_stride = (int32_t*)m->arena.take(4 * C);
-    m->scen_cell_end = (int32_t*)m->arena.take(4 * (int64_t)n);
+    m->chunks = (swe::Chunk*)m->arena.take(sizeof(swe::Chunk) * C);
   }
   if (m->arena.overflow) {
     g_cuda_msg = "mesh arena layout";
@@ -598,11 +585,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     chk(upload_real(m, g1, m->tg1));
     if (geo_arrays > 2) chk(upload_real(m, g2, m->tg2));
     chk(upload(m, hidx, m->hidx));
-    chk(upload(m, ch_scen, m->chunk_scen));
-    chk(upload(m, ch_tile0, m->chunk_tile0));
-    chk(upload(m, ch_ntiles, m->chunk_ntiles));
-    chk(upload(m, ch_stride, m->chunk_stride));
-    chk(upload(m, cell_end, m->scen_cell_end));
+    chk(upload(m, chunks, m->chunks));
   }
   if (st != SWE_OK) {
     swe_mesh_destroy(m);

@@ -5,11 +5,14 @@
 // depths at the gauge cells after every step, and the state every K steps
 // (checkpoints). swe_grad then runs the adjoint backwards through the steps:
 // segment by segment, from the last checkpoint to the first, it recomputes
-// the segment's states from its checkpoint with the forward kernel (the
-// forward is deterministic, so the replay reproduces the recorded states bit
-// for bit; the replay's dt is checked against the recorded one) and applies
-// the tiled adjoint kernel step by step, adding the gauge-loss seeds as it
-// passes their steps. Memory: ceil(n / K) + K + 2 states.
+// the segment's inner states from its checkpoint with the forward kernel
+// (the forward is deterministic, so the replay reproduces the recorded
+// states bit for bit; the replay's dt is checked against the recorded one;
+// the segment's last state is the next checkpoint, or the final state, and
+// is not recomputed) and applies the tiled adjoint kernel step by step,
+// adding the gauge-loss seeds as it passes their steps. Memory: ceil(n / K)
+// + 1 checkpoints, K - 1 replayed states and two adjoint states. K = 1 keeps
+// every state and replays nothing.
 #include <algorithm>
 #include <cmath>
 #include <limits>
@@ -150,8 +153,8 @@ struct swe_tape {
   size_t w = 8;
   int64_t Tp = 0, T = 0;
   Arena arena;
-  char* ck = nullptr;    // nck checkpoints of Tp interleaved cells: U^0, U^K, U^2K, ...
-  char* ring = nullptr;  // K replayed states U^{j0+1} .. U^{j0+K} of one segment
+  char* ck = nullptr;    // nck + 1 states of Tp interleaved cells: U^0, U^K, U^2K, ..., U^N
+  char* ring = nullptr;  // K - 1 replayed states U^{j0+1} .. U^{j0+K-1} of one segment
   char* lam[2] = {nullptr, nullptr};
   void* gn2 = nullptr;   // copy of the state's g n^2
   void* dgn2 = nullptr;
@@ -170,8 +173,11 @@ struct swe_tape {
   cudaEvent_t ev[2] = {nullptr, nullptr};
 
   size_t state_bytes() const { return 4 * w * (size_t)Tp; }
+  int64_t seg_len(int64_t seg) const { return std::min(N, (seg + 1) * K) - seg * K; }
   void* slot(int64_t seg, int64_t r) const {  // state U^{seg K + r} of segment seg
-    return r == 0 ? (void*)(ck + seg * state_bytes()) : (void*)(ring + (r - 1) * state_bytes());
+    if (r == 0) return ck + seg * state_bytes();
+    if (r == seg_len(seg)) return ck + (seg + 1) * state_bytes();
+    return ring + (r - 1) * state_bytes();
   }
 };
 
@@ -220,9 +226,9 @@ swe_status record_t(swe_state* s, swe_tape* t) {
     launch_forward(m, dev_state<Real>(s), st);
     k_record_step<Real><<<1, 128, 0, st>>>(s->ctl, b0, b1, t->dts_dev, k, t->gcells, t->G,
                                            t->gauge_dev);
-    if ((k + 1) % t->K == 0 && k + 1 < t->N)
+    if ((k + 1) % t->K == 0 || k + 1 == t->N)
       k_copy_current<Real><<<gs, 256, 0, st>>>(s->ctl, b0, b1,
-                                               (Real*)(t->ck + ((k + 1) / t->K) * t->state_bytes()),
+                                               (Real*)(t->ck + ((k + t->K) / t->K) * t->state_bytes()),
                                                t->Tp);
   }
   CK(cudaEventRecord(t->ev[1], st));
@@ -242,9 +248,11 @@ swe_status grad_t(swe_tape* t, bool seeds_gauge, int* lam_cur) {
     swe::k_inject_gauges<Real><<<1, 1, 0, st>>>((Real*)t->lam[cur], t->gcells, t->gseed_dev, t->N - 1, t->G);
   for (int64_t seg = t->nck - 1; seg >= 0; --seg) {
     const int64_t j0 = seg * t->K, j1 = std::min(t->N, j0 + t->K);
-    k_replay_begin<<<1, 1, 0, st>>>(t->ctl, t->dts[j0], sc.chunk0, sc.nchunks);
-    for (int64_t r = 0; r < j1 - j0; ++r) launch_forward(m, replay_state<Real>(t, seg, r), st);
-    k_replay_check<<<1, 1, 0, st>>>(t->ctl, t->dts[j1 - 1], t->err);
+    if (j1 - j0 > 1) {  // inner states U^{j0+1} .. U^{j1-1}
+      k_replay_begin<<<1, 1, 0, st>>>(t->ctl, t->dts[j0], sc.chunk0, sc.nchunks);
+      for (int64_t r = 0; r + 1 < j1 - j0; ++r) launch_forward(m, replay_state<Real>(t, seg, r), st);
+      k_replay_check<<<1, 1, 0, st>>>(t->ctl, t->dts[j1 - 2], t->err);
+    }
     for (int64_t j = j1 - 1; j >= j0; --j) {
       const int64_t r = j - j0;
       swe::AdjArgs<Real> a{};
@@ -309,8 +317,8 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   }
   const size_t sb = t->state_bytes();
   Layout L;
-  L.add(sb * t->nck);
-  L.add(sb * t->K);
+  L.add(sb * (t->nck + 1));
+  L.add(sb * std::max<int64_t>(1, t->K - 1));
   L.add(sb); L.add(sb);
   L.add(t->w * t->Tp);  // gn2
   L.add(t->w * t->Tp);  // dgn2
@@ -329,8 +337,8 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
     return SWE_ENOMEM;
   }
   t->arena.size = L.total;
-  t->ck = (char*)t->arena.take(sb * t->nck);
-  t->ring = (char*)t->arena.take(sb * t->K);
+  t->ck = (char*)t->arena.take(sb * (t->nck + 1));
+  t->ring = (char*)t->arena.take(sb * std::max<int64_t>(1, t->K - 1));
   t->lam[0] = (char*)t->arena.take(sb);
   t->lam[1] = (char*)t->arena.take(sb);
   t->gn2 = t->arena.take(t->w * t->Tp);

@@ -78,9 +78,7 @@ struct swe_mesh {
   int64_t *toff = nullptr, *hoff = nullptr;
   int32_t *tS = nullptr, *hidx = nullptr;
   void *tg0 = nullptr, *tg1 = nullptr, *tg2 = nullptr;
-  int32_t *chunk_scen = nullptr, *chunk_tile0 = nullptr, *chunk_ntiles = nullptr;
-  int32_t* chunk_stride = nullptr;
-  int32_t* scen_cell_end = nullptr;
+  swe::Chunk* chunks = nullptr;  // work of each block of the tiled kernels
   int grid_edge = 1, grid_cell = 1, grid_cfl = 1, max_grid = 1;
   // Handles that use this mesh (states). swe_mesh_destroy while some are
   // alive only marks the mesh; the last of them to go frees it.
@@ -127,11 +125,7 @@ swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
   d.cf0 = m->cf[0];
   d.cf1 = m->cf[1];
   d.cf2 = m->cf[2];
-  d.chunk_scen = m->chunk_scen;
-  d.chunk_tile0 = m->chunk_tile0;
-  d.chunk_ntiles = m->chunk_ntiles;
-  d.chunk_stride = m->chunk_stride;
-  d.scen_cell_end = m->scen_cell_end;
+  d.chunks = m->chunks;
   d.ntiles = m->ntiles;
   d.toff = m->toff;
   d.hoff = m->hoff;

@@ -71,6 +71,18 @@ inline Num make_num(double g, double courant, double h_eps) {
   return Num{g, courant, h_eps, f};
 }
 
+// Work of one block of the tiled kernels: the ntiles tiles tile0 + k stride
+// (k = 0, 1, ...) of scenario scen, whose cells end at cell_end. The chunks
+// of one scenario interleave (stride = their count), so the blocks resident
+// at any moment sweep neighbouring tiles together and a tile's halo cells
+// are mostly still in L2 from the neighbours' copies. part: the chunk's
+// mass partial slot (the scenario's slots are contiguous from its
+// control word's part0).
+struct Chunk {
+  int32_t scen, tile0, ntiles, stride;
+  int32_t part, cell_end, pad0, pad1;
+};
+
 template <typename Real>
 struct DevMesh {
   int64_t T;
@@ -87,17 +99,8 @@ struct DevMesh {
   const int32_t* cf0;
   const int32_t* cf1;
   const int32_t* cf2;
-  // tiled layout; work chunks: chunk b walks the chunk_ntiles[b] tiles
-  // chunk_tile0[b] + k chunk_stride[b] (k = 0, 1, ...) of scenario
-  // chunk_scen[b]; the cells of scenario s end at scen_cell_end[s]. The
-  // chunks of one scenario interleave (stride = their count), so the
-  // blocks resident at any moment sweep neighbouring tiles together and a
-  // tile's halo cells are mostly still in L2 from the neighbours' copies.
-  const int32_t* chunk_scen;
-  const int32_t* chunk_tile0;
-  const int32_t* chunk_ntiles;
-  const int32_t* chunk_stride;
-  const int32_t* scen_cell_end;
+  // tiled layout: block b of a launch works chunk chunks[b]
+  const struct Chunk* chunks;
   int64_t ntiles;
   const int64_t* toff;
   const int64_t* hoff;
@@ -715,9 +718,9 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
 }
 
 // ---------------------------------------------------------------------------
-// Tiled one-launch step on interleaved cells (h, hu, hv, z). A persistent
-// block of NT threads walks tiles of TC = NT * CPT consecutive cells
-// (tile = blockIdx.x + k gridDim.x) through NS shared-memory stages:
+// Tiled one-launch step on interleaved cells (h, hu, hv, z). A block of NT
+// threads walks the tiles of its work chunk (TC = NT * CPT consecutive cells
+// each; see Chunk) through NS shared-memory stages:
 //   - thread 0 queues bulk async copies (TMA) of tile k+NS-1's cell arrays,
 //     face records and halo list while the block works on tile k;
 //   - once tile k+1's copies have landed (mid-iteration k), every thread
@@ -748,12 +751,10 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bars);
 
   // This block's work: tiles t_first + k t_step (k < n_tiles) of one scenario.
-  const int scen = m.chunk_scen[blockIdx.x];
-  const int t_first = m.chunk_tile0[blockIdx.x];
-  const int n_tiles = m.chunk_ntiles[blockIdx.x];
-  const int t_step = m.chunk_stride[blockIdx.x];
-  const int cell_end = m.scen_cell_end[scen];
-  Ctl* ctl = s.ctl + scen;
+  const Chunk ch = m.chunks[blockIdx.x];
+  const int t_first = ch.tile0, n_tiles = ch.ntiles, t_step = ch.stride;
+  const int cell_end = ch.cell_end;
+  Ctl* ctl = s.ctl + ch.scen;
   if (ctl->done) return;
   const int cur = ctl->cur;
   const Real dt = Real(ctl->dt);
@@ -929,7 +930,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     for (int i = 0; i < NS; ++i)
       if ((pending >> i) & 1u) mbar_wait(&bar[i], (parity_bits >> i) & 1u);
   }
-  finish_launch<NT>(ctl, s.partial, blockIdx.x, ctl->part0, (int)ctl->nparts, mass.value(),
+  finish_launch<NT>(ctl, s.partial, ch.part, ctl->part0, (int)ctl->nparts, mass.value(),
                     (double)rate, (bad ? kErrNan : 0) | (timeout ? kErrTimeout : 0), neg, true,
                     num.courant);
 }
@@ -968,17 +969,16 @@ template <typename Real>
 __global__ void __launch_bounds__(256) k_cfl_tiled(DevMesh<Real> m, DevState<Real> s, Num num,
                                                    int TC) {
   using O = Ops<Real>;
-  const int scen = m.chunk_scen[blockIdx.x];
-  Ctl* ctl = s.ctl + scen;
+  const Chunk ch = m.chunks[blockIdx.x];
+  Ctl* ctl = s.ctl + ch.scen;
   const int cur = ctl->cur;
   const Real* __restrict__ U = cur ? s.h[1] : s.h[0];
-  const int64_t cell_end = m.scen_cell_end[scen];
-  const int n_tiles = m.chunk_ntiles[blockIdx.x];
+  const int64_t cell_end = ch.cell_end;
   MassAcc<Real> mass;
   Real rate = Real(0);
   int bad = 0;
-  for (int k = 0; k < n_tiles; ++k) {
-    const int64_t c0 = (int64_t)(m.chunk_tile0[blockIdx.x] + k * m.chunk_stride[blockIdx.x]) * TC;
+  for (int k = 0; k < ch.ntiles; ++k) {
+    const int64_t c0 = (int64_t)(ch.tile0 + k * ch.stride) * TC;
     const int64_t c1 = min(c0 + (int64_t)TC, cell_end);
     for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
       const Real hh = U[4 * i], qx = U[4 * i + 1], qy = U[4 * i + 2];
@@ -990,7 +990,7 @@ __global__ void __launch_bounds__(256) k_cfl_tiled(DevMesh<Real> m, DevState<Rea
       mass.add(m.area[i], hh);
     }
   }
-  finish_launch<256>(ctl, s.partial, blockIdx.x, ctl->part0, (int)ctl->nparts, mass.value(),
+  finish_launch<256>(ctl, s.partial, ch.part, ctl->part0, (int)ctl->nparts, mass.value(),
                      (double)rate, bad ? kErrNan : 0, 0, false, num.courant);
 }
 

@@ -307,6 +307,18 @@ def ensemble_cases(n_scen: int = 256, *, t_min: int = 5_000, t_max: int = 500_00
     return out
 
 
+def gauge_cells(case: Case, count: int = 64, seed: int = 5) -> np.ndarray:
+    """Gauge cells sampled without replacement (seeded)."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(case.mesh.n_tris, size=count, replace=False)).astype(np.int32)
+
+
+def perturbed_manning(case: Case, rel: float = 0.1, seed: int = 5) -> np.ndarray:
+    """Target roughness of the calibration workload: n (1 + rel xi), xi ~ N(0, 1)."""
+    rng = np.random.default_rng(seed + 17)
+    return case.n * (1.0 + rel * rng.standard_normal(case.mesh.n_tris))
+
+
 # The five workloads the benchmark and the parity tests are built on.
 CONFIGS = {
     "stoker_2500": dict(fn=stoker_case, kw={}, steps=None, t_end=2.0, prec="f64"),
