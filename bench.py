@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--adjoint-steps", type=int, default=500)
     ap.add_argument("--adjoint-checkpoint", type=int, default=50)
+    ap.add_argument("--no-water-drop", action="store_true", help="skip the water-drop leg")
+    ap.add_argument("--water-drop-test", type=int, default=4, help="Table 2 grid size (1-5)")
     ap.add_argument("--ref-cells", type=int, default=25_000)
     ap.add_argument("--cpu-cells", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=150)
@@ -338,6 +340,8 @@ def main():
         out["ensemble"] = ensemble_leg(args, stream)
     if rank == 0 and not args.no_extras and not args.no_adjoint:
         out["adjoint"] = adjoint_leg(args, stream)
+    if rank == 0 and not args.no_extras and not args.no_water_drop:
+        out["water_drop"] = water_drop_leg(args, stream)
     st.close()
     mesh.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -470,7 +474,7 @@ def adjoint_leg(args, stream):
     from paper_1807_00672_gb300 import inputs, swe
     N, K = args.adjoint_steps, args.adjoint_checkpoint
     case = inputs.make_config("calibration_1m")
-    gauges = inputs.gauge_cells(case, 64, seed=5)
+    gauges = inputs.gauge_cells(case, 64, seed=5, radius=1_500.0)
     n_obs = inputs.perturbed_manning(case, seed=5)
     res = {"workload": "calibration_1m", "triangles": case.mesh.n_tris, "steps": N,
            "checkpoint_every": K, "gauges": int(gauges.shape[0])}
@@ -526,6 +530,40 @@ def adjoint_leg(args, stream):
     res["note"] = ("backward = recompute of each checkpoint segment's inner steps with the forward "
                    "kernel + one adjoint launch per step; adjoint step time estimated as (backward - "
                    "recomputed steps x forward step) / steps")
+    return res
+
+
+def water_drop_leg(args, stream):
+    """The paper's water drop (Sec. 3) to its longest end time T_s = 2,400 s
+    on the grid of Table 2's test --water-drop-test (4: 1,057,058 triangles),
+    FP32 and FP64, through swe_advance (graph-replayed steps, exact end
+    time): steps, wall time, cell-updates/s, mass drift, and the FP32 free
+    surface's L1 / Linf distance to the FP64 one at T_s."""
+    import torch
+    from paper_1807_00672_gb300 import inputs, swe
+    n = inputs.WATER_DROP_N[args.water_drop_test]
+    case = inputs.water_drop_case(n)
+    res = {"table2_test": args.water_drop_test, "triangles": case.mesh.n_tris, "t_end": 2400.0}
+    fields = {}
+    for prec in ("f32", "f64"):
+        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=prec, stream=ctypes_stream(stream))
+        st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+        m0 = st.mass
+        st.run(16)  # capture the step graph
+        st.set(case.h, case.hu, case.hv)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = st.advance(2400.0)
+        secs = time.perf_counter() - t0
+        h, _, _ = st.fields()
+        fields[prec] = h
+        res[prec] = {"steps": k, "seconds": secs, "value": mesh.T * k / secs, "unit": UNIT,
+                     "t": st.t, "mass_rel_drift": abs(st.mass - m0) / m0}
+        st.close()
+        mesh.close()
+    eta32, eta64 = fields["f32"] - 10.0, fields["f64"] - 10.0
+    res["f32_vs_f64_linf_eta"] = float(np.abs(eta32 - eta64).max() / np.abs(eta64).max())
+    res["f32_vs_f64_l1_eta"] = float(np.abs(eta32 - eta64).sum() / np.abs(eta64).sum())
     return res
 
 

@@ -218,7 +218,7 @@ typedef struct swe_tape swe_tape;
  * gauge_cells[j] (caller indices, repeats allowed) after every step into
  * gauge_h[k * n_gauges + j] for step k = 0 .. n_steps-1 (host, may be NULL),
  * and the state every checkpoint_every steps (device memory: about
- * ceil(n_steps / K) + K + 2 states, K = checkpoint_every; K = 1 keeps every
+ * ceil(n_steps / K) + 2K + 1 states, K = checkpoint_every; K = 1 keeps every
  * state and swe_grad then recomputes nothing). The state is
  * left at step n_steps. Synchronises. Returns SWE_ENAN / SWE_EDRY if a step
  * fails (no tape is made). The tape holds the mesh (not the state). */

@@ -234,6 +234,14 @@ struct AdjArgs {
   Real* dgn2;          // accumulated dL/d(g n^2) per cell (read-modify-write)
   Real dt;
   int* err;            // kErr* bits (timeouts)
+  // Gauge seeds added to the depth adjoint of lam_out once every block is
+  // done (by the last block): lam_out[4 gcells[j]] += gseed[gstep G + j],
+  // j < G; gstep < 0 adds nothing. ticket: a zeroed counter.
+  const int32_t* gcells;
+  const double* gseed;
+  int G;
+  long long gstep;
+  unsigned int* ticket;
 };
 
 // Shared-memory plan of k_tiled_adjoint. Per stage: the tile's and its
@@ -364,12 +372,29 @@ __global__ void __launch_bounds__(NT)
     }
   };
 
+  // Per-cell inputs of the thread's own cells, loaded one tile ahead into
+  // registers (their latency hides behind the previous tile's face loop).
+  V4<Real> nu1[CPT], nla[CPT];
+  Real ngn[CPT], nar[CPT], ndg[CPT];
+  auto load_cells = [&](int t) {
+    const int64_t b0 = (int64_t)t * TC;
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      const int64_t i = b0 + tid + cc * NT;
+      nu1[cc] = ld4(A.u1 + 4 * i);
+      nla[cc] = ld4(A.lam_in + 4 * i);
+      ngn[cc] = A.gn2[i];
+      nar[cc] = m.area[i];
+      ndg[cc] = A.dgn2[i];
+    }
+  };
   int timeout = 0;
   if (tid == 0) {
 #pragma unroll
     for (int i = 0; i < NS - 1; ++i)
       if (i < n_tiles) issue(i, t_first + i * t_step);
   }
+  if (n_tiles > 0) load_cells(t_first);
   if (n_tiles > 0) {
     const bool ok = (tid == 0) ? wait_stage(0) : true;
     if (__syncthreads_or(!ok)) {
@@ -405,14 +430,16 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) {
       const int j = tid + cc * NT;
-      const V4<Real> c1 = ld4(A.u1 + 4 * (int64_t)(base + j));
-      const V4<Real> la = ld4(A.lam_in + 4 * (int64_t)(base + j));
+      const V4<Real> c1 = nu1[cc];
+      const V4<Real> la = nla[cc];
       dzr[cc] = la.w;
-      cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, A.gn2[base + j], dt, num, mu[cc][0],
-                     mu[cc][1], mu[cc][2], bg[cc]);
-      const Real a = j < nc ? -O::div(dt, m.area[base + j]) : Real(0);  // padding: area 0
+      cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, ngn[cc], dt, num, mu[cc][0], mu[cc][1],
+                     mu[cc][2], bg[cc]);
+      bg[cc] += ndg[cc];
+      const Real a = j < nc ? -O::div(dt, nar[cc]) : Real(0);  // padding: area 0
       st4(rho + 4 * j, a * mu[cc][0], a * mu[cc][1], a * mu[cc][2], Real(0));
     }
+    if (has_next) load_cells(tile + t_step);
     for (int q = tid; q < nh; q += NT) {
       const int j = TC + q;
       const V4<Real> c1 = ld4(su1 + 4 * q);
@@ -464,7 +491,7 @@ __global__ void __launch_bounds__(NT)
       st4(A.lam_out + 4 * (int64_t)(base + j), mu[cc][0] + f0.x + f1.x + f2.x,
           mu[cc][1] + f0.y + f1.y + f2.y, mu[cc][2] + f0.z + f1.z + f2.z,
           dzr[cc] + f0.w + f1.w + f2.w);
-      A.dgn2[base + j] += bg[cc];
+      A.dgn2[base + j] = bg[cc];
     }
     cp_async_wait_all();
     __syncthreads();
@@ -474,6 +501,23 @@ __global__ void __launch_bounds__(NT)
     for (int i = 0; i < NS; ++i)
       if ((pending >> i) & 1u) mbar_wait(&bar[i], (parity_bits >> i) & 1u);
     atomicOr(A.err, kErrTimeout);
+  }
+  // The last block to finish adds the gauge seeds (one thread, fixed order,
+  // so repeated gauge cells add up deterministically).
+  if (A.gstep >= 0) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      s_last = atomicAdd(A.ticket, 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (s_last && tid == 0) {
+      __threadfence();
+      for (int j = 0; j < A.G; ++j)
+        A.lam_out[4 * (int64_t)A.gcells[j]] += Real(A.gseed[A.gstep * A.G + j]);
+      *A.ticket = 0u;
+    }
   }
 }
 

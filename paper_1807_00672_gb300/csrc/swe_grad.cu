@@ -10,9 +10,11 @@
 // states bit for bit; the replay's dt is checked against the recorded one;
 // the segment's last state is the next checkpoint, or the final state, and
 // is not recomputed) and applies the tiled adjoint kernel step by step,
-// adding the gauge-loss seeds as it passes their steps. Memory: ceil(n / K)
-// + 1 checkpoints, K - 1 replayed states and two adjoint states. K = 1 keeps
-// every state and replays nothing.
+// adding the gauge-loss seeds as it passes their steps. The replay of the
+// next segment runs on a second stream while the current segment's adjoint
+// steps run, each into its own ring of states. Memory: ceil(n / K) + 1
+// checkpoints, 2 (K - 1) replayed states and two adjoint states. K = 1
+// keeps every state and replays nothing.
 #include <algorithm>
 #include <cmath>
 #include <limits>
@@ -85,27 +87,29 @@ __global__ void k_finish_dn(const Real* dgn2, const Real* gn2, double g, Real* o
 }
 
 template <typename Real, int NT, int CPT>
-void launch_adjoint_nt(const swe_mesh* m, const swe::AdjArgs<Real>& a, const swe::AdjLayout& L,
-                       int grid, cudaStream_t st) {
-  swe::k_tiled_adjoint<Real, NT, 2, CPT><<<grid, NT, L.total, st>>>(dev_mesh<Real>(m), a, num_of(m), L);
+void launch_adjoint_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::AdjArgs<Real>& a,
+                       const swe::AdjLayout& L, int grid, cudaStream_t st) {
+  swe::k_tiled_adjoint<Real, NT, 2, CPT><<<grid, NT, L.total, st>>>(dm, a, num_of(m), L);
 }
 
 template <typename Real, int CPT>
-void launch_adjoint_cpt(const swe_mesh* m, const swe::AdjArgs<Real>& a, const swe::AdjLayout& L,
-                        int grid, cudaStream_t st) {
+void launch_adjoint_cpt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::AdjArgs<Real>& a,
+                        const swe::AdjLayout& L, int grid, cudaStream_t st) {
   switch (m->tile / CPT) {
-    case 64: launch_adjoint_nt<Real, 64, CPT>(m, a, L, grid, st); break;
-    case 128: launch_adjoint_nt<Real, 128, CPT>(m, a, L, grid, st); break;
-    default: launch_adjoint_nt<Real, 256, CPT>(m, a, L, grid, st); break;
+    case 64: launch_adjoint_nt<Real, 64, CPT>(m, dm, a, L, grid, st); break;
+    case 128: launch_adjoint_nt<Real, 128, CPT>(m, dm, a, L, grid, st); break;
+    default: launch_adjoint_nt<Real, 256, CPT>(m, dm, a, L, grid, st); break;
   }
 }
 
+// The adjoint runs on its own chunk table (one wave at its own occupancy).
 template <typename Real>
-void launch_adjoint(const swe_mesh* m, const swe::AdjArgs<Real>& a, const swe::AdjLayout& L,
-                    cudaStream_t st) {
-  const int grid = (int)m->nchunks;
-  if (m->cpt == 2) launch_adjoint_cpt<Real, 2>(m, a, L, grid, st);
-  else launch_adjoint_cpt<Real, 1>(m, a, L, grid, st);
+void launch_adjoint(const swe_mesh* m, const swe::Chunk* chunks, int grid,
+                    const swe::AdjArgs<Real>& a, const swe::AdjLayout& L, cudaStream_t st) {
+  swe::DevMesh<Real> dm = dev_mesh<Real>(m);
+  dm.chunks = chunks;
+  if (m->cpt == 2) launch_adjoint_cpt<Real, 2>(m, dm, a, L, grid, st);
+  else launch_adjoint_cpt<Real, 1>(m, dm, a, L, grid, st);
 }
 
 // Opts the adjoint kernel into its shared memory; resident blocks per SM.
@@ -154,7 +158,12 @@ struct swe_tape {
   int64_t Tp = 0, T = 0;
   Arena arena;
   char* ck = nullptr;    // nck + 1 states of Tp interleaved cells: U^0, U^K, U^2K, ..., U^N
-  char* ring = nullptr;  // K - 1 replayed states U^{j0+1} .. U^{j0+K-1} of one segment
+  // Two rings of K - 1 replayed states U^{j0+1} .. U^{j0+K-1}: segment seg
+  // uses ring seg % 2, so the replay of the next segment (on the side
+  // stream) overlaps the adjoint steps of the current one.
+  char* ring[2] = {nullptr, nullptr};
+  cudaStream_t side = nullptr;
+  cudaEvent_t replayed[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
   char* lam[2] = {nullptr, nullptr};
   void* gn2 = nullptr;   // copy of the state's g n^2
   void* dgn2 = nullptr;
@@ -164,9 +173,12 @@ struct swe_tape {
   double* gauge_dev = nullptr;
   double* gseed_dev = nullptr;
   int32_t* gcells = nullptr;
-  swe::Ctl* ctl = nullptr;
-  double* partial = nullptr;
+  swe::Chunk* chunks = nullptr;  // work of the adjoint kernel's blocks
+  int64_t nchunks = 0;
+  swe::Ctl* ctl = nullptr;      // two replay control words (one per ring)
+  double* partial = nullptr;    // two arrays of per-chunk mass partials
   int* err = nullptr;
+  unsigned int* ticket = nullptr;
   std::vector<double> dts;
   swe::AdjLayout adj{};
   float record_ms = 0.f, grad_ms = 0.f;
@@ -177,7 +189,7 @@ struct swe_tape {
   void* slot(int64_t seg, int64_t r) const {  // state U^{seg K + r} of segment seg
     if (r == 0) return ck + seg * state_bytes();
     if (r == seg_len(seg)) return ck + (seg + 1) * state_bytes();
-    return ring + (r - 1) * state_bytes();
+    return ring[seg % 2] + (r - 1) * state_bytes();
   }
 };
 
@@ -185,8 +197,14 @@ namespace {
 
 void free_tape(swe_tape* t) {
   if (t->mesh && t->stream) cudaStreamSynchronize(t->stream);
+  if (t->side) cudaStreamSynchronize(t->side);
   for (auto& e : t->ev)
     if (e) cudaEventDestroy(e);
+  for (int i = 0; i < 2; ++i) {
+    if (t->replayed[i]) cudaEventDestroy(t->replayed[i]);
+    if (t->consumed[i]) cudaEventDestroy(t->consumed[i]);
+  }
+  if (t->side) cudaStreamDestroy(t->side);
   if (t->arena.base) cudaFree(t->arena.base);
   swe_mesh* m = t->mesh;
   delete t;
@@ -207,8 +225,8 @@ swe::DevState<Real> replay_state(const swe_tape* t, int64_t seg, int64_t r) {
   d.stride = 4;
   d.z = b0 + 3;
   d.gn2 = (const Real*)t->gn2;
-  d.partial = t->partial;
-  d.ctl = t->ctl;
+  d.partial = t->partial + (seg % 2) * std::max<int64_t>(1, t->mesh->nchunks);
+  d.ctl = t->ctl + seg % 2;
   return d;
 }
 
@@ -238,21 +256,43 @@ swe_status record_t(swe_state* s, swe_tape* t) {
   return SWE_OK;
 }
 
+// Recomputes the inner states U^{j0+1} .. U^{j1-1} of segment seg into its
+// ring, on stream st.
+template <typename Real>
+void replay_segment(swe_tape* t, int64_t seg, cudaStream_t st) {
+  const swe_mesh* m = t->mesh;
+  const Scenario& sc = m->scen[0];
+  const int64_t j0 = seg * t->K, j1 = std::min(t->N, j0 + t->K);
+  if (j1 - j0 <= 1) return;
+  swe::Ctl* ctl = t->ctl + seg % 2;
+  k_replay_begin<<<1, 1, 0, st>>>(ctl, t->dts[j0], sc.chunk0, sc.nchunks);
+  for (int64_t r = 0; r + 1 < j1 - j0; ++r) launch_forward(m, replay_state<Real>(t, seg, r), st);
+  k_replay_check<<<1, 1, 0, st>>>(ctl, t->dts[j1 - 2], t->err);
+}
+
 template <typename Real>
 swe_status grad_t(swe_tape* t, bool seeds_gauge, int* lam_cur) {
   swe_mesh* m = t->mesh;
   cudaStream_t st = m->stream;
-  const Scenario& sc = m->scen[0];
   int cur = 0;
   if (seeds_gauge)
     swe::k_inject_gauges<Real><<<1, 1, 0, st>>>((Real*)t->lam[cur], t->gcells, t->gseed_dev, t->N - 1, t->G);
+  // Replays run one segment ahead on the side stream: segment seg - 1's
+  // replay (ring (seg - 1) % 2) overlaps segment seg's adjoint steps; it
+  // first waits for the adjoint of segment seg + 1, the ring's last user.
+  CK(cudaEventRecord(t->consumed[0], st));
+  CK(cudaEventRecord(t->consumed[1], st));
+  CK(cudaStreamWaitEvent(t->side, t->consumed[0], 0));
+  replay_segment<Real>(t, t->nck - 1, t->side);
+  CK(cudaEventRecord(t->replayed[(t->nck - 1) % 2], t->side));
   for (int64_t seg = t->nck - 1; seg >= 0; --seg) {
     const int64_t j0 = seg * t->K, j1 = std::min(t->N, j0 + t->K);
-    if (j1 - j0 > 1) {  // inner states U^{j0+1} .. U^{j1-1}
-      k_replay_begin<<<1, 1, 0, st>>>(t->ctl, t->dts[j0], sc.chunk0, sc.nchunks);
-      for (int64_t r = 0; r + 1 < j1 - j0; ++r) launch_forward(m, replay_state<Real>(t, seg, r), st);
-      k_replay_check<<<1, 1, 0, st>>>(t->ctl, t->dts[j1 - 2], t->err);
+    if (seg >= 1) {
+      CK(cudaStreamWaitEvent(t->side, t->consumed[(seg - 1) % 2], 0));
+      replay_segment<Real>(t, seg - 1, t->side);
+      CK(cudaEventRecord(t->replayed[(seg - 1) % 2], t->side));
     }
+    CK(cudaStreamWaitEvent(st, t->replayed[seg % 2], 0));
     for (int64_t j = j1 - 1; j >= j0; --j) {
       const int64_t r = j - j0;
       swe::AdjArgs<Real> a{};
@@ -264,11 +304,15 @@ swe_status grad_t(swe_tape* t, bool seeds_gauge, int* lam_cur) {
       a.dgn2 = (Real*)t->dgn2;
       a.dt = Real(t->dts[j]);
       a.err = t->err;
-      launch_adjoint<Real>(m, a, t->adj, st);
+      a.gcells = t->gcells;
+      a.gseed = t->gseed_dev;
+      a.G = t->G;
+      a.gstep = (seeds_gauge && j >= 1) ? (long long)(j - 1) : -1ll;  // lambda^j gets dL/dh^j
+      a.ticket = t->ticket;
+      launch_adjoint<Real>(m, t->chunks, (int)t->nchunks, a, t->adj, st);
       cur ^= 1;
-      if (seeds_gauge && j >= 1)
-        swe::k_inject_gauges<Real><<<1, 1, 0, st>>>((Real*)t->lam[cur], t->gcells, t->gseed_dev, j - 1, t->G);
     }
+    CK(cudaEventRecord(t->consumed[seg % 2], st));
   }
   CK(cudaGetLastError());
   *lam_cur = cur;
@@ -315,9 +359,29 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
     free_tape(t);
     return SWE_ECUDA;
   }
+  // adjoint chunk table: one wave of resident blocks over the scenario's tiles
+  std::vector<swe::Chunk> chunks;
+  {
+    const Scenario& sc = m->scen[0];
+    const int64_t resident = (int64_t)m->sms * occ;
+    const int64_t per = std::max<int64_t>(1, (sc.ntiles + resident - 1) / resident);
+    const int64_t nc = (sc.ntiles + per - 1) / per;
+    for (int64_t r = 0; r < nc; ++r) {
+      swe::Chunk c{};
+      c.scen = 0;
+      c.tile0 = (int32_t)(sc.tile0 + r);
+      c.ntiles = (int32_t)((sc.ntiles - r + nc - 1) / nc);
+      c.stride = (int32_t)nc;
+      c.part = (int32_t)r;
+      c.cell_end = (int32_t)(sc.cell0 + sc.ncells);
+      chunks.push_back(c);
+    }
+    t->nchunks = nc;
+  }
   const size_t sb = t->state_bytes();
   Layout L;
   L.add(sb * (t->nck + 1));
+  L.add(sb * std::max<int64_t>(1, t->K - 1));
   L.add(sb * std::max<int64_t>(1, t->K - 1));
   L.add(sb); L.add(sb);
   L.add(t->w * t->Tp);  // gn2
@@ -328,9 +392,11 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   L.add(8 * t->N * std::max(1, t->G));  // gauge depths
   L.add(8 * t->N * std::max(1, t->G));  // gauge seeds
   L.add(4 * std::max(1, t->G));
-  L.add(sizeof(swe::Ctl));
-  L.add(8 * (size_t)std::max<int64_t>(1, m->nchunks));
+  L.add(sizeof(swe::Chunk) * chunks.size());
+  L.add(2 * sizeof(swe::Ctl));
+  L.add(2 * 8 * (size_t)std::max<int64_t>(1, m->nchunks));
   L.add(sizeof(int));
+  L.add(sizeof(unsigned int));
   if (cudaMalloc((void**)&t->arena.base, L.total) != cudaSuccess) {
     cudaGetLastError();
     free_tape(t);
@@ -338,7 +404,8 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   }
   t->arena.size = L.total;
   t->ck = (char*)t->arena.take(sb * (t->nck + 1));
-  t->ring = (char*)t->arena.take(sb * std::max<int64_t>(1, t->K - 1));
+  t->ring[0] = (char*)t->arena.take(sb * std::max<int64_t>(1, t->K - 1));
+  t->ring[1] = (char*)t->arena.take(sb * std::max<int64_t>(1, t->K - 1));
   t->lam[0] = (char*)t->arena.take(sb);
   t->lam[1] = (char*)t->arena.take(sb);
   t->gn2 = t->arena.take(t->w * t->Tp);
@@ -349,9 +416,11 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   t->gauge_dev = (double*)t->arena.take(8 * t->N * std::max(1, t->G));
   t->gseed_dev = (double*)t->arena.take(8 * t->N * std::max(1, t->G));
   t->gcells = (int32_t*)t->arena.take(4 * std::max(1, t->G));
-  t->ctl = (swe::Ctl*)t->arena.take(sizeof(swe::Ctl));
-  t->partial = (double*)t->arena.take(8 * (size_t)std::max<int64_t>(1, m->nchunks));
+  t->chunks = (swe::Chunk*)t->arena.take(sizeof(swe::Chunk) * chunks.size());
+  t->ctl = (swe::Ctl*)t->arena.take(2 * sizeof(swe::Ctl));
+  t->partial = (double*)t->arena.take(2 * 8 * (size_t)std::max<int64_t>(1, m->nchunks));
   t->err = (int*)t->arena.take(sizeof(int));
+  t->ticket = (unsigned int*)t->arena.take(sizeof(unsigned int));
   if (t->arena.overflow) {
     g_cuda_msg = "tape arena layout";
     free_tape(t);
@@ -359,7 +428,16 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   }
   auto fail = [&](swe_status r) { free_tape(t); return r; };
   if (cuda_failed(cudaMemsetAsync(t->arena.base, 0, L.total, m->stream)) ||
-      cuda_failed(cudaEventCreate(&t->ev[0])) || cuda_failed(cudaEventCreate(&t->ev[1])))
+      cuda_failed(cudaEventCreate(&t->ev[0])) || cuda_failed(cudaEventCreate(&t->ev[1])) ||
+      cuda_failed(cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking)))
+    return fail(SWE_ECUDA);
+  for (int i = 0; i < 2; ++i)
+    if (cuda_failed(cudaEventCreateWithFlags(&t->replayed[i], cudaEventDisableTiming)) ||
+        cuda_failed(cudaEventCreateWithFlags(&t->consumed[i], cudaEventDisableTiming)))
+      return fail(SWE_ECUDA);
+  if (cuda_failed(cudaMemcpyAsync(t->chunks, chunks.data(), sizeof(swe::Chunk) * chunks.size(),
+                                  cudaMemcpyHostToDevice, m->stream)) ||
+      cuda_failed(cudaStreamSynchronize(m->stream)))
     return fail(SWE_ECUDA);
   // gauge cells in internal order
   if (t->G > 0) {
@@ -408,6 +486,7 @@ swe_status swe_grad(swe_tape* t, const double* g_h, const double* g_hu, const do
   CK(cudaMemsetAsync(t->lam[1], 0, sb, st));
   CK(cudaMemsetAsync(t->dgn2, 0, t->w * t->Tp, st));
   CK(cudaMemsetAsync(t->err, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(t->ticket, 0, sizeof(unsigned int), st));
   const double* seeds[3] = {g_h, g_hu, g_hv};
   for (int c = 0; c < 3; ++c) {
     if (!seeds[c]) continue;

@@ -32,6 +32,10 @@ __all__ = [
     "uniform_flow_case",
     "random_flow_case",
     "ensemble_cases",
+    "water_drop_case",
+    "three_mounds_case",
+    "gauge_cells",
+    "perturbed_manning",
     "CONFIGS",
     "make_config",
 ]
@@ -76,7 +80,8 @@ def jittered_grid(nx: int, ny: int, lx: float, ly: float, *, jitter: float = 0.0
     Interior nodes move by U(-jitter, +jitter) cell widths in x and y (the
     boundary stays a rectangle). Each quad is cut along one diagonal:
     ``"random"`` picks it by a seeded coin, ``"shorter"`` takes the shorter
-    diagonal of the (jittered) quad, ties broken by the coin.
+    diagonal of the (jittered) quad, ties broken by the coin, ``"ac"`` cuts
+    every quad from its lower-left to its upper-right node.
     Counts: V = (nx+1)(ny+1), T = 2 nx ny.
     """
     if nx < 1 or ny < 1:
@@ -104,6 +109,8 @@ def jittered_grid(nx: int, ny: int, lx: float, ly: float, *, jitter: float = 0.0
     coin = rng.integers(0, 2, size=a.shape[0]).astype(bool)
     if diagonal == "random":
         use_ac = coin
+    elif diagonal == "ac":  # every quad cut the same way: point-symmetric about the centre
+        use_ac = np.ones(a.shape[0], dtype=bool)
     elif diagonal == "shorter":
         lac = np.sum((xy[a] - xy[c]) ** 2, axis=1)
         lbd = np.sum((xy[b] - xy[d]) ** 2, axis=1)
@@ -307,10 +314,64 @@ def ensemble_cases(n_scen: int = 256, *, t_min: int = 5_000, t_max: int = 500_00
     return out
 
 
-def gauge_cells(case: Case, count: int = 64, seed: int = 5) -> np.ndarray:
-    """Gauge cells sampled without replacement (seeded)."""
+# Quads per side of the water-drop meshes whose 2 n^2 triangles approximate
+# the paper's test grids 1-5 (Table 2: 1,036 to 10,261,932 triangles).
+WATER_DROP_N = {1: 23, 2: 71, 3: 229, 4: 727, 5: 2265}
+
+
+def water_drop_case(n: int = 71, *, l: float = 10_000.0, h0: float = 10.0, amp: float = 1.0,
+                    sigma: float = 500.0, jitter: float = 0.15, diagonal: str = "shorter",
+                    manning: float = 0.0, seed: int = 21) -> Case:
+    """The paper's water drop (Sec. 3): water at rest in a square basin closed
+    by walls, with a Gaussian hump of the free surface at the centre; the
+    paper runs it to T_s = 2,400 s. Its parameters are not printed; these are
+    project choices: a 10 km square, 10 m deep, a 1 m hump of width sigma =
+    500 m, flat bed, no friction, an n x n jittered grid (T = 2 n^2; see
+    WATER_DROP_N for the Table 2 sizes)."""
+    m = jittered_grid(n, n, l, l, jitter=jitter, diagonal=diagonal, seed=seed)
+    c = centroids(m)
+    r2 = (c[:, 0] - 0.5 * l) ** 2 + (c[:, 1] - 0.5 * l) ** 2
+    h = h0 + amp * np.exp(-r2 / (2.0 * sigma * sigma))
+    t = m.n_tris
+    return Case(m, h, _zeros(t), _zeros(t), _zeros(t), np.full(t, manning), name="water_drop",
+                meta=dict(n=n, l=l, h0=h0, amp=amp, sigma=sigma, seed=seed))
+
+
+# Three conical mounds (x, y, height, base radius) of the three-mound case.
+THREE_MOUNDS = ((32.0, 8.0, 1.2, 9.0), (32.0, 24.0, 1.2, 9.0), (52.0, 16.0, 2.8, 11.0))
+
+
+def three_mounds_case(nx: int = 160, ny: int = 64, *, lx: float = 80.0, ly: float = 32.0,
+                      x_dam: float = 18.0, h_up: float = 2.0, mounds=THREE_MOUNDS,
+                      manning: float = 0.02, jitter: float = 0.3, seed: int = 31) -> Case:
+    """A dam break over three mounds onto a dry bed, with wetting and drying
+    (the paper's three-mound case, Sec. 2.3 and Fig. 4, whose parameters it
+    does not print; these are project choices): an 80 m x 32 m basin closed
+    by walls, still water 2 m deep behind a dam at x = 18 m, a dry bed beyond
+    it carrying two 1.2 m cones and one 2.8 m cone, Manning n = 0.02."""
+    m = jittered_grid(nx, ny, lx, ly, jitter=jitter, diagonal="shorter", seed=seed)
+    c = centroids(m)
+    z = np.zeros(m.n_tris)
+    for (mx, my, height, radius) in mounds:
+        d = np.hypot(c[:, 0] - mx, c[:, 1] - my)
+        z = np.maximum(z, height * np.maximum(0.0, 1.0 - d / radius))
+    h = np.where(c[:, 0] < x_dam, np.maximum(0.0, h_up - z), 0.0)
+    t = m.n_tris
+    return Case(m, h, _zeros(t), _zeros(t), z, np.full(t, manning), name="three_mounds",
+                meta=dict(x_dam=x_dam, h_up=h_up, manning=manning, seed=seed))
+
+
+def gauge_cells(case: Case, count: int = 64, seed: int = 5, radius: float | None = None) -> np.ndarray:
+    """Gauge cells sampled without replacement (seeded), from the cells whose
+    centroid lies within ``radius`` of the domain centre if given (so that
+    the gauges see the flow within the run)."""
     rng = np.random.default_rng(seed)
-    return np.sort(rng.choice(case.mesh.n_tris, size=count, replace=False)).astype(np.int32)
+    pool = np.arange(case.mesh.n_tris)
+    if radius is not None:
+        c = centroids(case.mesh)
+        lx, ly = case.mesh.lx, case.mesh.ly
+        pool = pool[np.hypot(c[:, 0] - 0.5 * lx, c[:, 1] - 0.5 * ly) <= radius]
+    return np.sort(rng.choice(pool, size=count, replace=False)).astype(np.int32)
 
 
 def perturbed_manning(case: Case, rel: float = 0.1, seed: int = 5) -> np.ndarray:
