@@ -210,6 +210,9 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=500)
     ap.add_argument("--adjoint-checkpoint", type=int, default=50)
     ap.add_argument("--no-water-drop", action="store_true", help="skip the water-drop leg")
+    ap.add_argument("--adjoint-profile", action="store_true",
+                    help="only record 4 steps of the workload and run one gradient (a short "
+                         "command to profile the adjoint kernel under ncu); prints the tape info")
     ap.add_argument("--water-drop-test", type=int, default=4, help="Table 2 grid size (1-5)")
     ap.add_argument("--ref-cells", type=int, default=25_000)
     ap.add_argument("--cpu-cells", type=int, default=1_000_000)
@@ -238,6 +241,14 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
 
     case = make_case(args.workload)
+    if args.adjoint_profile:
+        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=args.precision)
+        st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+        tape = swe.Tape(st, 4, 4, [5, 100])
+        r = tape.grad(g_h=np.random.default_rng(0).standard_normal(mesh.T))
+        print(json.dumps({"adjoint_profile": tape.info(),
+                          "finite": bool(all(np.isfinite(v).all() for v in r.values()))}))
+        return
     stream = torch.cuda.Stream(device=dev)
     mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=args.precision, kernel=args.kernel,
                     tile=args.tile, stages=args.stages, cells_per_thread=args.cpt,
