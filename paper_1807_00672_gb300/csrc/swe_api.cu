@@ -111,6 +111,7 @@ int blocks_per_sm_tiled_nt(const swe_mesh* m) {
 template <typename Real, int CPT>
 int blocks_per_sm_tiled_cpt(const swe_mesh* m) {
   switch (m->tile / CPT) {
+    case 32: return blocks_per_sm_tiled_nt<Real, 32, CPT>(m);
     case 64: return blocks_per_sm_tiled_nt<Real, 64, CPT>(m);
     case 128: return blocks_per_sm_tiled_nt<Real, 128, CPT>(m);
     default: return blocks_per_sm_tiled_nt<Real, 256, CPT>(m);
@@ -137,6 +138,7 @@ template <typename Real, bool Comp, int CPT>
 void launch_tiled_cpt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::DevState<Real>& ds,
                       const swe::Num& num, cudaStream_t st) {
   switch (m->tile / CPT) {
+    case 32: launch_tiled_nt<Real, Comp, 32, CPT>(m, dm, ds, num, st); break;
     case 64: launch_tiled_nt<Real, Comp, 64, CPT>(m, dm, ds, num, st); break;
     case 128: launch_tiled_nt<Real, Comp, 128, CPT>(m, dm, ds, num, st); break;
     default: launch_tiled_nt<Real, Comp, 256, CPT>(m, dm, ds, num, st); break;
@@ -317,7 +319,7 @@ swe_status resolve_params(const swe_params* params, swe_params& p) {
   if (p.cells_per_thread == 0) p.cells_per_thread = 2;
   if (p.cells_per_thread != 1 && p.cells_per_thread != 2) return SWE_EINVAL;
   const int nt = p.tile / p.cells_per_thread;
-  if (p.tile % p.cells_per_thread != 0 || (nt != 64 && nt != 128 && nt != 256)) return SWE_EINVAL;
+  if (p.tile % p.cells_per_thread != 0 || (nt != 32 && nt != 64 && nt != 128 && nt != 256)) return SWE_EINVAL;
   if (p.stages == 0) p.stages = 2;
   if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
   if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
@@ -593,6 +595,18 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   }
   *out = m;
   return SWE_OK;
+}
+
+// Integrates every scenario's mass into its control word. The tiled step
+// does not integrate it; k_cfl_tiled does, from the current state (it also
+// recomputes the CFL dt of that same state, which leaves it unchanged).
+void refresh_mass(const swe_state* s) {
+  const swe_mesh* m = s->mesh;
+  if (m->kernel == SWE_KERNEL_TILED) {
+    if (m->prm.precision == SWE_F64) launch_cfl<double>(s);
+    else launch_cfl<float>(s);
+  }
+  swe::k_mass_sum<<<nscen(m), 256, 0, m->stream>>>(s->ctl, s->partial);
 }
 
 // Scatters buffer b of field k (0 h, 1 hu, 2 hv) to caller order in stage.
@@ -888,7 +902,7 @@ swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, d
   if (!s) return SWE_EINVAL;
   const swe_mesh* m = s->mesh;
   const int n = nscen(m);
-  if (mass) swe::k_mass_sum<<<n, 256, 0, m->stream>>>(s->ctl, s->partial);
+  if (mass) refresh_mass(s);
   swe_status st = read_ctl(s);
   if (st != SWE_OK) return st;
   bool same = true;
@@ -941,8 +955,7 @@ swe_status swe_state_info(const swe_state* s, int64_t* info) {
 swe_status swe_scenario_info(const swe_state* s, int32_t scenario, double* t, double* mass,
                              int64_t* steps, double* dt_next) {
   if (!s || scenario < 0 || scenario >= nscen(s->mesh)) return SWE_EINVAL;
-  const swe_mesh* m = s->mesh;
-  if (mass) swe::k_mass_sum<<<nscen(m), 256, 0, m->stream>>>(s->ctl, s->partial);
+  if (mass) refresh_mass(s);
   swe_status st = read_ctl(s);
   if (st != SWE_OK) return st;
   const swe::Ctl& c = s->host_ctl[scenario];

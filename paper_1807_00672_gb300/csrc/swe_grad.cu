@@ -96,6 +96,7 @@ template <typename Real, int CPT>
 void launch_adjoint_cpt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::AdjArgs<Real>& a,
                         const swe::AdjLayout& L, int grid, cudaStream_t st) {
   switch (m->tile / CPT) {
+    case 32: launch_adjoint_nt<Real, 32, CPT>(m, dm, a, L, grid, st); break;
     case 64: launch_adjoint_nt<Real, 64, CPT>(m, dm, a, L, grid, st); break;
     case 128: launch_adjoint_nt<Real, 128, CPT>(m, dm, a, L, grid, st); break;
     default: launch_adjoint_nt<Real, 256, CPT>(m, dm, a, L, grid, st); break;
@@ -131,6 +132,7 @@ int prepare_adjoint_nt(const swe::AdjLayout& L) {
 template <typename Real, int CPT>
 int prepare_adjoint_cpt(const swe_mesh* m, const swe::AdjLayout& L) {
   switch (m->tile / CPT) {
+    case 32: return prepare_adjoint_nt<Real, 32, CPT>(L);
     case 64: return prepare_adjoint_nt<Real, 64, CPT>(L);
     case 128: return prepare_adjoint_nt<Real, 128, CPT>(L);
     default: return prepare_adjoint_nt<Real, 256, CPT>(L);

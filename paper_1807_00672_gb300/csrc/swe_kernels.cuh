@@ -277,6 +277,14 @@ struct MassAcc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Stand-in accumulator for launches that do not integrate the mass (the
+// tiled step: the mass is integrated on demand by k_cfl_tiled).
+template <typename Real>
+struct NoMass {
+  __device__ __forceinline__ void add(Real, Real) {}
+  __device__ __forceinline__ double value() const { return 0.0; }
+};
+
 // Four consecutive values (one interleaved cell or one face slot).
 template <typename Real>
 struct V4 {
@@ -395,11 +403,11 @@ __device__ __forceinline__ void face_flux(Real hA, Real uA, Real vA, Real zA,
 // Per-cell end of the step: residual -> Euler update (Eq. 4) -> friction ->
 // next-step CFL rate. rhi/rlo: the residual as an unevaluated sum (lo = 0
 // for the plain path). Writes the new state and accumulates mass/rate.
-template <typename Real, bool Comp>
+template <typename Real, bool Comp, typename Acc>
 __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area, Real irP, Real gn2,
                                             Real dt, const Real rhi[3], const Real rlo[3],
                                             const Num& num, Real& h1, Real& hu1, Real& hv1,
-                                            MassAcc<Real>& mass, Real& rate, int& bad, int& neg) {
+                                            Acc& mass, Real& rate, int& bad, int& neg) {
   using O = Ops<Real>;
   const Real zero = Real(0);
   const Real a = O::div(dt, area);
@@ -736,9 +744,10 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
 // copy moves TC values.
 // ---------------------------------------------------------------------------
 // Resident blocks per SM the tiled kernel is compiled for (register budget):
-// 1024 threads per SM for FP32, 512 for FP64.
+// 768 threads per SM for FP32 (shared memory allows 6 blocks of 128 threads
+// anyway; up to 85 registers), 512 for FP64.
 template <typename Real, int NT>
-constexpr int tiled_min_blocks() { return (sizeof(Real) == 4 ? 1024 : 512) / NT; }
+constexpr int tiled_min_blocks() { return (sizeof(Real) == 4 ? 768 : 512) / NT; }
 
 // NT threads per block, CPT cells per thread: tiles of TC = NT * CPT cells.
 template <typename Real, bool Comp, int NT, int NS, int CPT>
@@ -816,7 +825,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     }
   };
 
-  MassAcc<Real> mass;
+  NoMass<Real> mass;  // integrated on demand (k_cfl_tiled), not every step
   Real rate = Real(0);
   int bad = 0, neg = 0, timeout = 0;
   if (tid == 0) {

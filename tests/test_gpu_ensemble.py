@@ -161,3 +161,28 @@ def test_mesh_closed_before_its_state_stays_alive_until_the_state_goes():
     for a, b in zip(st.fields(), ref.fields()):
         assert np.array_equal(a, b)
     st.close()
+
+
+def test_autotuner_picks_a_measured_shape_and_caches_it(tmp_path, monkeypatch):
+    pytest.importorskip("torch")
+    from paper_1807_00672_gb300 import autotune
+    ensure_built()
+    monkeypatch.setenv("SWE_TUNE_CACHE", str(tmp_path / "tune.json"))
+    cases = scenario_mix()[:3]
+    cand = ((256, 2, 2), (128, 1, 2), (64, 2, 2))
+    r = autotune.tune(cases, "f32", candidates=cand, steps=8)
+    assert not r["cached"]
+    assert (r["tile"], r["cells_per_thread"], r["stages"]) in cand
+    timed = [t for t in r["trials"] if "sec_per_step" in t]
+    assert len(timed) == 3
+    assert r["sec_per_step"] == min(t["sec_per_step"] for t in timed)
+    again = autotune.tune(cases, "f32", candidates=cand, steps=8)
+    assert again["cached"] and again["tile"] == r["tile"]
+    # the chosen shape runs and matches the default shape bitwise
+    mesh, st = ensemble_state(cases, precision="f32", tile=r["tile"],
+                              cells_per_thread=r["cells_per_thread"], stages=r["stages"])
+    ref_mesh, ref = ensemble_state(cases, precision="f32")
+    st.run(10)
+    ref.run(10)
+    for a, b in zip(st.fields(), ref.fields()):
+        assert np.array_equal(a, b)

@@ -197,3 +197,35 @@ def test_grad_needs_the_tiled_single_scenario_mesh():
     with pytest.raises(swe.SweError) as e:
         swe.Tape(st2, 3, 2)
     assert e.value.status == swe.SWE_ESTATE
+
+
+def test_grad_edge_cases():
+    """One step, no gauges, interval longer than the run, no seeds."""
+    c = smooth_wet_case(seed=6)
+    mesh, st, tape = record(c, 1, 1, None)
+    assert tape.gauge_h.shape == (1, 0)
+    g = seeds(c, 1, 0, 2)
+    r = tape.grad(g_h=g["g_h"], g_hu=g["g_hu"], g_hv=g["g_hv"])
+    v = directions(c, 3)
+    t, gd, _ = oracle_jvp(c, 1, [], v)
+    lhs = float(g["g_h"] @ t[0] + g["g_hu"] @ t[1] + g["g_hv"] @ t[2])
+    rhs = float(sum(r[k] @ v[k] for k in ("h", "hu", "hv", "z", "n")))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+    zero = tape.grad()
+    for k, a in zero.items():
+        assert np.all(a == 0.0), k
+    _, _, t2 = record(c, 3, 10, [4])  # K > N: one segment
+    assert t2.info()["checkpoint_every"] == 3
+    r2 = t2.grad(g_gauge=np.ones((3, 1)))
+    assert np.isfinite(r2["n"]).all() and np.abs(r2["h"]).max() > 0
+
+
+def test_grad_rejects_bad_arguments():
+    c = smooth_wet_case()
+    ensure_built()
+    mesh = swe.Mesh(c.mesh.xy, c.mesh.tri, precision="f64")
+    st = swe.State(mesh, c.h, c.hu, c.hv, c.z, c.n)
+    for n, k, gauges in ((0, 1, None), (3, 0, None), (3, 1, [mesh.T]), (3, 1, [-1])):
+        with pytest.raises(swe.SweError) as e:
+            swe.Tape(st, n, k, gauges)
+        assert e.value.status == swe.SWE_EINVAL
