@@ -315,34 +315,39 @@ __device__ __forceinline__ void st4(double* p, double x, double y, double z, dou
 template <typename Real>
 __device__ __forceinline__ void hllc(Real hA, Real unA, Real utA, Real hB, Real unB, Real utB,
                                      Real g, Real& F0, Real& F1, Real& F2) {
-  // Straight-line form: every case is computed and the right one selected
-  // (the same values the case analysis picks; no divergent branches).
+  // Straight-line form (no divergent branches). The HLL formula is evaluated
+  // with the clamped speeds S- = min(SA, 0) and S+ = max(SB, 0): it then
+  // equals the upwind flux F_A when SA >= 0 and F_B when SB <= 0, the cases
+  // of the case analysis, so mass and normal momentum need no case selection.
   using O = Ops<Real>;
   const Real zero = Real(0), half = Real(0.5);
   const bool wetA = hA > zero, wetB = hB > zero;
-  const Real cA = O::sqrt_(g * hA);
-  const Real cB = O::sqrt_(g * hB);
+  const Real ghA = g * hA, ghB = g * hB;
+  const Real cA = O::sqrt_(ghA);
+  const Real cB = O::sqrt_(ghB);
   // wave speeds: two-rarefaction estimates when both sides are wet, Toro's
   // dry-bed speeds when one side is dry
   const Real us = (unA + unB) * half + cA - cB;
   const Real cs = (cA + cB) * half + (unA - unB) * Real(0.25);
   const Real SA = wetA ? (wetB ? fmin(unA - cA, us - cs) : unA - cA) : unB - Real(2) * cB;
   const Real SB = wetA ? (wetB ? fmax(unB + cB, us + cs) : unA + Real(2) * cA) : unB + cB;
-  const Real qA = hA * unA;
-  const Real qB = hB * unB;
-  const Real FA1 = qA * unA + half * g * hA * hA;
-  const Real FB1 = qB * unB + half * g * hB * hB;
-  const Real inv = O::div(Real(1), SB - SA);
-  const Real H0 = (SB * qA - SA * qB + SA * SB * (hB - hA)) * inv;
-  const Real H1 = (SB * FA1 - SA * FB1 + SA * SB * (qB - qA)) * inv;
-  // Contact speed S* = num / den with den < 0 whenever a side is wet, so
-  // S* >= 0 exactly when num <= 0: no division needed for the upwind choice.
+  const Real Sm = fmin(SA, zero), Sp = fmax(SB, zero);
+  const Real qA = hA * unA, qB = hB * unB;
+  const Real FA1 = qA * unA + half * ghA * hA;
+  const Real FB1 = qB * unB + half * ghB * hB;
+  const Real inv = O::div(Real(1), Sp - Sm);
+  const Real SS = Sm * Sp;
+  const Real H0 = (Sp * qA - Sm * qB + SS * (hB - hA)) * inv;
+  const Real H1 = (Sp * FA1 - Sm * FB1 + SS * (qB - qA)) * inv;
+  // Transverse momentum from the upwind side of the contact: S* = num / den
+  // with den < 0 whenever a side is wet, so S* >= 0 exactly when num <= 0
+  // (no division); the supersonic cases take their own side.
   const Real num = SA * hB * (unB - SB) - SB * hA * (unA - SA);
-  const Real H2 = H0 * (num <= zero ? utA : utB);
-  const bool left = SA >= zero, right = SB <= zero, dry = !wetA && !wetB;
-  F0 = dry ? zero : left ? qA : right ? qB : H0;
-  F1 = dry ? zero : left ? FA1 : right ? FB1 : H1;
-  F2 = dry ? zero : left ? qA * utA : right ? qB * utB : H2;
+  const Real ut = SA >= zero ? utA : (SB <= zero ? utB : (num <= zero ? utA : utB));
+  const bool dry = !wetA && !wetB;
+  F0 = dry ? zero : H0;
+  F1 = dry ? zero : H1;
+  F2 = dry ? zero : H0 * ut;
 }
 
 // Velocity of a cell: (hu, hv) / h when wet, else 0.
@@ -350,8 +355,9 @@ template <typename Real>
 __device__ __forceinline__ void velocity(Real h, Real hu, Real hv, const Num& num, Real& u, Real& v) {
   const bool w = Ops<Real>::wet(h, num);
   if constexpr (sizeof(Real) == 8) {
-    u = w ? hu / h : 0.0;
-    v = w ? hv / h : 0.0;
+    const double r = w ? 1.0 / h : 0.0;  // one division for both components
+    u = hu * r;
+    v = hv * r;
   } else {
     const float r = rcp_approx(h);
     u = w ? hu * r : 0.0f;
@@ -427,17 +433,10 @@ __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area,
   if (O::wet(hs, num)) {
     const Real q = O::sqrt_(qx * qx + qy * qy);
     const Real d = Real(1) + O::friction(dt, gn2, q, hs);
-    Real qn;  // |q| after friction
-    if constexpr (sizeof(Real) == 8) {
-      qx = qx / d;
-      qy = qy / d;
-      qn = sqrt(qx * qx + qy * qy);
-    } else {
-      const Real rd = O::div(Real(1), d);
-      qx = qx * rd;
-      qy = qy * rd;
-      qn = q * rd;
-    }
+    const Real rd = O::div(Real(1), d);
+    qx = qx * rd;
+    qy = qy * rd;
+    const Real qn = q * rd;  // |q| after friction
     const Real lam = O::div(qn, hs) + O::sqrt_(Real(num.g) * hs);
     rate = fmax(rate, lam * irP);
   } else {
