@@ -406,6 +406,84 @@ __device__ __forceinline__ void face_flux(Real hA, Real uA, Real vA, Real zA,
   cB2 = len * (Fy + PB * ny);
 }
 
+// FP32 face of the tiled kernel: velocity + face_flux<float> + hllc in
+// fewer instructions, the same flux up to rounding:
+//  - a dry cell's reciprocal depth is 0, so its velocity comes out 0;
+//  - a reconstructed depth is x if x > h_eps, else 0 (max(0, x) and the dry
+//    test in one);
+//  - the transverse momentum is upwinded by the sign of the HLL mass flux
+//    F0: S* = F_hll / h_hll with h_hll > 0, so in the subsonic case F0 >= 0
+//    exactly when S* >= 0; when S_A >= 0, F0 = q_A >= 0 (side A, as S* >= 0),
+//    when S_B <= 0, F0 = q_B <= 0 (side B); where F0 = 0 the choice does not
+//    matter (F2 = F0 ut);
+//  - with both sides dry every numerator is 0; the wave-speed span is
+//    clamped away from 0, so the flux is 0 without a selection;
+//  - the contributions use the scaled normal (gx, gy) = l n directly:
+//    l (F_n n + F_t t + P n) = (F_n + P) (gx, gy) + F_t (-gy, gx).
+// A, B: interleaved cells (h, hu, hv, z); Wall: B is ignored (mirror of A).
+template <bool Wall>
+__device__ __forceinline__ void face_flux_f32(const V4<float>& A, const V4<float>& B, float gx,
+                                              float gy, const Num& num, float& c0, float& cA1,
+                                              float& cA2, float& cB1, float& cB2) {
+  const float g = (float)num.g, eps = num.h_eps_f32;
+  const float l2 = gx * gx + gy * gy;
+  const float rl = rsqrt_approx(l2);
+  const float nx = gx * rl, ny = gy * rl, len = l2 * rl;
+  const float rA = A.x > eps ? rcp_approx(A.x) : 0.0f;
+  const float uA = A.y * rA, vA = A.z * rA;
+  const float unA = uA * nx + vA * ny;
+  const float utA = vA * nx - uA * ny;
+  float hB, zB, unB, utB;
+  if (Wall) {
+    hB = A.x; zB = A.w; unB = -unA; utB = utA;
+  } else {
+    const float rB = B.x > eps ? rcp_approx(B.x) : 0.0f;
+    const float uB = B.y * rB, vB = B.z * rB;
+    hB = B.x; zB = B.w;
+    unB = uB * nx + vB * ny;
+    utB = vB * nx - uB * ny;
+  }
+  // hydrostatic reconstruction
+  const float zs = fmaxf(A.w, zB);
+  const float xA = A.x + A.w - zs, xB = hB + zB - zs;
+  const float hAs = xA > eps ? xA : 0.0f;
+  const float hBs = xB > eps ? xB : 0.0f;
+  // HLLC wave speeds (see hllc) and the HLL fluxes with clamped speeds
+  const bool wetA = hAs > 0.0f, wetB = hBs > 0.0f;
+  const float ghA = g * hAs, ghB = g * hBs;
+  const float cA = sqrt_approx(ghA), cB = sqrt_approx(ghB);
+  const float us = (unA + unB) * 0.5f + cA - cB;
+  const float cs = (cA + cB) * 0.5f + (unA - unB) * 0.25f;
+  const float SA = wetA ? (wetB ? fminf(unA - cA, us - cs) : unA - cA) : unB - 2.0f * cB;
+  const float SB = wetA ? (wetB ? fmaxf(unB + cB, us + cs) : unA + 2.0f * cA) : unB + cB;
+  const float Sm = fminf(SA, 0.0f), Sp = fmaxf(SB, 0.0f);
+  const float qA = hAs * unA, qB = hBs * unB;
+  const float FA1 = qA * unA + 0.5f * ghA * hAs;
+  const float FB1 = qB * unB + 0.5f * ghB * hBs;
+  const float inv = rcp_approx(fmaxf(Sp - Sm, 1e-30f));
+  const float SS = Sm * Sp;
+  float F0 = (Sp * qA - Sm * qB + SS * (hBs - hAs)) * inv;
+  const float F1 = (Sp * FA1 - Sm * FB1 + SS * (qB - qA)) * inv;
+  float F2 = F0 * (F0 >= 0.0f ? utA : utB);
+  if (Wall) { F0 = 0.0f; F2 = 0.0f; }
+  // bed pressure of each side, g/2 (h^2 - h*^2)
+  const float hg = 0.5f * g;
+  const float PA = hg * (A.x * A.x - hAs * hAs);
+  const float t1 = F2 * gy, t2 = F2 * gx;
+  c0 = len * F0;
+  const float FA = F1 + PA;
+  cA1 = FA * gx - t1;
+  cA2 = FA * gy + t2;
+  if (!Wall) {
+    const float FB = F1 + hg * (hB * hB - hBs * hBs);
+    cB1 = FB * gx - t1;
+    cB2 = FB * gy + t2;
+  } else {
+    cB1 = 0.0f;
+    cB2 = 0.0f;
+  }
+}
+
 // Per-cell end of the step: residual -> Euler update (Eq. 4) -> friction ->
 // next-step CFL rate. rhi/rlo: the residual as an unevaluated sum (lo = 0
 // for the plain path). Writes the new state and accumulates mass/rate.
@@ -780,13 +858,23 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   // Thread 0 tracks, per stage, the parity of the next phase to wait for and
   // whether a copy is in flight (bit st of each mask).
   uint32_t parity_bits = 0, pending = 0;
-  // Thread 0: queue the bulk copies of tile t into stage st.
+  // Thread 0: record and halo offsets of the next tile to queue, loaded one
+  // iteration before they are used so that their latency stays hidden.
+  int64_t o_r0 = 0, o_r1 = 0, o_h0 = 0, o_h1 = 0;
+  auto load_offsets = [&](int t) {
+    o_r0 = m.toff[t];
+    o_r1 = m.toff[t + 1];
+    o_h0 = m.hoff[t];
+    o_h1 = m.hoff[t + 1];
+  };
+  // Thread 0: queue the bulk copies of tile t (offsets already loaded) into
+  // stage st.
   auto issue = [&](int st, int t) {
     unsigned char* p = smem + st * L.stage;
     const int64_t base = (int64_t)t * TC;
-    const int64_t r0 = m.toff[t], h0 = m.hoff[t];
-    const uint32_t nrec = (uint32_t)(m.toff[t + 1] - r0);
-    const uint32_t nh = (uint32_t)(m.hoff[t + 1] - h0);
+    const int64_t r0 = o_r0, h0 = o_h0;
+    const uint32_t nrec = (uint32_t)(o_r1 - r0);
+    const uint32_t nh = (uint32_t)(o_h1 - h0);
     const uint32_t cells = TC * 4 * (uint32_t)sizeof(Real);
     s_nrec[st] = (int)nrec;
     s_nh[st] = (int)nh;
@@ -811,13 +899,15 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     return ok;
   };
   // All threads: gather the halo cells of stage st's tile (after its copies
-  // landed), one interleaved cell per cp.async group.
+  // landed), one interleaved cell per cp.async group. Lane l of warp w takes
+  // entries l W + w (W warps), so every warp gathers about nh / W cells.
   auto gather_halo = [&](int st) {
     unsigned char* p = smem + st * L.stage;
     const int32_t* hl = reinterpret_cast<const int32_t*>(p + L.off_hidx);
     Real* xc = reinterpret_cast<Real*>(p + L.off_cells) + 4 * TC;
     const int nh = s_nh[st];
-    for (int q = tid; q < nh; q += NT) {
+    constexpr int W = NT / 32;
+    for (int q = (tid & 31) * W + (tid >> 5); q < nh; q += NT) {
       const Real* src = U + 4 * (int64_t)hl[q];
 #pragma unroll
       for (int b = 0; b < (int)sizeof(Real) / 4; ++b) cp_async16(xc + 4 * q + b * (16 / sizeof(Real)), src + b * (16 / sizeof(Real)));
@@ -830,7 +920,11 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   if (tid == 0) {
 #pragma unroll
     for (int i = 0; i < NS - 1; ++i)
-      if (i < n_tiles) issue(i, t_first + i * t_step);
+      if (i < n_tiles) {
+        load_offsets(t_first + i * t_step);
+        issue(i, t_first + i * t_step);
+      }
+    if (NS - 1 < n_tiles) load_offsets(t_first + (NS - 1) * t_step);
   }
   if (n_tiles > 0) {
     const bool ok = (tid == 0) ? wait_stage(0) : true;
@@ -850,7 +944,10 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     const bool has_next = k + 1 < n_tiles;
     // The stage that receives tile k+NS-1 was released by the barrier that
     // ended iteration k-1.
-    if (tid == 0 && k + NS - 1 < n_tiles) issue((k + NS - 1) % NS, tile + (NS - 1) * t_step);
+    if (tid == 0 && k + NS - 1 < n_tiles) {
+      issue((k + NS - 1) % NS, tile + (NS - 1) * t_step);
+      if (k + NS < n_tiles) load_offsets(tile + NS * t_step);
+    }
     const unsigned char* p = smem + st * L.stage;
     const Real* xc = reinterpret_cast<const Real*>(p + L.off_cells);  // [ext][4]
     const int32_t* rS = reinterpret_cast<const int32_t*>(p + L.off_tS);
@@ -870,27 +967,57 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       c_gn2[cc] = s.gn2[base + tid + cc * NT];
     }
 
-    // face records
-    for (int r = tid; r < nrec; r += NT) {
+    // face records, the highest threads first: a partial last round falls
+    // on the last warps, away from warp 0, which also queues the copies
+    for (int r = NT - 1 - tid; r < nrec; r += NT) {
       const int32_t packed = rS[r];
       const int a = packed >> 16;                       // side A code
-      if (a == kSideWall) continue;                     // padding record
       const int b = (int)(int16_t)(packed & 0xffff);   // side B code
-      const bool wall = (b == kSideWall);
+      if constexpr (sizeof(Real) == 4) {
+        const float gx = rg0[r], gy = rg1[r];
+        float c0, cA1, cA2, cB1, cB2;
+        if (b == kSideWall) {
+          if (a == kSideWall) continue;  // padding record
+          const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));
+          face_flux_f32<true>(A, A, gx, gy, num, c0, cA1, cA2, cB1, cB2);
+          st4(slots + 4 * (-1 - a), c0, cA1, cA2, 0.0f);
+          continue;
+        }
+        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
+        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : TC + b;
+        const V4<Real> A = ld4(xc + 4 * ia);
+        const V4<Real> B = ld4(xc + 4 * ib);
+        face_flux_f32<false>(A, B, gx, gy, num, c0, cA1, cA2, cB1, cB2);
+        if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, 0.0f);
+        if (b < 0) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, 0.0f);
+        continue;
+      }
+      Real nx, ny, len;
+      Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
+      Real c0, cA1, cA2, cB1, cB2;
+      if (b == kSideWall) {
+        // Wall (side A is the tile cell owning the edge) or padding record;
+        // these are the last records of a tile.
+        if (a == kSideWall) continue;
+        const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));
+        Real uA, vA;
+        velocity(A.x, A.y, A.z, num, uA, vA);
+        face_flux<Real>(A.x, uA, vA, A.w, A.x, uA, vA, A.w, true, nx, ny, len, num, c0, cA1, cA2,
+                        cB1, cB2);
+        st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
+        continue;
+      }
       const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
-      const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (TC - 1)) : TC + b);
+      const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : TC + b;
       const V4<Real> A = ld4(xc + 4 * ia);
       const V4<Real> B = ld4(xc + 4 * ib);
       Real uA, vA, uB, vB;
       velocity(A.x, A.y, A.z, num, uA, vA);
       velocity(B.x, B.y, B.z, num, uB, vB);
-      Real nx, ny, len;
-      Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
-      Real c0, cA1, cA2, cB1, cB2;
-      face_flux<Real>(A.x, uA, vA, A.w, B.x, uB, vB, B.w, wall, nx, ny, len, num, c0, cA1, cA2, cB1,
+      face_flux<Real>(A.x, uA, vA, A.w, B.x, uB, vB, B.w, false, nx, ny, len, num, c0, cA1, cA2, cB1,
                       cB2);
       if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
-      if (b < 0 && !wall) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, Real(0));
+      if (b < 0) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, Real(0));
     }
     // The next tile's copies must have landed before its halo is gathered.
     const bool ok = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
