@@ -307,7 +307,7 @@ def main():
         "config": {
             "workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
             "triangles": T, "edges": mesh.E, "precision": args.precision,
-            "kernel": args.kernel, "tile": args.tile or 256, "stages": args.stages or 2,
+            "kernel": args.kernel, "tile": args.tile or (512 if args.precision == "f32" and (args.cpt or 2) == 2 else 256), "stages": args.stages or 2,
             "cells_per_thread": args.cpt or 2,
             "order": "morton", "seed": WORKLOADS[args.workload]["seed"],
             "l2": f"inputs larger than L2: {mesh.device_bytes() / 1e6:.0f} MB of mesh + "

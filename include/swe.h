@@ -83,7 +83,8 @@ typedef struct {
   int32_t order;      /* swe_order (default SWE_ORDER_MORTON) */
   int32_t kernel;     /* swe_kernel (default SWE_KERNEL_AUTO) */
   int32_t tile;       /* cells per tile of SWE_KERNEL_TILED; tile / cells_per_thread threads
-                         per block must be 32, 64, 128 or 256; 0 = default (256) */
+                         per block must be 32, 64, 128 or 256; 0 = default (512 in
+                         FP32 at 2 cells per thread, else 256) */
   int32_t stages;     /* shared-memory pipeline stages of SWE_KERNEL_TILED (2 or 3);
                          0 = default (2) */
   int32_t cells_per_thread;  /* cells each thread updates per tile (1 or 2); 0 = default (2) */

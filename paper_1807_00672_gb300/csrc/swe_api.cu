@@ -62,7 +62,11 @@ using namespace swe_host;
 namespace {
 
 constexpr int kStepsPerGraph = 16;
-constexpr int kDefaultTile = 256;
+// Default cells per tile: 512 for FP32 (fewer faces computed twice and less
+// per-tile work than 256, one block of 256 threads), 256 for FP64 (whose
+// tiles take twice the shared memory).
+constexpr int kDefaultTileF32 = 512;
+constexpr int kDefaultTileF64 = 256;
 constexpr int64_t kEnsembleWaves = 3;  // waves of work chunks for several scenarios
 
 #define cuda_failed(call) swe_host::cuda_failed_at((call), #call, __FILE__, __LINE__)
@@ -86,10 +90,10 @@ int grid_for(int64_t n, int threads, int cap) {
 
 // Opts the tiled kernel into its dynamic shared memory and returns its
 // resident blocks per SM (0 if it cannot run with this layout).
-template <typename Real, int NT, int NS, int CPT>
+template <typename Real, int NT, int NS, int TC>
 int prepare_tiled(const swe::TileLayout& L) {
   constexpr bool comp = sizeof(Real) == 4;
-  auto k = swe::k_tiled_step<Real, comp, NT, NS, CPT>;
+  auto k = swe::k_tiled_step<Real, comp, NT, NS, TC>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -104,8 +108,9 @@ int prepare_tiled(const swe::TileLayout& L) {
 
 template <typename Real, int NT, int CPT>
 int blocks_per_sm_tiled_nt(const swe_mesh* m) {
-  return m->stages == 3 ? prepare_tiled<Real, NT, 3, CPT>(m->layout)
-                        : prepare_tiled<Real, NT, 2, CPT>(m->layout);
+  constexpr int TC = NT * CPT;
+  return m->stages == 3 ? prepare_tiled<Real, NT, 3, TC>(m->layout)
+                        : prepare_tiled<Real, NT, 2, TC>(m->layout);
 }
 
 template <typename Real, int CPT>
@@ -128,10 +133,11 @@ void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe:
                      const swe::Num& num, cudaStream_t st) {
   const swe::TileLayout& L = m->layout;
   const int g = (int)m->nchunks;
+  constexpr int TC = NT * CPT;
   if (m->stages == 3)
-    swe::k_tiled_step<Real, Comp, NT, 3, CPT><<<g, NT, L.total, st>>>(dm, ds, num, L);
+    swe::k_tiled_step<Real, Comp, NT, 3, TC><<<g, NT, L.total, st>>>(dm, ds, num, L);
   else
-    swe::k_tiled_step<Real, Comp, NT, 2, CPT><<<g, NT, L.total, st>>>(dm, ds, num, L);
+    swe::k_tiled_step<Real, Comp, NT, 2, TC><<<g, NT, L.total, st>>>(dm, ds, num, L);
 }
 
 template <typename Real, bool Comp, int CPT>
@@ -315,8 +321,9 @@ swe_status resolve_params(const swe_params* params, swe_params& p) {
   if (p.precision != SWE_F64 && p.precision != SWE_F32) return SWE_EINVAL;
   if (p.order != SWE_ORDER_NONE && p.order != SWE_ORDER_MORTON) return SWE_EINVAL;
   if (p.kernel < SWE_KERNEL_AUTO || p.kernel > SWE_KERNEL_TILED) return SWE_EINVAL;
-  if (p.tile == 0) p.tile = kDefaultTile;
   if (p.cells_per_thread == 0) p.cells_per_thread = 2;
+  if (p.tile == 0)
+    p.tile = (p.precision == SWE_F32 && p.cells_per_thread == 2) ? kDefaultTileF32 : kDefaultTileF64;
   if (p.cells_per_thread != 1 && p.cells_per_thread != 2) return SWE_EINVAL;
   const int nt = p.tile / p.cells_per_thread;
   if (p.tile % p.cells_per_thread != 0 || (nt != 32 && nt != 64 && nt != 128 && nt != 256)) return SWE_EINVAL;

@@ -158,6 +158,24 @@ __device__ __forceinline__ void two_sum(Real a, Real b, Real& s, Real& e) {
   e = add_rn(sub_rn(a, ap), sub_rn(b, bp));
 }
 
+// Paired FP32 arithmetic (two IEEE round-to-nearest operations per
+// instruction, sm_100 and later). x - y is formed as fma(y, -1, x): the
+// product is exact, so the result is x - y rounded once.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// TwoSum on both lanes of a pair.
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bp = sub2(s, a);
+  const float2 ap = sub2(s, bp);
+  e = add2(sub2(a, ap), sub2(b, bp));
+}
+
 // ---------------------------------------------------------------------------
 // Precision-specific operations.
 // ---------------------------------------------------------------------------
@@ -417,7 +435,8 @@ __device__ __forceinline__ void face_flux(Real hA, Real uA, Real vA, Real zA,
 //    when S_B <= 0, F0 = q_B <= 0 (side B); where F0 = 0 the choice does not
 //    matter (F2 = F0 ut);
 //  - with both sides dry every numerator is 0; the wave-speed span is
-//    clamped away from 0, so the flux is 0 without a selection;
+//    clamped away from 0, so the flux is 0 without a selection (and the
+//    dry-bed wave speeds come from the same formula, see below);
 //  - the contributions use the scaled normal (gx, gy) = l n directly:
 //    l (F_n n + F_t t + P n) = (F_n + P) (gx, gy) + F_t (-gy, gx).
 // A, B: interleaved cells (h, hu, hv, z); Wall: B is ignored (mirror of A).
@@ -448,36 +467,42 @@ __device__ __forceinline__ void face_flux_f32(const V4<float>& A, const V4<float
   const float xA = A.x + A.w - zs, xB = hB + zB - zs;
   const float hAs = xA > eps ? xA : 0.0f;
   const float hBs = xB > eps ? xB : 0.0f;
-  // HLLC wave speeds (see hllc) and the HLL fluxes with clamped speeds
-  const bool wetA = hAs > 0.0f, wetB = hBs > 0.0f;
+  // HLLC wave speeds (see hllc). A dry side takes the normal velocity
+  // un_B - 2 c_B (A dry) or un_A + 2 c_A (B dry): the two-rarefaction
+  // estimates then reduce exactly to Toro's dry-bed speeds (c* = 0,
+  // u* = that velocity), so no case selection is needed; a dry side's
+  // discharge stays 0 (h* = 0).
+  const float hg = 0.5f * g;
   const float ghA = g * hAs, ghB = g * hBs;
   const float cA = sqrt_approx(ghA), cB = sqrt_approx(ghB);
-  const float us = (unA + unB) * 0.5f + cA - cB;
-  const float cs = (cA + cB) * 0.5f + (unA - unB) * 0.25f;
-  const float SA = wetA ? (wetB ? fminf(unA - cA, us - cs) : unA - cA) : unB - 2.0f * cB;
-  const float SB = wetA ? (wetB ? fmaxf(unB + cB, us + cs) : unA + 2.0f * cA) : unB + cB;
-  const float Sm = fminf(SA, 0.0f), Sp = fmaxf(SB, 0.0f);
+  const float vnA = hAs > 0.0f ? unA : unB - 2.0f * cB;
+  const float vnB = hBs > 0.0f ? unB : unA + 2.0f * cA;
+  const float us = (vnA + vnB) * 0.5f + cA - cB;
+  const float cs = (cA + cB) * 0.5f + (vnA - vnB) * 0.25f;
+  const float Sm = fminf(fminf(vnA - cA, us - cs), 0.0f);
+  const float Sp = fmaxf(fmaxf(vnB + cB, us + cs), 0.0f);
+  // HLL fluxes with the clamped speeds; e = g/2 h*^2 serves both the
+  // hydrostatic flux term and the bed pressure g/2 (h^2 - h*^2)
   const float qA = hAs * unA, qB = hBs * unB;
-  const float FA1 = qA * unA + 0.5f * ghA * hAs;
-  const float FB1 = qB * unB + 0.5f * ghB * hBs;
+  const float eA = hg * hAs * hAs, eB = hg * hBs * hBs;
+  const float FA1 = qA * unA + eA;
+  const float FB1 = qB * unB + eB;
   const float inv = rcp_approx(fmaxf(Sp - Sm, 1e-30f));
   const float SS = Sm * Sp;
   float F0 = (Sp * qA - Sm * qB + SS * (hBs - hAs)) * inv;
   const float F1 = (Sp * FA1 - Sm * FB1 + SS * (qB - qA)) * inv;
   float F2 = F0 * (F0 >= 0.0f ? utA : utB);
   if (Wall) { F0 = 0.0f; F2 = 0.0f; }
-  // bed pressure of each side, g/2 (h^2 - h*^2)
-  const float hg = 0.5f * g;
-  const float PA = hg * (A.x * A.x - hAs * hAs);
   const float t1 = F2 * gy, t2 = F2 * gx;
   c0 = len * F0;
-  const float FA = F1 + PA;
+  const float FA = F1 + (hg * A.x * A.x - eA);
   cA1 = FA * gx - t1;
   cA2 = FA * gy + t2;
   if (!Wall) {
-    const float FB = F1 + hg * (hB * hB - hBs * hBs);
-    cB1 = FB * gx - t1;
-    cB2 = FB * gy + t2;
+    // side B's contributions negated (its residual subtracts them)
+    const float FB = F1 + (hg * hB * hB - eB);
+    cB1 = t1 - FB * gx;
+    cB2 = -t2 - FB * gy;
   } else {
     cB1 = 0.0f;
     cB2 = 0.0f;
@@ -485,26 +510,27 @@ __device__ __forceinline__ void face_flux_f32(const V4<float>& A, const V4<float
 }
 
 // Per-cell end of the step: residual -> Euler update (Eq. 4) -> friction ->
-// next-step CFL rate. rhi/rlo: the residual as an unevaluated sum (lo = 0
-// for the plain path). Writes the new state and accumulates mass/rate.
+// next-step CFL rate. R: the residual (for Comp, the compensated face sum
+// rounded once, and U - a R is then one FMA). Writes the new state and
+// accumulates mass/rate.
 template <typename Real, bool Comp, typename Acc>
 __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area, Real irP, Real gn2,
-                                            Real dt, const Real rhi[3], const Real rlo[3],
-                                            const Num& num, Real& h1, Real& hu1, Real& hv1,
-                                            Acc& mass, Real& rate, int& bad, int& neg) {
+                                            Real dt, const Real R[3], const Num& num, Real& h1,
+                                            Real& hu1, Real& hv1, Acc& mass, Real& rate, Real& chk,
+                                            int& neg) {
   using O = Ops<Real>;
   const Real zero = Real(0);
   const Real a = O::div(dt, area);
-  Real U[3] = {h, hu, hv};
   Real out[3];
+  if constexpr (Comp && sizeof(Real) == 4) {
+    out[0] = fma_rn(-a, R[0], h);
+    const float2 o = fma2(make_float2(-a, -a), make_float2(R[1], R[2]), make_float2(hu, hv));
+    out[1] = o.x;
+    out[2] = o.y;
+  } else {
+    const Real U[3] = {h, hu, hv};
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (Comp) {
-      // The compensated face sum rounded once, then U - a R in one FMA.
-      out[c] = fma_rn(-a, add_rn(rhi[c], rlo[c]), U[c]);
-    } else {
-      out[c] = U[c] - a * rhi[c];
-    }
+    for (int c = 0; c < 3; ++c) out[c] = Comp ? fma_rn(-a, R[c], U[c]) : U[c] - a * R[c];
   }
   Real hs = out[0], qx = out[1], qy = out[2];
   if (hs < zero) { hs = zero; neg += 1; }
@@ -512,8 +538,14 @@ __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area,
     const Real q = O::sqrt_(qx * qx + qy * qy);
     const Real d = Real(1) + O::friction(dt, gn2, q, hs);
     const Real rd = O::div(Real(1), d);
-    qx = qx * rd;
-    qy = qy * rd;
+    if constexpr (sizeof(Real) == 4) {
+      const float2 qq = mul2(make_float2(qx, qy), make_float2(rd, rd));
+      qx = qq.x;
+      qy = qq.y;
+    } else {
+      qx = qx * rd;
+      qy = qy * rd;
+    }
     const Real qn = q * rd;  // |q| after friction
     const Real lam = O::div(qn, hs) + O::sqrt_(Real(num.g) * hs);
     rate = fmax(rate, lam * irP);
@@ -521,7 +553,8 @@ __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area,
     qx = zero;
     qy = zero;
   }
-  if (!isfinite(hs + qx + qy)) bad = 1;
+  // chk stays 0 unless a value is NaN or infinite (0 x that = NaN)
+  chk = fma_rn(hs + qx + qy, Real(0), chk);
   h1 = hs; hu1 = qx; hv1 = qy;
   mass.add(area, hs);
 }
@@ -664,8 +697,8 @@ __global__ void __launch_bounds__(256) k_cell_update(DevMesh<Real> m, DevState<R
   Real* __restrict__ hu1 = cur ? s.hu[0] : s.hu[1];
   Real* __restrict__ hv1 = cur ? s.hv[0] : s.hv[1];
   MassAcc<Real> mass;
-  Real rate = Real(0);
-  int bad = 0, neg = 0;
+  Real rate = Real(0), chk = Real(0);
+  int neg = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m.T;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t f[3] = {m.cf0[i], m.cf1[i], m.cf2[i]};
@@ -690,15 +723,18 @@ __global__ void __launch_bounds__(256) k_cell_update(DevMesh<Real> m, DevState<R
         }
       }
     }
+    Real R[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) R[q] = Comp ? add_rn(rhi[q], rlo[q]) : rhi[q];
     Real a1, b1, c1;
-    cell_finish<Real, Comp>(h[i], hu[i], hv[i], m.area[i], m.irP[i], s.gn2[i], dt, rhi, rlo, num,
-                            a1, b1, c1, mass, rate, bad, neg);
+    cell_finish<Real, Comp>(h[i], hu[i], hv[i], m.area[i], m.irP[i], s.gn2[i], dt, R, num, a1, b1,
+                            c1, mass, rate, chk, neg);
     h1[i] = a1;
     hu1[i] = b1;
     hv1[i] = c1;
   }
   finish_launch<256>(ctl, s.partial, blockIdx.x, 0, gridDim.x, mass.value(), (double)rate,
-                     bad ? kErrNan : 0, neg, true, num.courant);
+                     chk != Real(0) ? kErrNan : 0, neg, true, num.courant);
 }
 
 // ---------------------------------------------------------------------------
@@ -826,11 +862,13 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
 template <typename Real, int NT>
 constexpr int tiled_min_blocks() { return (sizeof(Real) == 4 ? 768 : 512) / NT; }
 
-// NT threads per block, CPT cells per thread: tiles of TC = NT * CPT cells.
-template <typename Real, bool Comp, int NT, int NS, int CPT>
+// NT threads per block, tiles of TC cells (a power of two, NT <= TC); a
+// thread updates the tile cells tid, tid + NT, ... (CPT = ceil(TC / NT)).
+template <typename Real, bool Comp, int NT, int NS, int TC>
 __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     k_tiled_step(DevMesh<Real> m, DevState<Real> s, Num num, TileLayout L) {
-  constexpr int TC = NT * CPT;
+  constexpr int CPT = (TC + NT - 1) / NT;
+  static_assert((TC & (TC - 1)) == 0 && NT <= TC && NT % 32 == 0, "tile shape");
   __shared__ int s_nrec[NS], s_nh[NS];  // record and halo counts of each stage's tile
   extern __shared__ __align__(128) unsigned char smem[];
   Real* slots = reinterpret_cast<Real*>(smem + L.off_slots);  // [3 TC][4], face k of cell j at k TC + j
@@ -916,7 +954,8 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
 
   NoMass<Real> mass;  // integrated on demand (k_cfl_tiled), not every step
   Real rate = Real(0);
-  int bad = 0, neg = 0, timeout = 0;
+  Real chk = Real(0);  // non-zero once a new value is NaN or infinite
+  int neg = 0, timeout = 0;
   if (tid == 0) {
 #pragma unroll
     for (int i = 0; i < NS - 1; ++i)
@@ -962,9 +1001,11 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     Real c_area[CPT], c_irP[CPT], c_gn2[CPT];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) {
-      c_area[cc] = m.area[base + tid + cc * NT];
-      c_irP[cc] = m.irP[base + tid + cc * NT];
-      c_gn2[cc] = s.gn2[base + tid + cc * NT];
+      const int j = tid + cc * NT;
+      if (TC % NT != 0 && j >= TC) break;
+      c_area[cc] = m.area[base + j];
+      c_irP[cc] = m.irP[base + j];
+      c_gn2[cc] = s.gn2[base + j];
     }
 
     // face records, the highest threads first: a partial last round falls
@@ -989,7 +1030,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
         const V4<Real> B = ld4(xc + 4 * ib);
         face_flux_f32<false>(A, B, gx, gy, num, c0, cA1, cA2, cB1, cB2);
         if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, 0.0f);
-        if (b < 0) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, 0.0f);
+        if (b < 0) st4(slots + 4 * (-1 - b), -c0, cB1, cB2, 0.0f);
         continue;
       }
       Real nx, ny, len;
@@ -1032,27 +1073,42 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     for (int cc = 0; cc < CPT; ++cc) {
       const int j = tid + cc * NT;
       if (j >= nc) break;
+      // the three face contributions (faces k = 0, 1, 2) of each field
       const V4<Real> f0 = ld4(slots + 4 * j);
       const V4<Real> f1 = ld4(slots + 4 * (TC + j));
       const V4<Real> f2 = ld4(slots + 4 * (2 * TC + j));
-      Real rhi[3] = {f0.x, f0.y, f0.z}, rlo[3] = {Real(0), Real(0), Real(0)};
-      const Real add1[3] = {f1.x, f1.y, f1.z}, add2[3] = {f2.x, f2.y, f2.z};
+      Real R[3];
+      if constexpr (Comp && sizeof(Real) == 4) {
+        // (f0 + f1) + f2 with both TwoSum errors added back, rounded once;
+        // h alone, (hu, hv) as a pair
+        Real s1, e1, s2, e2;
+        two_sum(f0.x, f1.x, s1, e1);
+        two_sum(s1, f2.x, s2, e2);
+        R[0] = add_rn(s2, add_rn(e1, e2));
+        float2 p1, q1, p2, q2;
+        two_sum2(make_float2(f0.y, f0.z), make_float2(f1.y, f1.z), p1, q1);
+        two_sum2(p1, make_float2(f2.y, f2.z), p2, q2);
+        const float2 r = add2(p2, add2(q1, q2));
+        R[1] = r.x;
+        R[2] = r.y;
+      } else {
+        const Real a0[3] = {f0.x, f0.y, f0.z}, a1[3] = {f1.x, f1.y, f1.z}, a2[3] = {f2.x, f2.y, f2.z};
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (Comp) {
-          Real s1, e1, s2, e2;
-          two_sum(rhi[q], add1[q], s1, e1);
-          two_sum(s1, add2[q], s2, e2);
-          rhi[q] = s2;
-          rlo[q] = add_rn(e1, e2);
-        } else {
-          rhi[q] = rhi[q] + add1[q] + add2[q];
+        for (int q = 0; q < 3; ++q) {
+          if (Comp) {
+            Real s1, e1, s2, e2;
+            two_sum(a0[q], a1[q], s1, e1);
+            two_sum(s1, a2[q], s2, e2);
+            R[q] = add_rn(s2, add_rn(e1, e2));
+          } else {
+            R[q] = a0[q] + a1[q] + a2[q];
+          }
         }
       }
       const V4<Real> c = ld4(xc + 4 * j);
       Real a1, b1, c1;
-      cell_finish<Real, Comp>(c.x, c.y, c.z, c_area[cc], c_irP[cc], c_gn2[cc], dt, rhi, rlo, num, a1,
-                              b1, c1, mass, rate, bad, neg);
+      cell_finish<Real, Comp>(c.x, c.y, c.z, c_area[cc], c_irP[cc], c_gn2[cc], dt, R, num, a1, b1,
+                              c1, mass, rate, chk, neg);
       st4(U1 + 4 * (int64_t)(base + j), a1, b1, c1, c.w);
     }
     cp_async_wait_all();
@@ -1066,7 +1122,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       if ((pending >> i) & 1u) mbar_wait(&bar[i], (parity_bits >> i) & 1u);
   }
   finish_launch<NT>(ctl, s.partial, ch.part, ctl->part0, (int)ctl->nparts, mass.value(),
-                    (double)rate, (bad ? kErrNan : 0) | (timeout ? kErrTimeout : 0), neg, true,
+                    (double)rate, (chk != Real(0) ? kErrNan : 0) | (timeout ? kErrTimeout : 0), neg, true,
                     num.courant);
 }
 
