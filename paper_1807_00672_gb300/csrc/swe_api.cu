@@ -134,10 +134,23 @@ void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe:
   const swe::TileLayout& L = m->layout;
   const int g = (int)m->nchunks;
   constexpr int TC = NT * CPT;
+  // Programmatic dependent launch: a step's blocks fetch their first tiles'
+  // mesh data while the previous step's last blocks finish, and wait for it
+  // (griddepcontrol.wait) before reading the state.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = L.total;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (m->stages == 3)
-    swe::k_tiled_step<Real, Comp, NT, 3, TC><<<g, NT, L.total, st>>>(dm, ds, num, L);
+    cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 3, TC>, dm, ds, num, L);
   else
-    swe::k_tiled_step<Real, Comp, NT, 2, TC><<<g, NT, L.total, st>>>(dm, ds, num, L);
+    cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC>, dm, ds, num, L);
 }
 
 template <typename Real, bool Comp, int CPT>

@@ -757,6 +757,17 @@ __device__ __forceinline__ void fence_mbar_init() {
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// Expect `bytes` more on the current phase without arriving.
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Programmatic dependent launch: let the next kernel in the stream start
+// (its blocks run until their own pdl_wait), and wait until the previous
+// kernel has completed with its memory visible.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
@@ -879,12 +890,12 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   const int t_first = ch.tile0, n_tiles = ch.ntiles, t_step = ch.stride;
   const int cell_end = ch.cell_end;
   Ctl* ctl = s.ctl + ch.scen;
-  if (ctl->done) return;
-  const int cur = ctl->cur;
-  const Real dt = Real(ctl->dt);
-  const Real* __restrict__ U = cur ? s.h[1] : s.h[0];  // interleaved cells (h, hu, hv, z)
-  Real* __restrict__ U1 = cur ? s.h[0] : s.h[1];
   const int tid = threadIdx.x;
+  // The state and the control word are read only after pdl_wait (they are
+  // the previous step's output); mesh data may be fetched before it.
+  const Real* __restrict__ U = nullptr;  // interleaved cells (h, hu, hv, z)
+  Real* __restrict__ U1 = nullptr;
+  Real dt = Real(0);
 
   if (tid == 0) {
 #pragma unroll
@@ -905,27 +916,36 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     o_h0 = m.hoff[t];
     o_h1 = m.hoff[t + 1];
   };
-  // Thread 0: queue the bulk copies of tile t (offsets already loaded) into
-  // stage st.
-  auto issue = [&](int st, int t) {
+  // Thread 0: queue the bulk copies of tile t's mesh data (offsets already
+  // loaded) into stage st: face records and halo list. The stage's phase
+  // completes once issue_cells has arrived as well.
+  auto issue_mesh = [&](int st) {
     unsigned char* p = smem + st * L.stage;
-    const int64_t base = (int64_t)t * TC;
     const int64_t r0 = o_r0, h0 = o_h0;
     const uint32_t nrec = (uint32_t)(o_r1 - r0);
     const uint32_t nh = (uint32_t)(o_h1 - h0);
-    const uint32_t cells = TC * 4 * (uint32_t)sizeof(Real);
     s_nrec[st] = (int)nrec;
     s_nh[st] = (int)nh;
     const uint32_t rb = nrec * (uint32_t)sizeof(Real);
     fence_proxy_async();
-    mbar_expect_tx(&bar[st], cells + nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
-    bulk_g2s(p + L.off_cells, U + 4 * base, cells, &bar[st]);
+    mbar_expect_tx_only(&bar[st], nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
     bulk_g2s(p + L.off_tS, m.tS + r0, nrec * 4, &bar[st]);
     bulk_g2s(p + L.off_g0, m.tg0 + r0, rb, &bar[st]);
     bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
     if (Geo<Real>::kArrays > 2) bulk_g2s(p + L.off_g2, m.tg2 + r0, rb, &bar[st]);
     if (nh > 0) bulk_g2s(p + L.off_hidx, m.hidx + h0, nh * 4, &bar[st]);
     pending |= 1u << st;
+  };
+  // Thread 0: queue tile t's state cells into stage st (arrives on its phase).
+  auto issue_cells = [&](int st, int t) {
+    unsigned char* p = smem + st * L.stage;
+    const uint32_t cells = TC * 4 * (uint32_t)sizeof(Real);
+    mbar_expect_tx(&bar[st], cells);
+    bulk_g2s(p + L.off_cells, U + 4 * (int64_t)t * TC, cells, &bar[st]);
+  };
+  auto issue = [&](int st, int t) {
+    issue_mesh(st);
+    issue_cells(st, t);
   };
   // Thread 0: wait for stage st's copies.
   auto wait_stage = [&](int st) -> bool {
@@ -956,13 +976,39 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   Real rate = Real(0);
   Real chk = Real(0);  // non-zero once a new value is NaN or infinite
   int neg = 0, timeout = 0;
+  // Mesh data of the first tiles, then wait for the previous step.
   if (tid == 0) {
 #pragma unroll
     for (int i = 0; i < NS - 1; ++i)
       if (i < n_tiles) {
         load_offsets(t_first + i * t_step);
-        issue(i, t_first + i * t_step);
+        issue_mesh(i);
       }
+  }
+  pdl_trigger();
+  pdl_wait();
+  if (ctl->done) {
+    // no step: let the mesh copies already queued land before exiting
+    if (tid == 0) {
+#pragma unroll
+      for (int i = 0; i < NS - 1; ++i)
+        if (i < n_tiles) {
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar[i])) : "memory");
+          mbar_wait(&bar[i], 0u);
+        }
+    }
+    return;
+  }
+  {
+    const int cur = ctl->cur;
+    dt = Real(ctl->dt);
+    U = cur ? s.h[1] : s.h[0];
+    U1 = cur ? s.h[0] : s.h[1];
+  }
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NS - 1; ++i)
+      if (i < n_tiles) issue_cells(i, t_first + i * t_step);
     if (NS - 1 < n_tiles) load_offsets(t_first + (NS - 1) * t_step);
   }
   if (n_tiles > 0) {
