@@ -210,7 +210,10 @@ void swe_state_destroy(swe_state* state);
  * initial state, the bed z and Manning's n. swe_grad can be called any
  * number of times on one tape (different seeds). Requires a single-scenario
  * mesh built with SWE_KERNEL_TILED (SWE_ESTATE otherwise). Results are in
- * the mesh precision; FP64 is the reference for accuracy.
+ * the mesh precision; FP64 is the reference for accuracy. The adjoint runs
+ * on the mesh's tiles: 256-cell tiles (swe_params.tile = 256) give the faster
+ * adjoint, since at 512 cells its shared memory fits half as many blocks per
+ * SM.
  * ------------------------------------------------------------------------- */
 typedef struct swe_tape swe_tape;
 
