@@ -296,6 +296,14 @@ swe_status swe_step_edges_static(int64_t n_cells, int64_t n_edges, const int32_t
                                  double dt, double* h_out, double* hu_out, double* hv_out,
                                  double* next_dt, double* mass, void* cuda_stream);
 
+/* Measurement helper (no counterpart in the paper): FP64 fused multiply-add
+ * throughput of the current device, for the FP64 path's arithmetic roofline.
+ * Runs a kernel of independent DFMA chains on every SM on `cuda_stream`
+ * (NULL: the default stream), timed with CUDA events; *tflops = FP64 flops
+ * (2 per fused multiply-add) per second / 1e12. Allocates a small output
+ * buffer, synchronises the stream. SWE_ECUDA on a CUDA error. */
+swe_status swe_fp64_fma_rate(void* cuda_stream, double* tflops);
+
 /* Static description of a status code. */
 const char* swe_strerror(swe_status status);
 

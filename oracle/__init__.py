@@ -60,8 +60,15 @@ def lib():
         L.oracle_run_tangent.restype = i64
         L.oracle_run_dts.argtypes = [vp, pp, i64, vp] + [vp] * 5 + [vp, i64, vp]
         L.oracle_run_dts.restype = i64
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the FP64 edge and cell loops (1: serial, the default).
+    The results do not depend on it."""
+    lib().oracle_set_threads(int(n))
 
 
 def _p(a: np.ndarray):

@@ -1,7 +1,8 @@
 """Compile the FP64 CPU oracle into oracle/liboracle_swe.so (test infrastructure).
 
 Plain g++, -O2 with floating-point contraction off so every product and sum
-rounds on its own, as the source is written.
+rounds on its own, as the source is written; OpenMP for the optional
+multi-threaded edge and cell loops (serial by default).
 """
 from __future__ import annotations
 
@@ -15,7 +16,7 @@ LIB = os.path.join(HERE, "liboracle_swe.so")
 
 
 def command() -> list[str]:
-    return ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+    return ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
             "-shared", SRC, "-o", LIB]
 
 

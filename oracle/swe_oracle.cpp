@@ -50,6 +50,7 @@
 #include <cstdint>
 #include <cstring>
 #include <limits>
+#include <type_traits>
 #include <vector>
 
 namespace oracle {
@@ -366,16 +367,50 @@ static int cell_update(const Mesh& m, const Params& p, int64_t i, const R& dt, c
   return neg;
 }
 
+// Host threads for the FP64 loops over edges and cells (1 = serial, the
+// default). Every edge and every cell writes only its own outputs, the
+// clipped-depth count is an integer sum and the CFL step a minimum, so the
+// results do not depend on the thread count. Dual numbers always run serially.
+static int g_threads = 1;
+
+// Per-cell CFL ratio (Omega/P) / (|u| + sqrt(g h)); false for a dry cell.
+template <class R>
+static bool cfl_ratio(const Mesh& m, const Params& p, const R* h, const R* hu, const R* hv,
+                      int64_t i, R& r) {
+  if (!(value_of(h[i]) > p.h_eps)) return false;
+  R u = hu[i] / h[i], v = hv[i] / h[i];
+  R lam = sqrt_(u * u + v * v) + sqrt_(p.g * h[i]);
+  r = (m.area[i] / m.perim[i]) / lam;
+  return true;
+}
+
 // CFL time step from the current state; E_DRY when no cell is wet.
 template <class R>
 static int cfl_dt(const Mesh& m, const Params& p, const R* h, const R* hu, const R* hv, R& dt) {
+  if constexpr (std::is_same<R, double>::value) {
+    if (g_threads > 1) {
+      // several threads: each finds the smallest ratio of its cells, then the
+      // smallest of those is taken (a minimum does not depend on the order)
+      double best = std::numeric_limits<double>::infinity();
+      int any = 0;
+#pragma omp parallel for num_threads(g_threads) reduction(min : best) reduction(max : any) schedule(static)
+      for (int64_t i = 0; i < m.T; ++i) {
+        double r;
+        if (cfl_ratio(m, p, h, hu, hv, i, r)) {
+          if (r < best) best = r;
+          any = 1;
+        }
+      }
+      if (!any) return E_DRY;
+      dt = p.courant * best;
+      return OK;
+    }
+  }
   bool any = false;
   R best(std::numeric_limits<double>::infinity());
   for (int64_t i = 0; i < m.T; ++i) {
-    if (!(value_of(h[i]) > p.h_eps)) continue;
-    R u = hu[i] / h[i], v = hv[i] / h[i];
-    R lam = sqrt_(u * u + v * v) + sqrt_(p.g * h[i]);
-    R r = (m.area[i] / m.perim[i]) / lam;
+    R r;
+    if (!cfl_ratio(m, p, h, hu, hv, i, r)) continue;
     if (!any || r < best) best = r;
     any = true;
   }
@@ -389,9 +424,12 @@ template <class R>
 static int64_t step(const Mesh& m, const Params& p, const R& dt,
                     const R* h, const R* hu, const R* hv, const R* z, const R* n,
                     R* h1, R* hu1, R* hv1) {
+  const int nt = std::is_same<R, double>::value ? g_threads : 1;
   std::vector<EdgeOut<R>> fl(m.E);
+#pragma omp parallel for num_threads(nt) schedule(static)
   for (int64_t e = 0; e < m.E; ++e) fl[e] = edge_flux(m, p, e, h, hu, hv, z);
   int64_t neg = 0;
+#pragma omp parallel for num_threads(nt) reduction(+ : neg) schedule(static)
   for (int64_t i = 0; i < m.T; ++i) {
     R res[3];
     cell_residual(m, i, fl, res);
@@ -412,6 +450,9 @@ extern "C" {
 typedef struct { double g, courant, h_eps; } oracle_params;
 
 static Params P(const oracle_params* p) { return Params{p->g, p->courant, p->h_eps}; }
+
+// Host threads of the FP64 edge and cell loops (values < 1 mean 1).
+void oracle_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
 
 void* oracle_mesh_new(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tris,
                       int* status) {

@@ -35,7 +35,7 @@ EXPORTS = (
     "swe_state_set", "swe_step", "swe_run", "swe_advance", "swe_sync", "swe_copy_out",
     "swe_state_info", "swe_next_dt", "swe_scenario_info", "swe_state_destroy", "swe_strerror",
     "swe_last_cuda_error", "swe_step_edges_static", "swe_grad_record", "swe_grad",
-    "swe_tape_info", "swe_tape_destroy",
+    "swe_tape_info", "swe_tape_destroy", "swe_fp64_fma_rate",
 )
 
 
@@ -103,6 +103,7 @@ def lib():
         "swe_tape_destroy": (None, [vp]),
         "swe_step_edges_static": (st, [i64, i64] + [vp] * 13 + [dbl] * 4 + [vp] * 3
                                   + [vp, vp, vp]),
+        "swe_fp64_fma_rate": (st, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -353,3 +354,11 @@ class Tape:
             self.close()
         except Exception:
             pass
+
+
+def fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 fused multiply-add throughput of the current device in
+    TFLOP/s (swe_fp64_fma_rate)."""
+    r = ctypes.c_double()
+    _check(lib().swe_fp64_fma_rate(stream, ctypes.byref(r)), "swe_fp64_fma_rate")
+    return r.value

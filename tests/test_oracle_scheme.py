@@ -224,3 +224,21 @@ def test_single_cell_updates_match_the_full_step():
     assert np.array_equal(one[0], s.h[cells])
     assert np.array_equal(one[1], s.hu[cells])
     assert np.array_equal(one[2], s.hv[cells])
+
+
+def test_threaded_loops_give_identical_results():
+    """The oracle's OpenMP edge and cell loops (used for the all-core CPU
+    baseline) change nothing: 4 threads reproduce the serial run bit for bit,
+    dt sequence included."""
+    case = inputs.random_flow_case(nx=40, ny=26, seed=17)
+    runs = []
+    for nt in (1, 4):
+        oracle.set_threads(nt)
+        try:
+            st = oracle.state_from_case(case)
+            dts = st.run(30)
+            runs.append((st.h.copy(), st.hu.copy(), st.hv.copy(), np.asarray(dts).copy()))
+        finally:
+            oracle.set_threads(1)
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(a, b)
