@@ -222,6 +222,146 @@ __device__ __forceinline__ void face_vjp(Real hA, Real huA, Real hvA, Real zA, R
   }
 }
 
+// Vector-Jacobian product of one face in the clamped form of the flux that
+// the FP32 step computes (face_flux_f32): one HLL formula with the clamped
+// speeds S- = min(S_A, 0), S+ = max(S_B, 0), the dry side's normal velocity
+// replaced by un_B - 2 c_B (or un_A + 2 c_A) in the wave-speed estimates,
+// the transverse momentum upwinded by the sign of F0. It is the same
+// function of the inputs as the case analysis of face_vjp (the clamped
+// speeds reproduce the supersonic cases: with S_A >= 0, S- = 0 and F = F_A,
+// whose derivative with respect to S_A is 0, as face_vjp takes it), so the
+// derivatives agree away from ties; it has no case branches. Ties follow the
+// same conventions: max(zA, zB) and the speed estimates take the first
+// argument, S_A = 0 counts as S_A >= 0 and S_B = 0 as S_B <= 0. A and B are
+// the sides' cells (h, hu, hv, z) as the forward step read them; for a wall
+// B is ignored (the mirror of A folds into gA).
+template <typename Real, bool Wall>
+__device__ __forceinline__ void face_vjp_clamped(const V4<Real>& A, const V4<Real>& B, Real nx,
+                                                 Real ny, Real len, const Num& num, Real rA0,
+                                                 Real rA1, Real rA2, Real rB0, Real rB1, Real rB2,
+                                                 Real gA[4], Real gB[4]) {
+  using O = Ops<Real>;
+  const Real zero = Real(0), half = Real(0.5), quarter = Real(0.25);
+  const Real g = Real(num.g), hg = half * g;
+  // ---- forward, keeping what the reverse sweep needs
+  const Real rA = O::wet(A.x, num) ? O::div(Real(1), A.x) : zero;  // 0 on a dry cell
+  const Real uA = A.y * rA, vA = A.z * rA;
+  const Real unA = uA * nx + vA * ny;
+  const Real utA = vA * nx - uA * ny;
+  Real hB, zB, unB, utB, uB = zero, vB = zero, rB = zero;
+  if (Wall) {
+    hB = A.x; zB = A.w; unB = -unA; utB = utA;
+  } else {
+    rB = O::wet(B.x, num) ? O::div(Real(1), B.x) : zero;
+    uB = B.y * rB;
+    vB = B.z * rB;
+    hB = B.x; zB = B.w;
+    unB = uB * nx + vB * ny;
+    utB = vB * nx - uB * ny;
+  }
+  const bool zsA = A.w >= zB;  // max(zA, zB) taken from A on a tie
+  const Real zs = zsA ? A.w : zB;
+  const Real xA = A.x + A.w - zs, xB = hB + zB - zs;
+  const bool wetA = O::wet(xA, num), wetB = O::wet(xB, num);  // reconstructed sides wet
+  const Real hAs = wetA ? xA : zero, hBs = wetB ? xB : zero;
+  const Real cA = O::sqrt_(g * hAs), cB = O::sqrt_(g * hBs);
+  const Real vnA = wetA ? unA : unB - Real(2) * cB;
+  const Real vnB = wetB ? unB : unA + Real(2) * cA;
+  const Real us = (vnA + vnB) * half + cA - cB;
+  const Real cs = (cA + cB) * half + (vnA - vnB) * quarter;
+  const Real a1 = vnA - cA, a2 = us - cs, b1 = vnB + cB, b2 = us + cs;
+  const bool firstA = a1 <= a2, firstB = b1 >= b2;
+  const Real SA = firstA ? a1 : a2, SB = firstB ? b1 : b2;
+  const bool negA = SA < zero, posB = SB > zero;
+  const Real Sm = negA ? SA : zero, Sp = posB ? SB : zero;
+  const Real qA = hAs * unA, qB = hBs * unB;
+  const Real FA1 = qA * unA + hg * hAs * hAs, FB1 = qB * unB + hg * hBs * hBs;
+  const bool live = wetA || wetB;  // both sides dry: F = 0 whatever the speeds
+  const Real inv = live ? O::div(Real(1), Sp - Sm) : zero;
+  const Real SS = Sm * Sp, dh = hBs - hAs, dq = qB - qA;
+  const Real N0 = Sp * qA - Sm * qB + SS * dh;
+  const Real N1 = Sp * FA1 - Sm * FB1 + SS * dq;
+  const Real F0 = N0 * inv;
+  const bool upA = F0 >= zero;  // transverse momentum from A where F0 >= 0
+
+  // ---- reverse sweep
+  // residual contributions: A gets +l (F0, Fx + PA nx, Fy + PA ny), B gets
+  // -l (F0, Fx + PB nx, Fy + PB ny), Fx = F1 nx - F2 ny, Fy = F1 ny + F2 nx
+  const Real bFx = len * (rA1 - rB1), bFy = len * (rA2 - rB2);
+  const Real bF1 = bFx * nx + bFy * ny;
+  Real bF0 = zero, bF2 = zero;
+  if (!Wall) {
+    bF0 = len * (rA0 - rB0);
+    bF2 = bFy * nx - bFx * ny;
+  }
+  const Real bPA = len * (rA1 * nx + rA2 * ny);
+  const Real bPB = Wall ? zero : -len * (rB1 * nx + rB2 * ny);
+  // P = g/2 (h^2 - h*^2)
+  Real bhA = g * A.x * bPA, bhB = g * hB * bPB;
+  Real bhAs = -g * hAs * bPA, bhBs = -g * hBs * bPB;
+  // F2 = F0 ut
+  bF0 += bF2 * (upA ? utA : utB);
+  const Real but = bF2 * F0;
+  Real butA = upA ? but : zero, butB = upA ? zero : but;
+  // F0 = N0 / D, F1 = N1 / D, D = S+ - S-
+  const Real bN0 = bF0 * inv, bN1 = bF1 * inv;
+  const Real bD = -(bF0 * N0 + bF1 * N1) * inv * inv;
+  const Real bSp = bD + bN0 * (qA + Sm * dh) + bN1 * (FA1 + Sm * dq);
+  const Real bSm = -bD + bN0 * (Sp * dh - qB) + bN1 * (Sp * dq - FB1);
+  Real bqA = bN0 * Sp - bN1 * SS, bqB = bN1 * SS - bN0 * Sm;
+  bhBs += bN0 * SS;
+  bhAs -= bN0 * SS;
+  const Real bFA1 = bN1 * Sp, bFB1 = -bN1 * Sm;
+  // F1 of each side = q un + g/2 h*^2, q = h* un
+  bqA += bFA1 * unA;
+  bqB += bFB1 * unB;
+  Real bunA = bFA1 * qA + bqA * hAs, bunB = bFB1 * qB + bqB * hBs;
+  bhAs += bFA1 * g * hAs + bqA * unA;
+  bhBs += bFB1 * g * hBs + bqB * unB;
+  // S- = min(S_A, 0), S+ = max(S_B, 0); the speed estimates
+  const Real bSA = negA ? bSm : zero, bSB = posB ? bSp : zero;
+  Real bvnA = zero, bvnB = zero, bcA = zero, bcB = zero, bus = zero, bcs = zero;
+  if (firstA) { bvnA += bSA; bcA -= bSA; } else { bus += bSA; bcs -= bSA; }
+  if (firstB) { bvnB += bSB; bcB += bSB; } else { bus += bSB; bcs += bSB; }
+  bvnA += half * bus + quarter * bcs;
+  bvnB += half * bus - quarter * bcs;
+  bcA += bus + half * bcs;
+  bcB += half * bcs - bus;
+  // a dry side's velocity in the estimates
+  if (wetA) { bunA += bvnA; } else { bunB += bvnA; bcB -= Real(2) * bvnA; }
+  if (wetB) { bunB += bvnB; } else { bunA += bvnB; bcA += Real(2) * bvnB; }
+  // c = sqrt(g h*): dc/dh* = g / (2 c) on a wet side (c = 0 and no term on a dry one)
+  if (wetA) bhAs += bcA * O::div(hg, cA);
+  if (wetB) bhBs += bcB * O::div(hg, cB);
+  // reconstruction h* = h + z - max(zA, zB) where it stays wet
+  Real bzA = zero, bzB = zero, bzs = zero;
+  if (wetA) { bhA += bhAs; bzA += bhAs; bzs -= bhAs; }
+  if (wetB) { bhB += bhBs; bzB += bhBs; bzs -= bhBs; }
+  if (zsA) bzA += bzs; else bzB += bzs;
+  if (Wall) {  // B mirrors A: hB = hA, zB = zA, unB = -unA, utB = utA
+    bhA += bhB;
+    bzA += bzB;
+    bunA -= bunB;
+    butA += butB;
+  }
+  // face frame -> x, y velocities -> conserved variables (u = hu r, r = 1/h
+  // on a wet cell, 0 on a dry one)
+  const Real buA = bunA * nx - butA * ny, bvA = bunA * ny + butA * nx;
+  gA[0] = bhA - (buA * uA + bvA * vA) * rA;
+  gA[1] = buA * rA;
+  gA[2] = bvA * rA;
+  gA[3] = bzA;
+  if (Wall) {
+    gB[0] = zero; gB[1] = zero; gB[2] = zero; gB[3] = zero;
+  } else {
+    const Real buB = bunB * nx - butB * ny, bvB = bunB * ny + butB * nx;
+    gB[0] = bhB - (buB * uB + bvB * vB) * rB;
+    gB[1] = buB * rB;
+    gB[2] = bvB * rB;
+    gB[3] = bzB;
+  }
+}
+
 // Inputs and outputs of one adjoint launch (interleaved cells, internal
 // order, padded to whole tiles).
 template <typename Real>
@@ -270,10 +410,15 @@ inline AdjLayout make_adj_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, u
   L.off_lam = o; o += a16(halo_cap * 4 * w);
   L.off_harea = o; o += a16(halo_cap * w);
   L.off_hgn2 = o; o += a16(halo_cap * w);
-  L.off_tS = o; o += a16(rec_cap * 4);
-  L.off_g0 = o; o += a16(rec_cap * w);
-  L.off_g1 = o; o += a16(rec_cap * w);
-  L.off_g2 = o; o += geo_arrays > 2 ? a16(rec_cap * w) : 0u;
+  if (w == 4) {  // FP32: interleaved 16-byte records
+    L.off_tS = o; o += a16(rec_cap * 16);
+    L.off_g0 = L.off_g1 = L.off_g2 = o;
+  } else {
+    L.off_tS = o; o += a16(rec_cap * 4);
+    L.off_g0 = o; o += a16(rec_cap * w);
+    L.off_g1 = o; o += a16(rec_cap * w);
+    L.off_g2 = o; o += geo_arrays > 2 ? a16(rec_cap * w) : 0u;
+  }
   L.off_hidx = o; o += a16(halo_cap * 4);
   L.stage = o;
   o = ns * L.stage;
@@ -295,11 +440,17 @@ inline AdjLayout make_adj_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, u
 //   (C) each cell: dL/dU^n = mu + its three slots in face order, the z parts
 //       added to the running dL/dz, and its dL/d(g n^2) accumulated.
 // Three block barriers per tile.
+#ifndef SWE_ADJ_CLAMPED_F64
+#define SWE_ADJ_CLAMPED_F64 0
+#endif
 template <typename Real, int NT, int NS, int CPT>
 __global__ void __launch_bounds__(NT)
     k_tiled_adjoint(DevMesh<Real> m, AdjArgs<Real> A, Num num, AdjLayout L) {
   using O = Ops<Real>;
   constexpr int TC = NT * CPT;
+  // FP32 differentiates the clamped form its step computes; FP64 the case
+  // analysis of its step (face_vjp)
+  constexpr bool kClampedVjp = sizeof(Real) == 4 || SWE_ADJ_CLAMPED_F64;
   __shared__ int s_nrec[NS], s_nh[NS];
   extern __shared__ __align__(128) unsigned char smem[];
   Real* rho = reinterpret_cast<Real*>(smem + L.off_rho);      // [ext][4]
@@ -331,12 +482,16 @@ __global__ void __launch_bounds__(NT)
     s_nh[st] = (int)nh;
     const uint32_t rb = nrec * (uint32_t)sizeof(Real);
     fence_proxy_async();
-    mbar_expect_tx(&bar[st], cells + nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
+    mbar_expect_tx(&bar[st], cells + nrec * rec_bytes<Real>() + nh * 4);
     bulk_g2s(p + L.off_un, A.un + 4 * base, cells, &bar[st]);
-    bulk_g2s(p + L.off_tS, m.tS + r0, nrec * 4, &bar[st]);
-    bulk_g2s(p + L.off_g0, m.tg0 + r0, rb, &bar[st]);
-    bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
-    if (Geo<Real>::kArrays > 2) bulk_g2s(p + L.off_g2, m.tg2 + r0, rb, &bar[st]);
+    if constexpr (sizeof(Real) == 4) {
+      bulk_g2s(p + L.off_tS, m.trec + r0, nrec * 16, &bar[st]);
+    } else {
+      bulk_g2s(p + L.off_tS, m.tS + r0, nrec * 4, &bar[st]);
+      bulk_g2s(p + L.off_g0, m.tg0 + r0, rb, &bar[st]);
+      bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
+      bulk_g2s(p + L.off_g2, m.tg2 + r0, rb, &bar[st]);
+    }
     if (nh > 0) bulk_g2s(p + L.off_hidx, m.hidx + h0, nh * 4, &bar[st]);
     pending |= 1u << st;
   };
@@ -453,10 +608,40 @@ __global__ void __launch_bounds__(NT)
 
     // (B) face records
     for (int r = tid; r < nrec; r += NT) {
-      const int32_t packed = rS[r];
+      int32_t packed;
+      Real nx, ny, len;
+      if constexpr (sizeof(Real) == 4) {
+        rec_f32(rS, r, packed, nx, ny, len);
+      } else {
+        packed = rS[r];
+        Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
+      }
       const int a = packed >> 16;
       if (a == kSideWall) continue;  // padding record
       const int b = (int)(int16_t)(packed & 0xffff);
+      if constexpr (kClampedVjp) {
+        Real gA[4], gB[4];
+        if (b == kSideWall) {  // wall: side A is the tile cell owning the edge
+          const int ia = (-1 - a) & (TC - 1);
+          const V4<Real> UA = ld4(sun + 4 * ia);
+          const V4<Real> RA = ld4(rho + 4 * ia);
+          face_vjp_clamped<Real, true>(UA, UA, nx, ny, len, num, RA.x, RA.y, RA.z, Real(0), Real(0),
+                                       Real(0), gA, gB);
+          st4(slots + 4 * (-1 - a), gA[0], gA[1], gA[2], gA[3]);
+          continue;
+        }
+        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
+        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : TC + b;
+        const V4<Real> UA = ld4(sun + 4 * ia);
+        const V4<Real> UB = ld4(sun + 4 * ib);
+        const V4<Real> RA = ld4(rho + 4 * ia);
+        const V4<Real> RB = ld4(rho + 4 * ib);
+        face_vjp_clamped<Real, false>(UA, UB, nx, ny, len, num, RA.x, RA.y, RA.z, RB.x, RB.y, RB.z,
+                                      gA, gB);
+        if (a < 0) st4(slots + 4 * (-1 - a), gA[0], gA[1], gA[2], gA[3]);
+        if (b < 0) st4(slots + 4 * (-1 - b), gB[0], gB[1], gB[2], gB[3]);
+        continue;
+      }
       const bool wall = (b == kSideWall);
       const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
       const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (TC - 1)) : TC + b);
@@ -464,8 +649,6 @@ __global__ void __launch_bounds__(NT)
       const V4<Real> UB = ld4(sun + 4 * ib);
       const V4<Real> RA = ld4(rho + 4 * ia);
       const V4<Real> RB = ld4(rho + 4 * ib);
-      Real nx, ny, len;
-      Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
       Real gA[4], gB[4];
       const Real zero = Real(0);
       face_vjp<Real>(UA.x, UA.y, UA.z, UA.w, UB.x, UB.y, UB.z, UB.w, wall, nx, ny, len, num, RA.x,

@@ -501,8 +501,12 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     L.add(4 * T); L.add(4 * T); L.add(4 * T);
   } else {
     L.add(8 * (tiles + 1)); L.add(8 * (tiles + 1));
-    L.add(4 * R);
-    for (int g = 0; g < geo_arrays; ++g) L.add(w * R);
+    if (geo_arrays > 2) {
+      L.add(4 * R);                                   // FP64: side codes
+      for (int g = 0; g < geo_arrays; ++g) L.add(w * R);  // and geometry arrays
+    } else {
+      L.add(16 * R);  // FP32: interleaved records
+    }
     L.add(4 * H);
     L.add(sizeof(swe::Chunk) * C);
   }
@@ -528,10 +532,14 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   } else {
     m->toff = (int64_t*)m->arena.take(8 * (tiles + 1));
     m->hoff = (int64_t*)m->arena.take(8 * (tiles + 1));
-    m->tS = (int32_t*)m->arena.take(4 * R);
-    m->tg0 = m->arena.take(w * R);
-    m->tg1 = m->arena.take(w * R);
-    if (geo_arrays > 2) m->tg2 = m->arena.take(w * R);
+    if (geo_arrays > 2) {  // FP64: side codes and geometry in separate arrays
+      m->tS = (int32_t*)m->arena.take(4 * R);
+      m->tg0 = m->arena.take(w * R);
+      m->tg1 = m->arena.take(w * R);
+      m->tg2 = m->arena.take(w * R);
+    } else {  // FP32: interleaved 16-byte records
+      m->trec = m->arena.take(16 * R);
+    }
     m->hidx = (int32_t*)m->arena.take(4 * H);
     m->chunks = (swe::Chunk*)m->arena.take(sizeof(swe::Chunk) * C);
   }
@@ -567,7 +575,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   } else if (st == SWE_OK) {
     std::vector<int64_t> toff(tiles + 1, 0), hoff(tiles + 1, 0);
     std::vector<int32_t> packed(R), hidx(H);
-    std::vector<double> g0(R), g1(R), g2(geo_arrays > 2 ? R : 0);
+    std::vector<double> g0(R), g1(R), g2(R);
     auto code = [](int32_t v) { return v == swe::kWall ? (int32_t)swe::kSideWall : v; };
     bool fits = true;
     int64_t r_at = 0, h_at = 0;
@@ -584,14 +592,9 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
         const int32_t a = code(hmi.tA[r]), b = code(hmi.tB[r]);
         fits = fits && a >= -32768 && a <= 32767 && b >= -32768 && b <= 32767;
         packed[r_at + r] = (int32_t)(((uint32_t)(uint16_t)a << 16) | (uint32_t)(uint16_t)b);
-        if (geo_arrays > 2) {
-          g0[r_at + r] = hmi.tnx[r];
-          g1[r_at + r] = hmi.tny[r];
-          g2[r_at + r] = hmi.tlen[r];
-        } else {  // scaled normal l n
-          g0[r_at + r] = hmi.tlen[r] * hmi.tnx[r];
-          g1[r_at + r] = hmi.tlen[r] * hmi.tny[r];
-        }
+        g0[r_at + r] = hmi.tnx[r];
+        g1[r_at + r] = hmi.tny[r];
+        g2[r_at + r] = hmi.tlen[r];
       }
       for (size_t q = 0; q < hmi.hidx.size(); ++q) hidx[h_at + q] = (int32_t)(sc.cell0 + hmi.hidx[q]);
       r_at += (int64_t)hmi.tA.size();
@@ -602,10 +605,22 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     if (!fits) chk(SWE_EINVAL);
     chk(upload(m, toff, m->toff));
     chk(upload(m, hoff, m->hoff));
-    chk(upload(m, packed, m->tS));
-    chk(upload_real(m, g0, m->tg0));
-    chk(upload_real(m, g1, m->tg1));
-    if (geo_arrays > 2) chk(upload_real(m, g2, m->tg2));
+    if (geo_arrays > 2) {
+      chk(upload(m, packed, m->tS));
+      chk(upload_real(m, g0, m->tg0));
+      chk(upload_real(m, g1, m->tg1));
+      chk(upload_real(m, g2, m->tg2));
+    } else {
+      // FP32 record r: {packed sides, nx, ny, l} as one 16-byte word (the
+      // geometry rounded once from FP64)
+      std::vector<int32_t> rec(4 * R);
+      for (int64_t r = 0; r < R; ++r) {
+        const float f[3] = {(float)g0[r], (float)g1[r], (float)g2[r]};
+        rec[4 * r] = packed[r];
+        std::memcpy(&rec[4 * r + 1], f, sizeof f);
+      }
+      chk(upload(m, rec, m->trec));
+    }
     chk(upload(m, hidx, m->hidx));
     chk(upload(m, chunks, m->chunks));
   }

@@ -78,6 +78,7 @@ struct swe_mesh {
   int64_t *toff = nullptr, *hoff = nullptr;
   int32_t *tS = nullptr, *hidx = nullptr;
   void *tg0 = nullptr, *tg1 = nullptr, *tg2 = nullptr;
+  void* trec = nullptr;  // FP32: interleaved records {packed sides, nx, ny, l}
   swe::Chunk* chunks = nullptr;  // work of each block of the tiled kernels
   int grid_edge = 1, grid_cell = 1, grid_cfl = 1, max_grid = 1;
   // Handles that use this mesh (states). swe_mesh_destroy while some are
@@ -134,6 +135,7 @@ swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
   d.tg0 = (const Real*)m->tg0;
   d.tg1 = (const Real*)m->tg1;
   d.tg2 = (const Real*)m->tg2;
+  d.trec = (const int4*)m->trec;
   return d;
 }
 

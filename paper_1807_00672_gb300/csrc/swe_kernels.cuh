@@ -112,6 +112,7 @@ struct DevMesh {
   const Real* tg0;
   const Real* tg1;
   const Real* tg2;
+  const int4* trec;  // FP32: interleaved records {packed sides, nx, ny, l}
 };
 
 // Cell state of one buffer b: h[b][i * stride], hu[b][i * stride],
@@ -237,10 +238,10 @@ struct Ops<float> {
   }
 };
 
-// Face geometry of the tiled records. FP64: unit normal and length as
-// computed on the host. FP32: the scaled normal (l nx, l ny) only, from which
-// the unit normal and the length are recovered with one reciprocal square
-// root (both tiles of a shared face recover the same bits).
+// Face geometry of the tiled records: unit normal and length as computed on
+// the host. FP64 keeps the side codes and the three values in separate
+// arrays (tS, tg0, tg1, tg2); FP32 keeps each record as one 16-byte word
+// {side codes, nx, ny, l} (trec), read with a single 128-bit load.
 template <typename Real>
 struct Geo;
 
@@ -255,19 +256,19 @@ struct Geo<double> {
   }
 };
 
-template <>
-struct Geo<float> {
-  static constexpr int kArrays = 2;
-  static __device__ __forceinline__ void get(const float* g0, const float* g1, const float*, int r,
-                                             float& nx, float& ny, float& len) {
-    const float gx = g0[r], gy = g1[r];
-    const float l2 = gx * gx + gy * gy;
-    const float rl = rsqrt_approx(l2);
-    nx = gx * rl;
-    ny = gy * rl;
-    len = l2 * rl;
-  }
-};
+// Bytes of one staged face record and its geometry (all arrays together).
+template <typename Real>
+__host__ __device__ constexpr uint32_t rec_bytes() { return sizeof(Real) == 4 ? 16u : 4u + 3u * 8u; }
+
+// FP32 record r of an interleaved record array: side codes and geometry.
+__device__ __forceinline__ void rec_f32(const void* base, int r, int32_t& packed, float& nx,
+                                        float& ny, float& len) {
+  const int4 v = reinterpret_cast<const int4*>(base)[r];
+  packed = v.x;
+  nx = __int_as_float(v.y);
+  ny = __int_as_float(v.z);
+  len = __int_as_float(v.w);
+}
 
 // Mass integral accumulator: plain FP64, or for FP32 exact products and a
 // compensated running sum, converted to FP64 at the end.
@@ -437,17 +438,15 @@ __device__ __forceinline__ void face_flux(Real hA, Real uA, Real vA, Real zA,
 //  - with both sides dry every numerator is 0; the wave-speed span is
 //    clamped away from 0, so the flux is 0 without a selection (and the
 //    dry-bed wave speeds come from the same formula, see below);
-//  - the contributions use the scaled normal (gx, gy) = l n directly:
+//  - the contributions use the scaled normal (gx, gy) = l n:
 //    l (F_n n + F_t t + P n) = (F_n + P) (gx, gy) + F_t (-gy, gx).
 // A, B: interleaved cells (h, hu, hv, z); Wall: B is ignored (mirror of A).
 template <bool Wall>
-__device__ __forceinline__ void face_flux_f32(const V4<float>& A, const V4<float>& B, float gx,
-                                              float gy, const Num& num, float& c0, float& cA1,
-                                              float& cA2, float& cB1, float& cB2) {
+__device__ __forceinline__ void face_flux_f32(const V4<float>& A, const V4<float>& B, float nx,
+                                              float ny, float len, const Num& num, float& c0,
+                                              float& cA1, float& cA2, float& cB1, float& cB2) {
   const float g = (float)num.g, eps = num.h_eps_f32;
-  const float l2 = gx * gx + gy * gy;
-  const float rl = rsqrt_approx(l2);
-  const float nx = gx * rl, ny = gy * rl, len = l2 * rl;
+  const float gx = len * nx, gy = len * ny;
   const float rA = A.x > eps ? rcp_approx(A.x) : 0.0f;
   const float uA = A.y * rA, vA = A.z * rA;
   const float unA = uA * nx + vA * ny;
@@ -836,10 +835,15 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
   L.ext = tc + halo_cap;
   uint32_t o = 0;
   L.off_cells = o; o += a16(L.ext * 4 * w);
-  L.off_tS = o; o += a16(rec_cap * 4);
-  L.off_g0 = o; o += a16(rec_cap * w);
-  L.off_g1 = o; o += a16(rec_cap * w);
-  L.off_g2 = o; o += geo_arrays > 2 ? a16(rec_cap * w) : 0u;
+  if (w == 4) {  // FP32: interleaved 16-byte records
+    L.off_tS = o; o += a16(rec_cap * 16);
+    L.off_g0 = L.off_g1 = L.off_g2 = o;
+  } else {
+    L.off_tS = o; o += a16(rec_cap * 4);
+    L.off_g0 = o; o += a16(rec_cap * w);
+    L.off_g1 = o; o += a16(rec_cap * w);
+    L.off_g2 = o; o += geo_arrays > 2 ? a16(rec_cap * w) : 0u;
+  }
   L.off_hidx = o; o += a16(halo_cap * 4);
   L.stage = o;
   o = ns * L.stage;
@@ -928,11 +932,15 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     s_nh[st] = (int)nh;
     const uint32_t rb = nrec * (uint32_t)sizeof(Real);
     fence_proxy_async();
-    mbar_expect_tx_only(&bar[st], nrec * 4 + Geo<Real>::kArrays * rb + nh * 4);
-    bulk_g2s(p + L.off_tS, m.tS + r0, nrec * 4, &bar[st]);
-    bulk_g2s(p + L.off_g0, m.tg0 + r0, rb, &bar[st]);
-    bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
-    if (Geo<Real>::kArrays > 2) bulk_g2s(p + L.off_g2, m.tg2 + r0, rb, &bar[st]);
+    mbar_expect_tx_only(&bar[st], nrec * rec_bytes<Real>() + nh * 4);
+    if constexpr (sizeof(Real) == 4) {
+      bulk_g2s(p + L.off_tS, m.trec + r0, nrec * 16, &bar[st]);
+    } else {
+      bulk_g2s(p + L.off_tS, m.tS + r0, nrec * 4, &bar[st]);
+      bulk_g2s(p + L.off_g0, m.tg0 + r0, rb, &bar[st]);
+      bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
+      bulk_g2s(p + L.off_g2, m.tg2 + r0, rb, &bar[st]);
+    }
     if (nh > 0) bulk_g2s(p + L.off_hidx, m.hidx + h0, nh * 4, &bar[st]);
     pending |= 1u << st;
   };
@@ -1057,16 +1065,18 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     // face records, the highest threads first: a partial last round falls
     // on the last warps, away from warp 0, which also queues the copies
     for (int r = NT - 1 - tid; r < nrec; r += NT) {
-      const int32_t packed = rS[r];
+      int32_t packed;
+      float fnx = 0.0f, fny = 0.0f, flen = 0.0f;
+      if constexpr (sizeof(Real) == 4) rec_f32(rS, r, packed, fnx, fny, flen);
+      else packed = rS[r];
       const int a = packed >> 16;                       // side A code
       const int b = (int)(int16_t)(packed & 0xffff);   // side B code
       if constexpr (sizeof(Real) == 4) {
-        const float gx = rg0[r], gy = rg1[r];
         float c0, cA1, cA2, cB1, cB2;
         if (b == kSideWall) {
           if (a == kSideWall) continue;  // padding record
           const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));
-          face_flux_f32<true>(A, A, gx, gy, num, c0, cA1, cA2, cB1, cB2);
+          face_flux_f32<true>(A, A, fnx, fny, flen, num, c0, cA1, cA2, cB1, cB2);
           st4(slots + 4 * (-1 - a), c0, cA1, cA2, 0.0f);
           continue;
         }
@@ -1074,37 +1084,37 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
         const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : TC + b;
         const V4<Real> A = ld4(xc + 4 * ia);
         const V4<Real> B = ld4(xc + 4 * ib);
-        face_flux_f32<false>(A, B, gx, gy, num, c0, cA1, cA2, cB1, cB2);
+        face_flux_f32<false>(A, B, fnx, fny, flen, num, c0, cA1, cA2, cB1, cB2);
         if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, 0.0f);
         if (b < 0) st4(slots + 4 * (-1 - b), -c0, cB1, cB2, 0.0f);
-        continue;
-      }
-      Real nx, ny, len;
-      Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
-      Real c0, cA1, cA2, cB1, cB2;
-      if (b == kSideWall) {
-        // Wall (side A is the tile cell owning the edge) or padding record;
-        // these are the last records of a tile.
-        if (a == kSideWall) continue;
-        const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));
-        Real uA, vA;
+      } else {
+        Real nx, ny, len;
+        Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
+        Real c0, cA1, cA2, cB1, cB2;
+        if (b == kSideWall) {
+          // Wall (side A is the tile cell owning the edge) or padding record;
+          // these are the last records of a tile.
+          if (a == kSideWall) continue;
+          const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));
+          Real uA, vA;
+          velocity(A.x, A.y, A.z, num, uA, vA);
+          face_flux<Real>(A.x, uA, vA, A.w, A.x, uA, vA, A.w, true, nx, ny, len, num, c0, cA1, cA2,
+                          cB1, cB2);
+          st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
+          continue;
+        }
+        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
+        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : TC + b;
+        const V4<Real> A = ld4(xc + 4 * ia);
+        const V4<Real> B = ld4(xc + 4 * ib);
+        Real uA, vA, uB, vB;
         velocity(A.x, A.y, A.z, num, uA, vA);
-        face_flux<Real>(A.x, uA, vA, A.w, A.x, uA, vA, A.w, true, nx, ny, len, num, c0, cA1, cA2,
-                        cB1, cB2);
-        st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
-        continue;
+        velocity(B.x, B.y, B.z, num, uB, vB);
+        face_flux<Real>(A.x, uA, vA, A.w, B.x, uB, vB, B.w, false, nx, ny, len, num, c0, cA1, cA2, cB1,
+                        cB2);
+        if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
+        if (b < 0) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, Real(0));
       }
-      const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
-      const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : TC + b;
-      const V4<Real> A = ld4(xc + 4 * ia);
-      const V4<Real> B = ld4(xc + 4 * ib);
-      Real uA, vA, uB, vB;
-      velocity(A.x, A.y, A.z, num, uA, vA);
-      velocity(B.x, B.y, B.z, num, uB, vB);
-      face_flux<Real>(A.x, uA, vA, A.w, B.x, uB, vB, B.w, false, nx, ny, len, num, c0, cA1, cA2, cB1,
-                      cB2);
-      if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
-      if (b < 0) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, Real(0));
     }
     // The next tile's copies must have landed before its halo is gathered.
     const bool ok = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
