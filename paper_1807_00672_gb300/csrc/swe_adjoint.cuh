@@ -439,7 +439,7 @@ inline AdjLayout make_adj_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, u
 //       tile's side, as in the forward);
 //   (C) each cell: dL/dU^n = mu + its three slots in face order, the z parts
 //       added to the running dL/dz, and its dL/d(g n^2) accumulated.
-// Three block barriers per tile.
+// (A) of the next tile runs right after (C), so two block barriers per tile.
 #ifndef SWE_ADJ_CLAMPED_F64
 #define SWE_ADJ_CLAMPED_F64 0
 #endif
@@ -543,6 +543,41 @@ __global__ void __launch_bounds__(NT)
       ndg[cc] = A.dgn2[i];
     }
   };
+  // (A) of a tile: mu (registers) and the friction and dL/dz parts of the
+  // thread's own cells from the registers load_cells filled, rho of those
+  // cells and of the halo cells this thread gathered (gather_halo's
+  // assignment, so no barrier is needed after its own copies land).
+  Real mu[CPT][3], bg[CPT], dzr[CPT];
+  auto phase_a = [&](int st, int tile) {
+    const unsigned char* p = smem + st * L.stage;
+    const Real* su1 = reinterpret_cast<const Real*>(p + L.off_u1);
+    const Real* sla = reinterpret_cast<const Real*>(p + L.off_lam);
+    const Real* har = reinterpret_cast<const Real*>(p + L.off_harea);
+    const Real* hgn = reinterpret_cast<const Real*>(p + L.off_hgn2);
+    const int nc = min(TC, cell_end - tile * TC);
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      const int j = tid + cc * NT;
+      const V4<Real> c1 = nu1[cc];
+      const V4<Real> la = nla[cc];
+      dzr[cc] = la.w;
+      cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, ngn[cc], dt, num, mu[cc][0], mu[cc][1],
+                     mu[cc][2], bg[cc]);
+      bg[cc] += ndg[cc];
+      const Real a = j < nc ? -O::div(dt, nar[cc]) : Real(0);  // padding: area 0
+      st4(rho + 4 * j, a * mu[cc][0], a * mu[cc][1], a * mu[cc][2], Real(0));
+    }
+    const int nh = s_nh[st];
+    for (int q = tid; q < nh; q += NT) {
+      const int j = TC + q;
+      const V4<Real> c1 = ld4(su1 + 4 * q);
+      const V4<Real> la = ld4(sla + 4 * q);
+      Real mh, mx, my, b;
+      cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, hgn[q], dt, num, mh, mx, my, b);
+      const Real a = -O::div(dt, har[q]);
+      st4(rho + 4 * j, a * mh, a * mx, a * my, Real(0));
+    }
+  };
   int timeout = 0;
   if (tid == 0) {
 #pragma unroll
@@ -557,20 +592,22 @@ __global__ void __launch_bounds__(NT)
     } else {
       gather_halo(0);
       cp_async_wait_all();
+      phase_a(0, t_first);
       __syncthreads();
     }
   }
+  // Each iteration: (B) the faces of tile k, then (C) its cells followed by
+  // (A) of tile k+1 (rho is free once every face of tile k is done). Two
+  // block barriers per tile.
   for (int k = 0; !timeout && k < n_tiles; ++k) {
     const int st = k % NS;
     const int tile = t_first + k * t_step;
     const bool has_next = k + 1 < n_tiles;
     if (tid == 0 && k + NS - 1 < n_tiles) issue((k + NS - 1) % NS, tile + (NS - 1) * t_step);
+    // the next tile's own-cell inputs, into registers while the faces run
+    if (has_next) load_cells(tile + t_step);
     const unsigned char* p = smem + st * L.stage;
     const Real* sun = reinterpret_cast<const Real*>(p + L.off_un);
-    const Real* su1 = reinterpret_cast<const Real*>(p + L.off_u1);
-    const Real* sla = reinterpret_cast<const Real*>(p + L.off_lam);
-    const Real* har = reinterpret_cast<const Real*>(p + L.off_harea);
-    const Real* hgn = reinterpret_cast<const Real*>(p + L.off_hgn2);
     const int32_t* rS = reinterpret_cast<const int32_t*>(p + L.off_tS);
     const Real* rg0 = reinterpret_cast<const Real*>(p + L.off_g0);
     const Real* rg1 = reinterpret_cast<const Real*>(p + L.off_g1);
@@ -578,33 +615,6 @@ __global__ void __launch_bounds__(NT)
     const int base = tile * TC;
     const int nc = min(TC, cell_end - base);
     const int nrec = s_nrec[st];
-    const int nh = s_nh[st];
-
-    // (A) mu, rho
-    Real mu[CPT][3], bg[CPT], dzr[CPT];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) {
-      const int j = tid + cc * NT;
-      const V4<Real> c1 = nu1[cc];
-      const V4<Real> la = nla[cc];
-      dzr[cc] = la.w;
-      cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, ngn[cc], dt, num, mu[cc][0], mu[cc][1],
-                     mu[cc][2], bg[cc]);
-      bg[cc] += ndg[cc];
-      const Real a = j < nc ? -O::div(dt, nar[cc]) : Real(0);  // padding: area 0
-      st4(rho + 4 * j, a * mu[cc][0], a * mu[cc][1], a * mu[cc][2], Real(0));
-    }
-    if (has_next) load_cells(tile + t_step);
-    for (int q = tid; q < nh; q += NT) {
-      const int j = TC + q;
-      const V4<Real> c1 = ld4(su1 + 4 * q);
-      const V4<Real> la = ld4(sla + 4 * q);
-      Real mh, mx, my, b;
-      cell_vjp<Real>(c1.x, c1.y, c1.z, la.x, la.y, la.z, hgn[q], dt, num, mh, mx, my, b);
-      const Real a = -O::div(dt, har[q]);
-      st4(rho + 4 * j, a * mh, a * mx, a * my, Real(0));
-    }
-    __syncthreads();
 
     // (B) face records
     for (int r = tid; r < nrec; r += NT) {
@@ -677,6 +687,7 @@ __global__ void __launch_bounds__(NT)
       A.dgn2[base + j] = bg[cc];
     }
     cp_async_wait_all();
+    if (has_next) phase_a((k + 1) % NS, tile + t_step);
     __syncthreads();
   }
   if (timeout && tid == 0) {
