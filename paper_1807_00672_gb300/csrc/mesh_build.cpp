@@ -224,8 +224,8 @@ int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t 
     // Per tile: every face of every tile cell, an interior face whose cells
     // are both in the tile emitted once. Sides: a tile cell by its face slot
     // (face k of tile cell j is slot k * tile + j, encoded -1 - slot), a cell
-    // of another tile by its index in the tile's halo list (>= 0), a wall as
-    // kWall. Records with both cells in the tile come first, then those with a
+    // of another tile as tile + its index in the tile's halo list (where the
+    // kernels stage it, after the tile's cells), a wall as kWall. Records with both cells in the tile come first, then those with a
     // halo side, then walls (fewer divergent warps); within a class, in cell
     // order. Record and halo lists are padded to multiples of 4 entries
     // (null records: both sides kWall, zero length; halo padding repeats the
@@ -264,7 +264,7 @@ int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t 
               halo_pos[jo] = (int32_t)halo.size();
               halo.push_back((int32_t)jo);
             }
-            enc_other = halo_pos[jo];
+            enc_other = tile + halo_pos[jo];  // the cell's place after the tile's cells
             cls = 1;
           }
           // side A is always the edge's left cell

@@ -8,7 +8,8 @@
 namespace swe {
 
 // Encoding of one side of a tile face record:
-//   >= 0             index of a cell of another tile in the tile's halo list
+//   >= 0             tile + q for the cell of another tile at index q of the
+//                    tile's halo list (its place after the tile's cells)
 //   kWall            wall (mirror ghost)
 //   < 0, != kWall    local face slot s = -1 - value: face s / tile of tile cell s % tile
 constexpr int32_t kWall = INT32_MIN;

@@ -640,8 +640,8 @@ __global__ void __launch_bounds__(NT)
           st4(slots + 4 * (-1 - a), gA[0], gA[1], gA[2], gA[3]);
           continue;
         }
-        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
-        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : TC + b;
+        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : a;
+        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : b;
         const V4<Real> UA = ld4(sun + 4 * ia);
         const V4<Real> UB = ld4(sun + 4 * ib);
         const V4<Real> RA = ld4(rho + 4 * ia);
@@ -653,8 +653,8 @@ __global__ void __launch_bounds__(NT)
         continue;
       }
       const bool wall = (b == kSideWall);
-      const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
-      const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (TC - 1)) : TC + b);
+      const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : a;
+      const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (TC - 1)) : b);
       const V4<Real> UA = ld4(sun + 4 * ia);
       const V4<Real> UB = ld4(sun + 4 * ib);
       const V4<Real> RA = ld4(rho + 4 * ia);

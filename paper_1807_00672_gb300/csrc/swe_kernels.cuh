@@ -134,8 +134,9 @@ struct DevState {
 };
 
 // Side codes of packed face records (int16): -1 - slot for a cell of the
-// tile, the halo index (>= 0) for a cell of another tile, kSideWall for a
-// wall (and for side A of a padding record).
+// tile, TC + q (its place in the staged cells) for the cell at index q of
+// the tile's halo list, kSideWall for a wall (and for side A of a padding
+// record).
 constexpr int kSideWall = -32768;
 
 // ---------------------------------------------------------------------------
@@ -1080,8 +1081,8 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
           st4(slots + 4 * (-1 - a), c0, cA1, cA2, 0.0f);
           continue;
         }
-        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
-        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : TC + b;
+        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : a;
+        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : b;
         const V4<Real> A = ld4(xc + 4 * ia);
         const V4<Real> B = ld4(xc + 4 * ib);
         face_flux_f32<false>(A, B, fnx, fny, flen, num, c0, cA1, cA2, cB1, cB2);
@@ -1103,8 +1104,8 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
           st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
           continue;
         }
-        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : TC + a;
-        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : TC + b;
+        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : a;
+        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : b;
         const V4<Real> A = ld4(xc + 4 * ia);
         const V4<Real> B = ld4(xc + 4 * ib);
         Real uA, vA, uB, vB;
