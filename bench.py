@@ -257,7 +257,7 @@ def main():
 
     case = make_case(args.workload)
     if args.adjoint_profile:
-        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=args.precision)
+        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=args.precision, tile=args.tile)
         st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
         tape = swe.Tape(st, 4, 4, [5, 100])
         r = tape.grad(g_h=np.random.default_rng(0).standard_normal(mesh.T))
