@@ -817,9 +817,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // largest per-tile record and halo counts. Each of the NS stages holds one
 // tile: its interleaved cells (h, hu, hv, z), the tile's tc cells followed by
 // its halo cells; its packed face records and their geometry arrays; its halo
-// index list. After the stages: the face slots (c0, c1, c2, -) per face of
-// each tile cell, face-major, and the NS mbarriers. Every offset is a
-// multiple of 16 bytes.
+// index list. After the stages: the face slots per face of each tile cell,
+// face-major, and the NS mbarriers. A slot is (c0, c1, c2, -) in FP64 and
+// (c0, -, c1, c2) in FP32, where the momentum pair sits in the aligned half
+// that the paired FP32 instructions read. Every offset is a multiple of 16
+// bytes.
 struct TileLayout {
   uint32_t ext, rec_cap, halo_cap;
   uint32_t off_cells, off_tS, off_g0, off_g1, off_g2, off_hidx;
@@ -1078,7 +1080,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
           if (a == kSideWall) continue;  // padding record
           const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));
           face_flux_f32<true>(A, A, fnx, fny, flen, num, c0, cA1, cA2, cB1, cB2);
-          st4(slots + 4 * (-1 - a), c0, cA1, cA2, 0.0f);
+          st4(slots + 4 * (-1 - a), c0, 0.0f, cA1, cA2);
           continue;
         }
         const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : a;
@@ -1086,8 +1088,8 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
         const V4<Real> A = ld4(xc + 4 * ia);
         const V4<Real> B = ld4(xc + 4 * ib);
         face_flux_f32<false>(A, B, fnx, fny, flen, num, c0, cA1, cA2, cB1, cB2);
-        if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, 0.0f);
-        if (b < 0) st4(slots + 4 * (-1 - b), -c0, cB1, cB2, 0.0f);
+        if (a < 0) st4(slots + 4 * (-1 - a), c0, 0.0f, cA1, cA2);
+        if (b < 0) st4(slots + 4 * (-1 - b), -c0, 0.0f, cB1, cB2);
       } else {
         Real nx, ny, len;
         Geo<Real>::get(rg0, rg1, rg2, r, nx, ny, len);
@@ -1143,13 +1145,16 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
         two_sum(s1, f2.x, s2, e2);
         R[0] = add_rn(s2, add_rn(e1, e2));
         float2 p1, q1, p2, q2;
-        two_sum2(make_float2(f0.y, f0.z), make_float2(f1.y, f1.z), p1, q1);
-        two_sum2(p1, make_float2(f2.y, f2.z), p2, q2);
+        two_sum2(make_float2(f0.z, f0.w), make_float2(f1.z, f1.w), p1, q1);
+        two_sum2(p1, make_float2(f2.z, f2.w), p2, q2);
         const float2 r = add2(p2, add2(q1, q2));
         R[1] = r.x;
         R[2] = r.y;
       } else {
-        const Real a0[3] = {f0.x, f0.y, f0.z}, a1[3] = {f1.x, f1.y, f1.z}, a2[3] = {f2.x, f2.y, f2.z};
+        constexpr bool kPad = sizeof(Real) == 4;
+        const Real a0[3] = {f0.x, kPad ? f0.z : f0.y, kPad ? f0.w : f0.z};
+        const Real a1[3] = {f1.x, kPad ? f1.z : f1.y, kPad ? f1.w : f1.z};
+        const Real a2[3] = {f2.x, kPad ? f2.z : f2.y, kPad ? f2.w : f2.z};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           if (Comp) {
