@@ -452,7 +452,8 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   std::vector<swe::Chunk> chunks;
   if (kernel == SWE_KERNEL_TILED) {
     m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)geo_arrays, (uint32_t)tile,
-                                      (uint32_t)m->stages, (uint32_t)rec_cap, (uint32_t)halo_cap);
+                                      (uint32_t)m->stages, (uint32_t)rec_cap, (uint32_t)halo_cap,
+                                      (uint32_t)(tile / m->cpt));
     const int occ = (p.precision == SWE_F64) ? blocks_per_sm_tiled<double>(m)
                                              : blocks_per_sm_tiled<float>(m);
     if (occ < 1) {
@@ -509,6 +510,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     }
     L.add(4 * H);
     L.add(sizeof(swe::Chunk) * C);
+    if (m->layout.hreg) L.add(4 * tiles * (int64_t)m->layout.halo_cap);
   }
   if (cudaMalloc((void**)&m->arena.base, L.total) != cudaSuccess) {
     cudaGetLastError();
@@ -542,6 +544,8 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     }
     m->hidx = (int32_t*)m->arena.take(4 * H);
     m->chunks = (swe::Chunk*)m->arena.take(sizeof(swe::Chunk) * C);
+    if (m->layout.hreg)
+      m->hpad = (int32_t*)m->arena.take(4 * tiles * (int64_t)m->layout.halo_cap);
   }
   if (m->arena.overflow) {
     g_cuda_msg = "mesh arena layout";
@@ -623,6 +627,21 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     }
     chk(upload(m, hidx, m->hidx));
     chk(upload(m, chunks, m->chunks));
+    if (m->layout.hreg) {
+      // tile t's halo list at t * halo_cap, padded with the tile's first cell
+      const int64_t hc = m->layout.halo_cap;
+      std::vector<int32_t> hpad(tiles * hc);
+      for (int i = 0; i < n; ++i) {
+        const Scenario& sc = m->scen[i];
+        for (int64_t t = 0; t < sc.ntiles; ++t) {
+          const int64_t tg = sc.tile0 + t;
+          const int64_t q0 = hoff[tg], nq = hoff[tg + 1] - q0;
+          for (int64_t q = 0; q < hc; ++q)
+            hpad[tg * hc + q] = q < nq ? hidx[q0 + q] : (int32_t)(sc.cell0 + t * tile);
+        }
+      }
+      chk(upload(m, hpad, m->hpad));
+    }
   }
   if (st != SWE_OK) {
     swe_mesh_destroy(m);

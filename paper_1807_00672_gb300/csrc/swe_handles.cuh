@@ -77,6 +77,7 @@ struct swe_mesh {
   void *nx = nullptr, *ny = nullptr, *len = nullptr;
   int64_t *toff = nullptr, *hoff = nullptr;
   int32_t *tS = nullptr, *hidx = nullptr;
+  int32_t* hpad = nullptr;  // halo lists padded to halo_cap per tile (layout.hreg)
   void *tg0 = nullptr, *tg1 = nullptr, *tg2 = nullptr;
   void* trec = nullptr;  // FP32: interleaved records {packed sides, nx, ny, l}
   swe::Chunk* chunks = nullptr;  // work of each block of the tiled kernels
@@ -131,6 +132,7 @@ swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
   d.toff = m->toff;
   d.hoff = m->hoff;
   d.hidx = m->hidx;
+  d.hpad = m->hpad;
   d.tS = m->tS;
   d.tg0 = (const Real*)m->tg0;
   d.tg1 = (const Real*)m->tg1;

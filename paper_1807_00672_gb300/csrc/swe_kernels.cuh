@@ -105,6 +105,10 @@ struct DevMesh {
   const int64_t* toff;
   const int64_t* hoff;
   const int32_t* hidx;
+  // the same halo lists padded to halo_cap entries per tile (tile t's at
+  // t * halo_cap; padding repeats the tile's first cell), when TileLayout's
+  // hreg is set
+  const int32_t* hpad;
   // face records: both sides packed as int16 codes (side A in the high half,
   // side B in the low half; see kSideWall), then the geometry arrays of
   // Geo<Real>
@@ -817,7 +821,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // largest per-tile record and halo counts. Each of the NS stages holds one
 // tile: its interleaved cells (h, hu, hv, z), the tile's tc cells followed by
 // its halo cells; its packed face records and their geometry arrays; its halo
-// index list. After the stages: the face slots per face of each tile cell,
+// index list (unless hreg). After the stages: the face slots per face of each tile cell,
 // face-major, and the NS mbarriers. A slot is (c0, c1, c2, -) in FP64 and
 // (c0, -, c1, c2) in FP32, where the momentum pair sits in the aligned half
 // that the paired FP32 instructions read. Every offset is a multiple of 16
@@ -827,14 +831,19 @@ struct TileLayout {
   uint32_t off_cells, off_tS, off_g0, off_g1, off_g2, off_hidx;
   uint32_t stage;
   uint32_t off_slots, off_bars, total;
+  uint32_t hreg;  // 1: halo lists read from DevMesh::hpad into registers, not staged
 };
 
+// nt: threads per block. When no tile has more halo cells than the block has
+// threads, each thread prefetches at most one halo index into a register and
+// the stages hold no halo list.
 inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, uint32_t ns,
-                                   uint32_t rec_cap, uint32_t halo_cap) {
+                                   uint32_t rec_cap, uint32_t halo_cap, uint32_t nt) {
   auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
   TileLayout L{};
   L.rec_cap = rec_cap;
   L.halo_cap = halo_cap;
+  L.hreg = halo_cap <= nt ? 1u : 0u;
   L.ext = tc + halo_cap;
   uint32_t o = 0;
   L.off_cells = o; o += a16(L.ext * 4 * w);
@@ -847,7 +856,7 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
     L.off_g1 = o; o += a16(rec_cap * w);
     L.off_g2 = o; o += geo_arrays > 2 ? a16(rec_cap * w) : 0u;
   }
-  L.off_hidx = o; o += a16(halo_cap * 4);
+  L.off_hidx = o; o += L.hreg ? 0u : a16(halo_cap * 4);
   L.stage = o;
   o = ns * L.stage;
   L.off_slots = o; o += a16(3 * tc * 4 * w);
@@ -917,11 +926,14 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   // Thread 0: record and halo offsets of the next tile to queue, loaded one
   // iteration before they are used so that their latency stays hidden.
   int64_t o_r0 = 0, o_r1 = 0, o_h0 = 0, o_h1 = 0;
+  const bool hreg = L.hreg != 0;
   auto load_offsets = [&](int t) {
     o_r0 = m.toff[t];
     o_r1 = m.toff[t + 1];
-    o_h0 = m.hoff[t];
-    o_h1 = m.hoff[t + 1];
+    if (!hreg) {
+      o_h0 = m.hoff[t];
+      o_h1 = m.hoff[t + 1];
+    }
   };
   // Thread 0: queue the bulk copies of tile t's mesh data (offsets already
   // loaded) into stage st: face records and halo list. The stage's phase
@@ -944,7 +956,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       bulk_g2s(p + L.off_g1, m.tg1 + r0, rb, &bar[st]);
       bulk_g2s(p + L.off_g2, m.tg2 + r0, rb, &bar[st]);
     }
-    if (nh > 0) bulk_g2s(p + L.off_hidx, m.hidx + h0, nh * 4, &bar[st]);
+    if (nh > 0) bulk_g2s(p + L.off_hidx, m.hidx + h0, nh * 4, &bar[st]);  // never with hreg
     pending |= 1u << st;
   };
   // Thread 0: queue tile t's state cells into stage st (arrives on its phase).
@@ -970,17 +982,31 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   // All threads: gather the halo cells of stage st's tile (after its copies
   // landed), one interleaved cell per cp.async group. Lane l of warp w takes
   // entries l W + w (W warps), so every warp gathers about nh / W cells.
+  // With hreg the thread's one entry q_h was prefetched into h_q by
+  // load_halo, and all halo_cap entries are gathered (the padding ones copy
+  // the tile's first cell into slots no record names).
+  constexpr int W = NT / 32;
+  const int q_h = (tid & 31) * W + (tid >> 5);
+  int32_t h_q = 0;
+  auto load_halo = [&](int t) {
+    if (q_h < (int)L.halo_cap) h_q = __ldg(m.hpad + (int64_t)t * L.halo_cap + q_h);
+  };
   auto gather_halo = [&](int st) {
     unsigned char* p = smem + st * L.stage;
-    const int32_t* hl = reinterpret_cast<const int32_t*>(p + L.off_hidx);
     Real* xc = reinterpret_cast<Real*>(p + L.off_cells) + 4 * TC;
-    const int nh = s_nh[st];
-    constexpr int W = NT / 32;
-    for (int q = (tid & 31) * W + (tid >> 5); q < nh; q += NT) {
-      const Real* src = U + 4 * (int64_t)hl[q];
+    auto copy_cell = [&](int q, int32_t i) {
+      const Real* src = U + 4 * (int64_t)i;
 #pragma unroll
-      for (int b = 0; b < (int)sizeof(Real) / 4; ++b) cp_async16(xc + 4 * q + b * (16 / sizeof(Real)), src + b * (16 / sizeof(Real)));
+      for (int b = 0; b < (int)sizeof(Real) / 4; ++b)
+        cp_async16(xc + 4 * q + b * (16 / sizeof(Real)), src + b * (16 / sizeof(Real)));
+    };
+    if (hreg) {
+      if (q_h < (int)L.halo_cap) copy_cell(q_h, h_q);
+      return;
     }
+    const int32_t* hl = reinterpret_cast<const int32_t*>(p + L.off_hidx);
+    const int nh = s_nh[st];
+    for (int q = q_h; q < nh; q += NT) copy_cell(q, hl[q]);
   };
 
   NoMass<Real> mass;  // integrated on demand (k_cfl_tiled), not every step
@@ -996,6 +1022,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
         issue_mesh(i);
       }
   }
+  if (hreg && n_tiles > 0) load_halo(t_first);
   pdl_trigger();
   pdl_wait();
   if (ctl->done) {
@@ -1044,6 +1071,8 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       issue((k + NS - 1) % NS, tile + (NS - 1) * t_step);
       if (k + NS < n_tiles) load_offsets(tile + NS * t_step);
     }
+    // the next tile's halo indices, used by its gather after the face loop
+    if (hreg && has_next) load_halo(tile + t_step);
     const unsigned char* p = smem + st * L.stage;
     const Real* xc = reinterpret_cast<const Real*>(p + L.off_cells);  // [ext][4]
     const int32_t* rS = reinterpret_cast<const int32_t*>(p + L.off_tS);
