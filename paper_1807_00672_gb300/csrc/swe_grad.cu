@@ -162,8 +162,11 @@ struct swe_tape {
   char* ck = nullptr;    // nck + 1 states of Tp interleaved cells: U^0, U^K, U^2K, ..., U^N
   // Two rings of K - 1 replayed states U^{j0+1} .. U^{j0+K-1}: segment seg
   // uses ring seg % 2, so the replay of the next segment (on the side
-  // stream) overlaps the adjoint steps of the current one.
+  // stream) overlaps the adjoint steps of the current one. The last
+  // segment's inner states are kept from the recording in `tail`, so a
+  // backward sweep starts with adjoint steps instead of a replay.
   char* ring[2] = {nullptr, nullptr};
+  char* tail = nullptr;
   cudaStream_t side = nullptr;
   cudaEvent_t replayed[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
   char* lam[2] = {nullptr, nullptr};
@@ -191,6 +194,7 @@ struct swe_tape {
   void* slot(int64_t seg, int64_t r) const {  // state U^{seg K + r} of segment seg
     if (r == 0) return ck + seg * state_bytes();
     if (r == seg_len(seg)) return ck + (seg + 1) * state_bytes();
+    if (seg == nck - 1) return tail + (r - 1) * state_bytes();
     return ring[seg % 2] + (r - 1) * state_bytes();
   }
 };
@@ -242,10 +246,14 @@ swe_status record_t(swe_state* s, swe_tape* t) {
   k_copy_current<Real><<<gs, 256, 0, st>>>(s->ctl, b0, b1, (Real*)t->ck, t->Tp);
   CK(cudaMemcpyAsync(t->gn2, s->gn2, t->w * t->Tp, cudaMemcpyDeviceToDevice, st));
   CK(cudaEventRecord(t->ev[0], st));
+  const int64_t j_tail = (t->nck - 1) * t->K;  // first step of the last segment
   for (int64_t k = 0; k < t->N; ++k) {
     launch_forward(m, dev_state<Real>(s), st);
     k_record_step<Real><<<1, 128, 0, st>>>(s->ctl, b0, b1, t->dts_dev, k, t->gcells, t->G,
                                            t->gauge_dev);
+    if (k + 1 > j_tail && k + 1 < t->N)  // an inner state of the last segment
+      k_copy_current<Real><<<gs, 256, 0, st>>>(s->ctl, b0, b1,
+                                               (Real*)t->slot(t->nck - 1, k + 1 - j_tail), t->Tp);
     if ((k + 1) % t->K == 0 || k + 1 == t->N)
       k_copy_current<Real><<<gs, 256, 0, st>>>(s->ctl, b0, b1,
                                                (Real*)(t->ck + ((k + t->K) / t->K) * t->state_bytes()),
@@ -282,11 +290,9 @@ swe_status grad_t(swe_tape* t, bool seeds_gauge, int* lam_cur) {
   // Replays run one segment ahead on the side stream: segment seg - 1's
   // replay (ring (seg - 1) % 2) overlaps segment seg's adjoint steps; it
   // first waits for the adjoint of segment seg + 1, the ring's last user.
+  // The last segment needs none (its states are in the tail).
   CK(cudaEventRecord(t->consumed[0], st));
   CK(cudaEventRecord(t->consumed[1], st));
-  CK(cudaStreamWaitEvent(t->side, t->consumed[0], 0));
-  replay_segment<Real>(t, t->nck - 1, t->side);
-  CK(cudaEventRecord(t->replayed[(t->nck - 1) % 2], t->side));
   for (int64_t seg = t->nck - 1; seg >= 0; --seg) {
     const int64_t j0 = seg * t->K, j1 = std::min(t->N, j0 + t->K);
     if (seg >= 1) {
@@ -294,7 +300,7 @@ swe_status grad_t(swe_tape* t, bool seeds_gauge, int* lam_cur) {
       replay_segment<Real>(t, seg - 1, t->side);
       CK(cudaEventRecord(t->replayed[(seg - 1) % 2], t->side));
     }
-    CK(cudaStreamWaitEvent(st, t->replayed[seg % 2], 0));
+    if (seg < t->nck - 1) CK(cudaStreamWaitEvent(st, t->replayed[seg % 2], 0));
     for (int64_t j = j1 - 1; j >= j0; --j) {
       const int64_t r = j - j0;
       swe::AdjArgs<Real> a{};
@@ -385,6 +391,7 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   L.add(sb * (t->nck + 1));
   L.add(sb * std::max<int64_t>(1, t->K - 1));
   L.add(sb * std::max<int64_t>(1, t->K - 1));
+  L.add(sb * std::max<int64_t>(1, t->K - 1));  // tail
   L.add(sb); L.add(sb);
   L.add(t->w * t->Tp);  // gn2
   L.add(t->w * t->Tp);  // dgn2
@@ -408,6 +415,7 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   t->ck = (char*)t->arena.take(sb * (t->nck + 1));
   t->ring[0] = (char*)t->arena.take(sb * std::max<int64_t>(1, t->K - 1));
   t->ring[1] = (char*)t->arena.take(sb * std::max<int64_t>(1, t->K - 1));
+  t->tail = (char*)t->arena.take(sb * std::max<int64_t>(1, t->K - 1));
   t->lam[0] = (char*)t->arena.take(sb);
   t->lam[1] = (char*)t->arena.take(sb);
   t->gn2 = t->arena.take(t->w * t->Tp);
