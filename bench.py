@@ -474,7 +474,8 @@ def ensemble_leg(args, stream):
                           use_cache=False)
     mesh = swe.Mesh.ensemble([(c.mesh.xy, c.mesh.tri) for c in cases], precision="f32",
                              tile=tuned["tile"], cells_per_thread=tuned["cells_per_thread"],
-                             stages=tuned["stages"], stream=ctypes_stream(stream))
+                             stages=tuned["stages"], halo_schedule=tuned["halo_schedule"],
+                             stream=ctypes_stream(stream))
     cat = lambda name: np.concatenate([getattr(c, name) for c in cases])
     st = swe.State(mesh, cat("h"), cat("hu"), cat("hv"), cat("z"), cat("n"))
     setup_s = time.perf_counter() - t0
@@ -499,7 +500,8 @@ def ensemble_leg(args, stream):
            "hbm_frac": achieved / peak, "achieved_gbs": achieved, "alg_bytes_per_cell": balg,
            "peak_source": f"{kind} HBM copy bandwidth",
            "shape": {"tile": tuned["tile"], "cells_per_thread": tuned["cells_per_thread"],
-                     "stages": tuned["stages"], "autotuned_on": f"{len(cases[::8])} scenarios"},
+                     "stages": tuned["stages"], "halo_schedule": tuned["halo_schedule"],
+                     "autotuned_on": f"{len(cases[::8])} scenarios"},
            "autotune_trials": [(t["shape"], round(t["sec_per_step"] * 1e6, 1))
                                for t in tuned["trials"] if "sec_per_step" in t],
            "setup_s": setup_s, "scenario_steps": sorted(steps)}

@@ -88,6 +88,13 @@ typedef struct {
   int32_t stages;     /* shared-memory pipeline stages of SWE_KERNEL_TILED (2 or 3);
                          0 = default (2) */
   int32_t cells_per_thread;  /* cells each thread updates per tile (1 or 2); 0 = default (2) */
+  int32_t halo_schedule;     /* when SWE_KERNEL_TILED gathers a tile's halo cells: 0 = default,
+                                after the previous tile's face loop; 1 = at the start of the
+                                previous tile, so the gather overlaps its whole face loop
+                                (faster on some ensembles, slower on single large meshes: a
+                                choice for the autotuner). 1 applies to FP32 meshes with 2
+                                stages whose halo lists fit one entry per thread, and is
+                                ignored otherwise. Results are identical. */
 } swe_params;
 
 typedef struct swe_mesh swe_mesh;
@@ -221,9 +228,10 @@ typedef struct swe_tape swe_tape;
  * and records: every step's dt, the depth at each of the n_gauges cells
  * gauge_cells[j] (caller indices, repeats allowed) after every step into
  * gauge_h[k * n_gauges + j] for step k = 0 .. n_steps-1 (host, may be NULL),
- * and the state every checkpoint_every steps (device memory: about
- * ceil(n_steps / K) + 2K + 1 states, K = checkpoint_every; K = 1 keeps every
- * state and swe_grad then recomputes nothing). The state is
+ * the state every checkpoint_every steps, and the K - 1 inner states of the
+ * last segment (device memory: about ceil(n_steps / K) + 3K states,
+ * K = checkpoint_every; K = 1 keeps every state and swe_grad then recomputes
+ * nothing). The state is
  * left at step n_steps. Synchronises. Returns SWE_ENAN / SWE_EDRY if a step
  * fails (no tape is made). The tape holds the mesh (not the state). */
 swe_status swe_grad_record(swe_state* state, int64_t n_steps, int64_t checkpoint_every,
@@ -235,8 +243,8 @@ swe_status swe_grad_record(swe_state* state, int64_t n_steps, int64_t checkpoint
  * [n_tris each]; g_gauge = dL/d gauge_h [n_steps * n_gauges]. Outputs (host,
  * caller order, any may be NULL): dL/dh, dL/dhu, dL/dhv of the initial state,
  * dL/dz, dL/dn (n >= 0 assumed). Recomputes each segment of checkpoint_every
- * steps from its checkpoint; returns SWE_ESTATE if a recomputed step did not
- * reproduce the recorded dt. Synchronises. */
+ * steps but the last from its checkpoint; returns SWE_ESTATE if a recomputed
+ * step did not reproduce the recorded dt. Synchronises. */
 swe_status swe_grad(swe_tape* tape, const double* g_h, const double* g_hu, const double* g_hv,
                     const double* g_gauge, double* d_h0, double* d_hu0, double* d_hv0, double* d_z,
                     double* d_n);

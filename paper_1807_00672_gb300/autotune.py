@@ -1,6 +1,6 @@
 """Autotuner for the tiled step kernel's shape: cells per tile, cells per
-thread and shared-memory pipeline stages (``swe_params.tile``,
-``cells_per_thread``, ``stages``).
+thread, shared-memory pipeline stages and halo-gather schedule
+(``swe_params.tile``, ``cells_per_thread``, ``stages``, ``halo_schedule``).
 
 The best shape depends on the mesh (how many faces and halo cells a tile
 has, how many tiles each block walks) and on the precision, so it is chosen
@@ -21,10 +21,11 @@ import time
 
 from . import swe
 
-# (tile, cells_per_thread, stages); threads per block = tile / cells_per_thread.
+# (tile, cells_per_thread, stages[, halo_schedule]); threads per block =
+# tile / cells_per_thread; a missing halo_schedule is 0.
 CANDIDATES = (
-    (256, 2, 2), (256, 2, 3), (256, 1, 2), (256, 1, 3),
-    (512, 2, 2), (128, 1, 2), (128, 2, 3),
+    (256, 2, 2), (256, 2, 2, 1), (256, 2, 3), (256, 1, 2), (256, 1, 3),
+    (512, 2, 2), (512, 2, 2, 1), (128, 1, 2), (128, 2, 3),
 )
 
 
@@ -59,9 +60,9 @@ def _store(path, data):
 
 
 def _build(cases, precision, shape, stream):
-    tile, cpt, stages = shape
+    tile, cpt, stages = shape[:3]
     kw = dict(precision=precision, kernel="tiled", tile=tile, cells_per_thread=cpt,
-              stages=stages, stream=stream)
+              stages=stages, halo_schedule=shape[3] if len(shape) > 3 else 0, stream=stream)
     if len(cases) == 1:
         c = cases[0]
         mesh = swe.Mesh(c.mesh.xy, c.mesh.tri, **kw)
@@ -101,12 +102,12 @@ def measure(cases, precision: str, shape, steps: int = 32, warmup: int = 16) -> 
 def tune(cases, precision: str = "f32", *, candidates=CANDIDATES, steps: int = 32,
          use_cache: bool = True, key_cells: int | None = None, key_scenarios: int | None = None,
          log=None) -> dict:
-    """Best (tile, cells_per_thread, stages) for these cases.
+    """Best (tile, cells_per_thread, stages, halo_schedule) for these cases.
 
     ``cases`` may be a representative sample of a larger problem; key_cells
     and key_scenarios then name the full problem's size for the cache key.
-    Returns {"tile", "cells_per_thread", "stages", "sec_per_step", "cached",
-    "trials": [...]}.
+    Returns {"tile", "cells_per_thread", "stages", "halo_schedule",
+    "sec_per_step", "cached", "trials": [...]}.
     """
     import torch
     n_cells = key_cells if key_cells is not None else sum(c.mesh.n_tris for c in cases)
@@ -117,7 +118,7 @@ def tune(cases, precision: str = "f32", *, candidates=CANDIDATES, steps: int = 3
     if use_cache:
         hit = _load(path).get(key)
         if hit:
-            return dict(hit, cached=True, key=key)
+            return dict({"halo_schedule": 0}, **hit, cached=True, key=key)
     trials = []
     for shape in candidates:
         t0 = time.perf_counter()
@@ -134,8 +135,10 @@ def tune(cases, precision: str = "f32", *, candidates=CANDIDATES, steps: int = 3
     if not ok:
         raise RuntimeError("autotune: no candidate shape could run")
     best = min(ok, key=lambda t: t["sec_per_step"])
-    tile, cpt, stages = best["shape"]
-    res = dict(tile=tile, cells_per_thread=cpt, stages=stages, sec_per_step=best["sec_per_step"],
+    tile, cpt, stages = best["shape"][:3]
+    sched = best["shape"][3] if len(best["shape"]) > 3 else 0
+    res = dict(tile=tile, cells_per_thread=cpt, stages=stages, halo_schedule=sched,
+               sec_per_step=best["sec_per_step"],
                sample_cells=sum(c.mesh.n_tris for c in cases), trials=trials)
     if use_cache:
         data = _load(path)

@@ -90,10 +90,10 @@ int grid_for(int64_t n, int threads, int cap) {
 
 // Opts the tiled kernel into its dynamic shared memory and returns its
 // resident blocks per SM (0 if it cannot run with this layout).
-template <typename Real, int NT, int NS, int TC>
+template <typename Real, int NT, int NS, int TC, bool Early = false>
 int prepare_tiled(const swe::TileLayout& L) {
   constexpr bool comp = sizeof(Real) == 4;
-  auto k = swe::k_tiled_step<Real, comp, NT, NS, TC>;
+  auto k = swe::k_tiled_step<Real, comp, NT, NS, TC, Early>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -109,6 +109,9 @@ int prepare_tiled(const swe::TileLayout& L) {
 template <typename Real, int NT, int CPT>
 int blocks_per_sm_tiled_nt(const swe_mesh* m) {
   constexpr int TC = NT * CPT;
+  // the Early kernel (halo_schedule 1) exists for FP32 with 2 stages only
+  if constexpr (sizeof(Real) == 4)
+    if (m->layout.early) return prepare_tiled<Real, NT, 2, TC, true>(m->layout);
   return m->stages == 3 ? prepare_tiled<Real, NT, 3, TC>(m->layout)
                         : prepare_tiled<Real, NT, 2, TC>(m->layout);
 }
@@ -147,6 +150,12 @@ void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe:
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if constexpr (sizeof(Real) == 4) {
+    if (L.early) {
+      cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, true>, dm, ds, num, L);
+      return;
+    }
+  }
   if (m->stages == 3)
     cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 3, TC>, dm, ds, num, L);
   else
@@ -342,6 +351,7 @@ swe_status resolve_params(const swe_params* params, swe_params& p) {
   if (p.tile % p.cells_per_thread != 0 || (nt != 32 && nt != 64 && nt != 128 && nt != 256)) return SWE_EINVAL;
   if (p.stages == 0) p.stages = 2;
   if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
+  if (p.halo_schedule != 0 && p.halo_schedule != 1) return SWE_EINVAL;
   if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
   if (p.kernel == SWE_KERNEL_AUTO) p.kernel = SWE_KERNEL_TILED;
   return SWE_OK;
@@ -454,6 +464,8 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)geo_arrays, (uint32_t)tile,
                                       (uint32_t)m->stages, (uint32_t)rec_cap, (uint32_t)halo_cap,
                                       (uint32_t)(tile / m->cpt));
+    m->layout.early =
+        (m->layout.hreg && p.halo_schedule == 1 && p.precision == SWE_F32 && m->stages == 2) ? 1u : 0u;
     const int occ = (p.precision == SWE_F64) ? blocks_per_sm_tiled<double>(m)
                                              : blocks_per_sm_tiled<float>(m);
     if (occ < 1) {
@@ -742,6 +754,7 @@ void swe_params_default(swe_params* p) {
   p->tile = 0;
   p->stages = 0;
   p->cells_per_thread = 0;
+  p->halo_schedule = 0;
 }
 
 const char* swe_strerror(swe_status s) {

@@ -831,7 +831,8 @@ struct TileLayout {
   uint32_t off_cells, off_tS, off_g0, off_g1, off_g2, off_hidx;
   uint32_t stage;
   uint32_t off_slots, off_bars, total;
-  uint32_t hreg;  // 1: halo lists read from DevMesh::hpad into registers, not staged
+  uint32_t hreg;   // 1: halo lists read from DevMesh::hpad into registers, not staged
+  uint32_t early;  // 1 (with hreg): launch the Early kernel (halo_schedule 1)
 };
 
 // nt: threads per block. When no tile has more halo cells than the block has
@@ -891,7 +892,9 @@ constexpr int tiled_min_blocks() { return (sizeof(Real) == 4 ? 768 : 512) / NT; 
 
 // NT threads per block, tiles of TC cells (a power of two, NT <= TC); a
 // thread updates the tile cells tid, tid + NT, ... (CPT = ceil(TC / NT)).
-template <typename Real, bool Comp, int NT, int NS, int TC>
+// Early: a tile's halo gather is issued at the start of the previous tile's
+// iteration (launched only on layouts with hreg).
+template <typename Real, bool Comp, int NT, int NS, int TC, bool Early = false>
 __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     k_tiled_step(DevMesh<Real> m, DevState<Real> s, Num num, TileLayout L) {
   constexpr int CPT = (TC + NT - 1) / NT;
@@ -927,6 +930,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   // iteration before they are used so that their latency stays hidden.
   int64_t o_r0 = 0, o_r1 = 0, o_h0 = 0, o_h1 = 0;
   const bool hreg = L.hreg != 0;
+  constexpr bool early = Early;
   auto load_offsets = [&](int t) {
     o_r0 = m.toff[t];
     o_r1 = m.toff[t + 1];
@@ -1050,17 +1054,23 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     if (NS - 1 < n_tiles) load_offsets(t_first + (NS - 1) * t_step);
   }
   if (n_tiles > 0) {
+    if (early) {
+      // the gather needs only the indices in registers, not the stage
+      gather_halo(0);
+      if (n_tiles > 1) load_halo(t_first + t_step);
+    }
     const bool ok = (tid == 0) ? wait_stage(0) : true;
     if (__syncthreads_or(!ok)) {
       timeout = 1;
     } else {
-      gather_halo(0);
+      if (!early) gather_halo(0);
       cp_async_wait_all();
       __syncthreads();
     }
   }
   // Each iteration: the face records of tile k, then the cell updates of
-  // tile k while tile k+1's halo gather is in flight. Two block barriers.
+  // tile k while tile k+1's halo gather is in flight (with `early`, issued
+  // before the face records). Two block barriers.
   for (int k = 0; !timeout && k < n_tiles; ++k) {
     const int st = k % NS;
     const int tile = t_first + k * t_step;
@@ -1071,8 +1081,18 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       issue((k + NS - 1) % NS, tile + (NS - 1) * t_step);
       if (k + NS < n_tiles) load_offsets(tile + NS * t_step);
     }
-    // the next tile's halo indices, used by its gather after the face loop
-    if (hreg && has_next) load_halo(tile + t_step);
+    if (early) {
+      // Tile k+1's gather starts now, from indices loaded an iteration ago:
+      // its destination, the halo part of the stage the previous iteration
+      // released, is not written by the stage's bulk copies. Then the
+      // indices of tile k+2.
+      if (has_next) {
+        gather_halo((k + 1) % NS);
+        if (k + 2 < n_tiles) load_halo(tile + 2 * t_step);
+      }
+    } else if (hreg && has_next) {
+      load_halo(tile + t_step);  // used by tile k+1's gather after the face loop
+    }
     const unsigned char* p = smem + st * L.stage;
     const Real* xc = reinterpret_cast<const Real*>(p + L.off_cells);  // [ext][4]
     const int32_t* rS = reinterpret_cast<const int32_t*>(p + L.off_tS);
@@ -1148,13 +1168,14 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
         if (b < 0) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, Real(0));
       }
     }
-    // The next tile's copies must have landed before its halo is gathered.
-    const bool ok = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
+    // The next tile's copies must have landed before its halo is gathered
+    // (with `early` they are waited for at the end of the iteration).
+    const bool ok = (!early && tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
     if (__syncthreads_or(!ok)) {
       timeout = 1;
       break;
     }
-    if (has_next) gather_halo((k + 1) % NS);
+    if (!early && has_next) gather_halo((k + 1) % NS);
 
     // cell updates of tile k
 #pragma unroll
@@ -1202,8 +1223,17 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
                               c1, mass, rate, chk, neg);
       st4(U1 + 4 * (int64_t)(base + j), a1, b1, c1, c.w);
     }
-    cp_async_wait_all();
-    __syncthreads();
+    if (early) {
+      const bool ok_end = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
+      cp_async_wait_all();
+      if (__syncthreads_or(!ok_end)) {
+        timeout = 1;
+        break;
+      }
+    } else {
+      cp_async_wait_all();
+      __syncthreads();
+    }
   }
   // After a timed-out wait, let every copy still in flight land before the
   // block's shared memory is released (bounded as well).

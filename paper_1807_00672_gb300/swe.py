@@ -50,6 +50,7 @@ class Params(ctypes.Structure):
         ("tile", ctypes.c_int32),
         ("stages", ctypes.c_int32),
         ("cells_per_thread", ctypes.c_int32),
+        ("halo_schedule", ctypes.c_int32),
     ]
 
 
@@ -127,7 +128,7 @@ def _check(status: int, what: str):
 
 
 def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, courant=0.7,
-           h_eps=1e-6, stages=0, cells_per_thread=0) -> Params:
+           h_eps=1e-6, stages=0, cells_per_thread=0, halo_schedule=0) -> Params:
     p = Params()
     lib().swe_params_default(ctypes.byref(p))
     p.g, p.courant, p.h_eps = g, courant, h_eps
@@ -137,6 +138,7 @@ def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, coura
     p.tile = tile
     p.stages = stages
     p.cells_per_thread = cells_per_thread
+    p.halo_schedule = halo_schedule
     return p
 
 
@@ -145,25 +147,28 @@ class Mesh:
     scenario meshes (``Mesh.ensemble``, swe_mesh_create_batch)."""
 
     def __init__(self, xy, tri, *, precision="f64", order="morton", kernel="auto", tile=0,
-                 stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6):
+                 stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6,
+                 halo_schedule=0):
         self._build([(xy, tri)], precision, order, kernel, tile, stages, cells_per_thread,
-                    stream, g, courant, h_eps, batch=False)
+                    stream, g, courant, h_eps, batch=False, halo_schedule=halo_schedule)
 
     @classmethod
     def ensemble(cls, meshes, *, precision="f64", order="morton", kernel="auto", tile=0,
-                 stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6):
+                 stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6,
+                 halo_schedule=0):
         """One mesh holding the scenarios ``meshes`` = [(xy, tri), ...]; cell
         arrays are the scenarios' cells concatenated in this order."""
         self = cls.__new__(cls)
         self._build(list(meshes), precision, order, kernel, tile, stages, cells_per_thread,
-                    stream, g, courant, h_eps, batch=True)
+                    stream, g, courant, h_eps, batch=True, halo_schedule=halo_schedule)
         return self
 
     def _build(self, meshes, precision, order, kernel, tile, stages, cpt, stream, g, courant,
-               h_eps, batch):
+               h_eps, batch, halo_schedule=0):
         xys = [_f64(xy).reshape(-1, 2) for xy, _ in meshes]
         tris = [np.ascontiguousarray(t, dtype=np.int32).reshape(-1, 3) for _, t in meshes]
-        self.prm = params(precision, order, kernel, tile, g, courant, h_eps, stages, cpt)
+        self.prm = params(precision, order, kernel, tile, g, courant, h_eps, stages, cpt,
+                          halo_schedule)
         self.precision = precision
         h = ctypes.c_void_p()
         if batch:

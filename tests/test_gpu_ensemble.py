@@ -169,20 +169,39 @@ def test_autotuner_picks_a_measured_shape_and_caches_it(tmp_path, monkeypatch):
     ensure_built()
     monkeypatch.setenv("SWE_TUNE_CACHE", str(tmp_path / "tune.json"))
     cases = scenario_mix()[:3]
-    cand = ((256, 2, 2), (128, 1, 2), (64, 2, 2))
+    cand = ((256, 2, 2), (256, 2, 2, 1), (128, 1, 2), (64, 2, 2))
     r = autotune.tune(cases, "f32", candidates=cand, steps=8)
     assert not r["cached"]
-    assert (r["tile"], r["cells_per_thread"], r["stages"]) in cand
+    picked = (r["tile"], r["cells_per_thread"], r["stages"])
+    assert picked + (r["halo_schedule"],) in cand or (r["halo_schedule"] == 0 and picked in cand)
     timed = [t for t in r["trials"] if "sec_per_step" in t]
-    assert len(timed) == 3
+    assert len(timed) == 4
     assert r["sec_per_step"] == min(t["sec_per_step"] for t in timed)
     again = autotune.tune(cases, "f32", candidates=cand, steps=8)
     assert again["cached"] and again["tile"] == r["tile"]
     # the chosen shape runs and matches the default shape bitwise
     mesh, st = ensemble_state(cases, precision="f32", tile=r["tile"],
-                              cells_per_thread=r["cells_per_thread"], stages=r["stages"])
+                              cells_per_thread=r["cells_per_thread"], stages=r["stages"],
+                              halo_schedule=r["halo_schedule"])
     ref_mesh, ref = ensemble_state(cases, precision="f32")
     st.run(10)
     ref.run(10)
     for a, b in zip(st.fields(), ref.fields()):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("tile,cpt", [(256, 2), (64, 1)])
+def test_early_halo_schedule_is_bitwise_equal(precision, tile, cpt):
+    """halo_schedule = 1 moves only when each tile's halo gather is issued;
+    the arithmetic and its order are those of the default schedule."""
+    cases = scenario_mix()
+    runs = []
+    for sched in (0, 1):
+        mesh, st = ensemble_state(cases, precision=precision, tile=tile, cells_per_thread=cpt,
+                                  halo_schedule=sched)
+        st.run(21)
+        runs.append(st.fields())
+        assert st.info()["err"] == 0
+    for a, b in zip(*runs):
         assert np.array_equal(a, b)

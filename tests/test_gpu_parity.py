@@ -24,7 +24,9 @@ KERNELS = [("tiled", "morton", 256), ("tiled", "morton", 128), ("tiled", "none",
            ("edge", "morton", 0), ("edge", "none", 0)]
 
 # tiled kernel shapes: (cells per tile, cells per thread, stages)
-TILED_SHAPES = [(256, 2, 3), (256, 1, 2), (256, 1, 3), (128, 1, 2), (512, 2, 2), (64, 1, 3)]
+# (tile, cells_per_thread, stages, halo_schedule)
+TILED_SHAPES = [(256, 2, 3, 0), (256, 1, 2, 0), (256, 1, 3, 0), (128, 1, 2, 0), (512, 2, 2, 0),
+                (64, 1, 3, 0), (256, 2, 2, 1), (64, 1, 3, 1)]
 
 
 def small_cases():
@@ -52,17 +54,18 @@ def test_fp64_matches_oracle_100_steps(kernel, order, tile):
         assert info["steps"] == 100 and info["neg"] == 0 and info["err"] == 0
 
 
-@pytest.mark.parametrize("tile,cpt,stages", TILED_SHAPES)
-def test_tiled_shapes_match_oracle(tile, cpt, stages):
-    """Every tiled-kernel shape, FP64 within 1e-11 of the oracle and FP32
-    within its stated error, on a mesh spanning many tiles with a ragged tail."""
+@pytest.mark.parametrize("tile,cpt,stages,sched", TILED_SHAPES)
+def test_tiled_shapes_match_oracle(tile, cpt, stages, sched):
+    """Every tiled-kernel shape and halo-gather schedule, FP64 within 1e-11
+    of the oracle and FP32 within its stated error, on a mesh spanning many
+    tiles with a ragged tail."""
     case = inputs.humps_case(nx=71, ny=29, lx=2_000.0, ly=1_000.0, seed=61)   # 4,118 cells
     ref, _ = oracle_run(case, 60)
     area = ref.mesh.cells()["area"]
     for prec in ("f64", "f32"):
         ensure_built()
         mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=prec, kernel="tiled", tile=tile,
-                        cells_per_thread=cpt, stages=stages)
+                        cells_per_thread=cpt, stages=stages, halo_schedule=sched)
         st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
         st.run(60)
         if prec == "f64":
