@@ -870,10 +870,13 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
 // Tiled one-launch step on interleaved cells (h, hu, hv, z). A block of NT
 // threads walks the tiles of its work chunk (TC = NT * CPT consecutive cells
 // each; see Chunk) through NS shared-memory stages:
-//   - thread 0 queues bulk async copies (TMA) of tile k+NS-1's cell arrays,
-//     face records and halo list while the block works on tile k;
-//   - once tile k+1's copies have landed (mid-iteration k), every thread
-//     gathers its halo cells (16 bytes each) with cp.async;
+//   - thread 0 queues bulk async copies (TMA) of tile k+NS-1's cell arrays
+//     and face records (and its halo list, unless the layout's hreg has each
+//     thread load its halo index into a register) while the block works on
+//     tile k;
+//   - once tile k+1's copies have landed (mid-iteration k; with Early, at the
+//     start of iteration k, which needs only the register indices), every
+//     thread gathers its halo cells (16 bytes each) with cp.async;
 //   (1) every face record of the tile once, velocities formed per side:
 //       interior faces of the tile fill
 //       both of their cells' slots, faces shared with another tile fill only
