@@ -529,19 +529,32 @@ __global__ void __launch_bounds__(NT)
 
   // Per-cell inputs of the thread's own cells, loaded one tile ahead into
   // registers (their latency hides behind the previous tile's face loop).
+  // load_tape_cells: U^{n+1}, g n^2 and area (tape and mesh data);
+  // load_adj_cells: lambda and dL/d(g n^2) (the previous launch's output).
   V4<Real> nu1[CPT], nla[CPT];
   Real ngn[CPT], nar[CPT], ndg[CPT];
-  auto load_cells = [&](int t) {
+  auto load_tape_cells = [&](int t) {
     const int64_t b0 = (int64_t)t * TC;
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) {
       const int64_t i = b0 + tid + cc * NT;
       nu1[cc] = ld4(A.u1 + 4 * i);
-      nla[cc] = ld4(A.lam_in + 4 * i);
       ngn[cc] = A.gn2[i];
       nar[cc] = m.area[i];
+    }
+  };
+  auto load_adj_cells = [&](int t) {
+    const int64_t b0 = (int64_t)t * TC;
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      const int64_t i = b0 + tid + cc * NT;
+      nla[cc] = ld4(A.lam_in + 4 * i);
       ndg[cc] = A.dgn2[i];
     }
+  };
+  auto load_cells = [&](int t) {
+    load_tape_cells(t);
+    load_adj_cells(t);
   };
   // (A) of a tile: mu (registers) and the friction and dL/dz parts of the
   // thread's own cells from the registers load_cells filled, rho of those
@@ -579,12 +592,19 @@ __global__ void __launch_bounds__(NT)
     }
   };
   int timeout = 0;
+  // Programmatic dependent launch: the first tiles' tape states, records and
+  // halo lists and the own cells' tape inputs are fetched while the previous
+  // adjoint step finishes; lambda and dL/d(g n^2), its output, only after
+  // griddepcontrol.wait.
   if (tid == 0) {
 #pragma unroll
     for (int i = 0; i < NS - 1; ++i)
       if (i < n_tiles) issue(i, t_first + i * t_step);
   }
-  if (n_tiles > 0) load_cells(t_first);
+  if (n_tiles > 0) load_tape_cells(t_first);
+  pdl_trigger();
+  pdl_wait();
+  if (n_tiles > 0) load_adj_cells(t_first);
   if (n_tiles > 0) {
     const bool ok = (tid == 0) ? wait_stage(0) : true;
     if (__syncthreads_or(!ok)) {

@@ -86,10 +86,23 @@ __global__ void k_finish_dn(const Real* dgn2, const Real* gn2, double g, Real* o
     out[i] = Real((double)dgn2[i] * 2.0 * sqrt(g * (double)gn2[i]));
 }
 
+// Programmatic dependent launch: a step's blocks fetch their first tiles'
+// tape and mesh data while the previous adjoint step's last blocks finish,
+// and wait for it (griddepcontrol.wait) before reading its output.
 template <typename Real, int NT, int CPT>
 void launch_adjoint_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::AdjArgs<Real>& a,
                        const swe::AdjLayout& L, int grid, cudaStream_t st) {
-  swe::k_tiled_adjoint<Real, NT, 2, CPT><<<grid, NT, L.total, st>>>(dm, a, num_of(m), L);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = L.total;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, swe::k_tiled_adjoint<Real, NT, 2, CPT>, dm, a, num_of(m), L);
 }
 
 template <typename Real, int CPT>
