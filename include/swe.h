@@ -95,6 +95,14 @@ typedef struct {
                                 choice for the autotuner). 1 applies to FP32 meshes with 2
                                 stages whose halo lists fit one entry per thread, and is
                                 ignored otherwise. Results are identical. */
+  int32_t wait_rounds;       /* bounded device waits of SWE_KERNEL_TILED steps (a block waiting
+                                for its tile copies) give up after this many rounds of at most
+                                20 us and latch SWE_ETIMEOUT: 0 = default (50,000 rounds,
+                                about a second); n > 0 = n rounds; -1 = give up at once, so
+                                every step of the mesh ends with SWE_ETIMEOUT (a hook for
+                                testing the timeout path: copies already in flight are still
+                                waited for before a block exits, and nothing is left
+                                running). Other values: SWE_EINVAL. */
 } swe_params;
 
 typedef struct swe_mesh swe_mesh;
@@ -259,14 +267,16 @@ void swe_tape_destroy(swe_tape* tape);
 /* ---------------------------------------------------------------------------
  * Allocation-free step (no counterpart in the paper).
  *
- * For callers that cannot call cudaMalloc: code running inside CUDA graph
- * capture, programs that must not allocate after start-up, and hosts whose
- * device memory comes from their own pool. swe_step_edges_static makes one
- * FP64 step of the two-launch kernels (per-edge face outputs, then each cell
- * gathers its three faces) with every input and output a caller-owned device
- * pointer, and its scratch (per-edge face outputs, per-block partial sums,
- * the control word) in one static device array of SWE_STATIC_SCRATCH_BYTES
- * that each GPU loading the library keeps until the process exits.
+ * For callers that cannot call cudaMalloc: programs that must not allocate
+ * once they are running (fixed memory budgets, real-time loops), and hosts
+ * whose device memory comes from their own pool, which a foreign cudaMalloc
+ * would bypass. swe_step_edges_static makes one FP64 step of the two-launch
+ * kernels (per-edge face outputs, then each cell gathers its three faces)
+ * with every input and output a caller-owned device pointer, and its scratch
+ * (per-edge face outputs, per-block partial sums, the control word) in one
+ * static device array of SWE_STATIC_SCRATCH_BYTES that each GPU loading the
+ * library keeps until the process exits. It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
  *
  * Meshes up to SWE_STATIC_MAX_EDGES edges; larger ones (or n_cells > n_edges,
  * which no triangle mesh has) return SWE_EINVAL before any GPU work.
@@ -293,7 +303,11 @@ void swe_tape_destroy(swe_tape* tape);
  * Host outputs (either may be NULL): *next_dt = CFL dt of the new state,
  * *mass = sum of area * h_out. If either is given the call synchronises the
  * stream and also reports SWE_ENAN / SWE_EDRY; if both are NULL it returns
- * after queueing the work. dt is the length of this step. */
+ * after queueing the work and reports no numerical error (a NaN or an
+ * all-dry state is then seen only in the outputs, and the next call resets
+ * the control word that recorded it). dt is the length of this step: finite
+ * and >= 0, else SWE_EINVAL. Returns SWE_ECUDA if one of its own launches
+ * fails; a CUDA error left pending by earlier work is not consumed. */
 swe_status swe_step_edges_static(int64_t n_cells, int64_t n_edges, const int32_t* edge_left,
                                  const int32_t* edge_right, const double* edge_nx,
                                  const double* edge_ny, const double* edge_len,

@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(NT)
     pending |= 1u << st;
   };
   auto wait_stage = [&](int st) -> bool {
-    const bool ok = mbar_wait(&bar[st], (parity_bits >> st) & 1u);
+    const bool ok = mbar_wait(&bar[st], (parity_bits >> st) & 1u, num.wait_rounds);
     if (ok) {
       parity_bits ^= 1u << st;
       pending &= ~(1u << st);

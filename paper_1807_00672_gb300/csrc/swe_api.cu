@@ -39,6 +39,21 @@ __global__ void k_set_end(Ctl* ctls, int n, double t_end) {
   }
 }
 
+// Caller-order Manning n (FP64, device) -> internal-order g n^2 in the mesh
+// precision, formed in FP64 as the host path forms it: dst[j] = g (n n).
+template <typename Real>
+__global__ void k_gather_gn2(const double* __restrict__ n, const int32_t* __restrict__ perm,
+                             Real* __restrict__ dst, int64_t cells, double g) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cells;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = perm[j];
+    if (c >= 0) {
+      const double nn = n[c];
+      dst[j] = Real(__dmul_rn(g, __dmul_rn(nn, nn)));
+    }
+  }
+}
+
 }  // namespace swe
 
 namespace swe_host {
@@ -301,16 +316,37 @@ void open_end(swe_state* s) {
   s->open_ended = true;
 }
 
-swe_status upload_state_fields(swe_state* s, const double* h, const double* hu, const double* hv) {
+// (h, hu, hv) in caller order -> buffer 0. Host arrays go through the
+// staging buffer; device arrays (on_device) are gathered from directly.
+swe_status upload_state_fields(swe_state* s, const double* h, const double* hu, const double* hv,
+                               bool on_device = false) {
   const swe_mesh* m = s->mesh;
   const double* src[3] = {h, hu, hv};
   void* dst[3] = {s->h[0], s->hu[0], s->hv[0]};
   for (int k = 0; k < 3; ++k) {
-    CK(cudaMemcpyAsync(s->stage, src[k], m->T * 8, cudaMemcpyHostToDevice, m->stream));
-    if (m->prm.precision == SWE_F64) launch_gather<double>(m, s->stage, dst[k], s->stride);
-    else launch_gather<float>(m, s->stage, dst[k], s->stride);
+    const double* from = src[k];
+    if (!on_device) {
+      CK(cudaMemcpyAsync(s->stage, src[k], m->T * 8, cudaMemcpyHostToDevice, m->stream));
+      from = s->stage;
+    }
+    if (m->prm.precision == SWE_F64) launch_gather<double>(m, from, dst[k], s->stride);
+    else launch_gather<float>(m, from, dst[k], s->stride);
   }
   CK(cudaGetLastError());
+  return SWE_OK;
+}
+
+// Orders the mesh stream after the work queued so far on the caller's
+// stream (the device-pointer calls: the caller wrote its buffers there).
+swe_status wait_for_caller(const swe_mesh* m, void* caller_stream) {
+  cudaStream_t cs = (cudaStream_t)caller_stream;
+  if (!cs || cs == m->stream) return SWE_OK;
+  cudaEvent_t ev = nullptr;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(m->stream, ev, 0);
+  cudaEventDestroy(ev);  // released once the recorded work completes
+  if (cuda_failed(e)) return SWE_ECUDA;
   return SWE_OK;
 }
 
@@ -352,6 +388,7 @@ swe_status resolve_params(const swe_params* params, swe_params& p) {
   if (p.stages == 0) p.stages = 2;
   if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
   if (p.halo_schedule != 0 && p.halo_schedule != 1) return SWE_EINVAL;
+  if (p.wait_rounds < -1) return SWE_EINVAL;
   if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
   if (p.kernel == SWE_KERNEL_AUTO) p.kernel = SWE_KERNEL_TILED;
   return SWE_OK;
@@ -675,12 +712,13 @@ void refresh_mass(const swe_state* s) {
   swe::k_mass_sum<<<nscen(m), 256, 0, m->stream>>>(s->ctl, s->partial);
 }
 
-// Scatters buffer b of field k (0 h, 1 hu, 2 hv) to caller order in stage.
-void scatter_field(const swe_state* s, int k, int b) {
+// Scatters buffer b of field k (0 h, 1 hu, 2 hv) to caller order in dst
+// (T doubles of device memory).
+void scatter_field(const swe_state* s, int k, int b, double* dst) {
   const swe_mesh* m = s->mesh;
   const void* src = (k == 0) ? s->h[b] : (k == 1) ? s->hu[b] : s->hv[b];
-  if (m->prm.precision == SWE_F64) launch_scatter<double>(m, src, s->stage, s->stride);
-  else launch_scatter<float>(m, src, s->stage, s->stride);
+  if (m->prm.precision == SWE_F64) launch_scatter<double>(m, src, dst, s->stride);
+  else launch_scatter<float>(m, src, dst, s->stride);
 }
 
 }  // namespace
@@ -755,6 +793,7 @@ void swe_params_default(swe_params* p) {
   p->stages = 0;
   p->cells_per_thread = 0;
   p->halo_schedule = 0;
+  p->wait_rounds = 0;
 }
 
 const char* swe_strerror(swe_status s) {
@@ -813,9 +852,15 @@ void swe_mesh_destroy(swe_mesh* m) {
   release_mesh(m);
 }
 
-swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const double* hv,
-                          const double* z, const double* manning, double manning_const,
-                          swe_state** out) {
+}  // extern "C"
+
+namespace {
+
+// swe_state_init and swe_state_init_device: the fields come from host
+// arrays, or (on_device) from device arrays written on caller_stream.
+swe_status state_init(swe_mesh* m, const double* h, const double* hu, const double* hv,
+                      const double* z, const double* manning, double manning_const,
+                      bool on_device, void* caller_stream, swe_state** out) {
   if (!out) return SWE_EINVAL;
   *out = nullptr;
   if (!m || !h || !hu || !hv || !z) return SWE_EINVAL;
@@ -883,25 +928,42 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
     swe_state_destroy(s);
     return SWE_ECUDA;
   }
-  // Bed and friction coefficient g n^2 (FP64 on the host, caller order).
-  std::vector<double> gn2(T);
-  for (int64_t i = 0; i < T; ++i) {
-    const double nn = manning ? manning[i] : manning_const;
-    gn2[i] = m->prm.g * (nn * nn);
+  if (on_device) st = wait_for_caller(m, caller_stream);
+  // Bed and friction coefficient g n^2 (FP64, caller order): formed on the
+  // host from host arrays or a constant n, on the device from a device n.
+  std::vector<double> gn2;
+  if (!(on_device && manning)) {
+    gn2.resize(T);
+    for (int64_t i = 0; i < T; ++i) {
+      const double nn = manning ? manning[i] : manning_const;
+      gn2[i] = m->prm.g * (nn * nn);
+    }
+  } else if (st == SWE_OK) {
+    const int gg = grid_for(m->Tp, 256, m->sms * 16);
+    if (m->prm.precision == SWE_F64)
+      swe::k_gather_gn2<double><<<gg, 256, 0, m->stream>>>(manning, m->perm, (double*)s->gn2, m->Tp, m->prm.g);
+    else
+      swe::k_gather_gn2<float><<<gg, 256, 0, m->stream>>>(manning, m->perm, (float*)s->gn2, m->Tp, m->prm.g);
   }
-  const double* fields[2] = {z, gn2.data()};
+  const double* fields[2] = {z, gn2.empty() ? nullptr : gn2.data()};
   void* dsts[2] = {s->z, s->gn2};
   for (int k = 0; k < 2 && st == SWE_OK; ++k) {
-    if (cuda_failed(cudaMemcpyAsync(s->stage, fields[k], T * 8, cudaMemcpyHostToDevice, m->stream))) {
-      st = SWE_ECUDA;
-      break;
+    if (!fields[k]) continue;  // g n^2 already gathered on the device
+    const double* from = fields[k];
+    if (!(on_device && k == 0)) {  // host array: through the staging buffer
+      if (cuda_failed(cudaMemcpyAsync(s->stage, fields[k], T * 8, cudaMemcpyHostToDevice, m->stream))) {
+        st = SWE_ECUDA;
+        break;
+      }
+      from = s->stage;
     }
     const int sd = (k == 0) ? s->stride : 1;  // z lives in the cells, gn2 is its own array
-    if (m->prm.precision == SWE_F64) launch_gather<double>(m, s->stage, dsts[k], sd);
-    else launch_gather<float>(m, s->stage, dsts[k], sd);
+    if (m->prm.precision == SWE_F64) launch_gather<double>(m, from, dsts[k], sd);
+    else launch_gather<float>(m, from, dsts[k], sd);
   }
+  if (st == SWE_OK && cuda_failed(cudaGetLastError())) st = SWE_ECUDA;
   if (st == SWE_OK && cuda_failed(cudaStreamSynchronize(m->stream))) st = SWE_ECUDA;
-  if (st == SWE_OK) st = upload_state_fields(s, h, hu, hv);
+  if (st == SWE_OK) st = upload_state_fields(s, h, hu, hv, on_device);
   if (st == SWE_OK) st = reset_and_cfl(s);
   if (st != SWE_OK) {
     swe_state_destroy(s);
@@ -911,9 +973,34 @@ swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const 
   return SWE_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const double* hv,
+                          const double* z, const double* manning, double manning_const,
+                          swe_state** out) {
+  return state_init(m, h, hu, hv, z, manning, manning_const, false, nullptr, out);
+}
+
+swe_status swe_state_init_device(swe_mesh* m, const double* h, const double* hu, const double* hv,
+                                 const double* z, const double* manning, double manning_const,
+                                 void* cuda_stream, swe_state** out) {
+  return state_init(m, h, hu, hv, z, manning, manning_const, true, cuda_stream, out);
+}
+
 swe_status swe_state_set(swe_state* s, const double* h, const double* hu, const double* hv) {
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
   swe_status st = upload_state_fields(s, h, hu, hv);
+  if (st != SWE_OK) return st;
+  return reset_and_cfl(s);
+}
+
+swe_status swe_state_set_device(swe_state* s, const double* h, const double* hu, const double* hv,
+                                void* cuda_stream) {
+  if (!s || !h || !hu || !hv) return SWE_EINVAL;
+  swe_status st = wait_for_caller(s->mesh, cuda_stream);
+  if (st == SWE_OK) st = upload_state_fields(s, h, hu, hv, true);
   if (st != SWE_OK) return st;
   return reset_and_cfl(s);
 }
@@ -964,8 +1051,14 @@ swe_status swe_sync(swe_state* s) {
   return status_all(s);
 }
 
-swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, double* t,
-                        double* mass) {
+}  // extern "C"
+
+namespace {
+
+// swe_copy_out and swe_copy_out_device (to_device: h, hu, hv are device
+// arrays, written by the scatter kernels or device-to-device copies).
+swe_status copy_out(const swe_state* s, double* h, double* hu, double* hv, double* t, double* mass,
+                    bool to_device) {
   if (!s) return SWE_EINVAL;
   const swe_mesh* m = s->mesh;
   const int n = nscen(m);
@@ -977,19 +1070,22 @@ swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, d
   double* dst[3] = {h, hu, hv};
   for (int k = 0; k < 3; ++k) {
     if (!dst[k]) continue;
-    if (same) {
-      scatter_field(s, k, s->host_ctl[0].cur);
-      CK(cudaMemcpyAsync(dst[k], s->stage, m->T * 8, cudaMemcpyDeviceToHost, m->stream));
+    const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (same && to_device) {
+      scatter_field(s, k, s->host_ctl[0].cur, dst[k]);
+    } else if (same) {
+      scatter_field(s, k, s->host_ctl[0].cur, s->stage);
+      CK(cudaMemcpyAsync(dst[k], s->stage, m->T * 8, kind, m->stream));
     } else {
       // Scenarios that stopped at different step counts sit in different
       // buffers: copy each one's range from the buffer it is in.
       for (int b = 0; b < 2; ++b) {
-        scatter_field(s, k, b);
+        scatter_field(s, k, b, s->stage);
         for (int i = 0; i < n; ++i) {
           if (s->host_ctl[i].cur != b) continue;
           const Scenario& sc = m->scen[i];
-          CK(cudaMemcpyAsync(dst[k] + sc.caller0, s->stage + sc.caller0, sc.ncells * 8,
-                             cudaMemcpyDeviceToHost, m->stream));
+          CK(cudaMemcpyAsync(dst[k] + sc.caller0, s->stage + sc.caller0, sc.ncells * 8, kind,
+                             m->stream));
         }
       }
     }
@@ -1003,6 +1099,24 @@ swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, d
     *mass = sum;
   }
   return status_all(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, double* t,
+                        double* mass) {
+  return copy_out(s, h, hu, hv, t, mass, false);
+}
+
+swe_status swe_copy_out_device(const swe_state* s, double* h, double* hu, double* hv, double* t,
+                               double* mass, void* cuda_stream) {
+  if (!s) return SWE_EINVAL;
+  // the destinations may still be in use by the caller's earlier work
+  swe_status st = wait_for_caller(s->mesh, cuda_stream);
+  if (st != SWE_OK) return st;
+  return copy_out(s, h, hu, hv, t, mass, true);
 }
 
 swe_status swe_state_info(const swe_state* s, int64_t* info) {

@@ -485,7 +485,7 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   if (s->host_ctl[0].err) {
     const int e = s->host_ctl[0].err;
     free_tape(t);
-    return (e & swe::kErrNan) ? SWE_ENAN : (e & swe::kErrDry) ? SWE_EDRY : SWE_ETIMEOUT;
+    return (e & swe::kErrTimeout) ? SWE_ETIMEOUT : (e & swe::kErrNan) ? SWE_ENAN : SWE_EDRY;
   }
   if (s->host_ctl[0].steps - steps0 != t->N) return fail(SWE_ESTATE);
   t->dts.resize(t->N);
@@ -498,13 +498,30 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   return SWE_OK;
 }
 
-swe_status swe_grad(swe_tape* t, const double* g_h, const double* g_hu, const double* g_hv,
-                    const double* g_gauge, double* d_h0, double* d_hu0, double* d_hv0, double* d_z,
-                    double* d_n) {
+}  // extern "C"
+
+namespace {
+
+// swe_grad and swe_grad_device: seeds and outputs in host memory, or
+// (on_device) in device memory ordered on caller_stream.
+swe_status grad(swe_tape* t, const double* g_h, const double* g_hu, const double* g_hv,
+                const double* g_gauge, double* d_h0, double* d_hu0, double* d_hv0, double* d_z,
+                double* d_n, bool on_device, void* caller_stream) {
   if (!t) return SWE_EINVAL;
   swe_mesh* m = t->mesh;
   cudaStream_t st = m->stream;
   const size_t sb = t->state_bytes();
+  if (on_device && caller_stream && (cudaStream_t)caller_stream != st) {
+    // the seeds were written, and the outputs may still be read, on the
+    // caller's stream
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, (cudaStream_t)caller_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    cudaEventDestroy(ev);
+    CK(e);
+  }
+  const cudaMemcpyKind in_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CK(cudaMemsetAsync(t->lam[0], 0, sb, st));
   CK(cudaMemsetAsync(t->lam[1], 0, sb, st));
   CK(cudaMemsetAsync(t->dgn2, 0, t->w * t->Tp, st));
@@ -513,11 +530,15 @@ swe_status swe_grad(swe_tape* t, const double* g_h, const double* g_hu, const do
   const double* seeds[3] = {g_h, g_hu, g_hv};
   for (int c = 0; c < 3; ++c) {
     if (!seeds[c]) continue;
-    CK(cudaMemcpyAsync(t->stage, seeds[c], 8 * t->T, cudaMemcpyHostToDevice, st));
-    gather_any(m, t->stage, t->lam[0] + c * t->w, 4);
+    const double* from = seeds[c];
+    if (!on_device) {
+      CK(cudaMemcpyAsync(t->stage, seeds[c], 8 * t->T, cudaMemcpyHostToDevice, st));
+      from = t->stage;
+    }
+    gather_any(m, from, t->lam[0] + c * t->w, 4);
   }
   const bool gseed = g_gauge && t->G > 0;
-  if (gseed) CK(cudaMemcpyAsync(t->gseed_dev, g_gauge, 8 * t->N * t->G, cudaMemcpyHostToDevice, st));
+  if (gseed) CK(cudaMemcpyAsync(t->gseed_dev, g_gauge, 8 * t->N * t->G, in_kind, st));
   CK(cudaEventRecord(t->ev[0], st));
   int cur = 0;
   swe_status r = m->prm.precision == SWE_F64 ? grad_t<double>(t, gseed, &cur)
@@ -527,6 +548,10 @@ swe_status swe_grad(swe_tape* t, const double* g_h, const double* g_hu, const do
   double* outs[4] = {d_h0, d_hu0, d_hv0, d_z};
   for (int c = 0; c < 4; ++c) {
     if (!outs[c]) continue;
+    if (on_device) {
+      scatter_any(m, t->lam[cur] + c * t->w, outs[c], 4);
+      continue;
+    }
     scatter_any(m, t->lam[cur] + c * t->w, t->stage, 4);
     CK(cudaMemcpyAsync(outs[c], t->stage, 8 * t->T, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -539,8 +564,12 @@ swe_status swe_grad(swe_tape* t, const double* g_h, const double* g_hu, const do
     else
       k_finish_dn<float><<<gs, 256, 0, st>>>((const float*)t->dgn2, (const float*)t->gn2, m->prm.g,
                                              (float*)t->scratch, t->Tp);
-    scatter_any(m, t->scratch, t->stage, 1);
-    CK(cudaMemcpyAsync(d_n, t->stage, 8 * t->T, cudaMemcpyDeviceToHost, st));
+    if (on_device) {
+      scatter_any(m, t->scratch, d_n, 1);
+    } else {
+      scatter_any(m, t->scratch, t->stage, 1);
+      CK(cudaMemcpyAsync(d_n, t->stage, 8 * t->T, cudaMemcpyDeviceToHost, st));
+    }
   }
   int err = 0;
   CK(cudaMemcpyAsync(&err, t->err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -549,6 +578,39 @@ swe_status swe_grad(swe_tape* t, const double* g_h, const double* g_hu, const do
   CK(cudaEventElapsedTime(&t->grad_ms, t->ev[0], t->ev[1]));
   if (err & swe::kErrTimeout) return SWE_ETIMEOUT;
   if (err) return SWE_ESTATE;  // the replay did not reproduce the recorded steps
+  return SWE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+swe_status swe_grad(swe_tape* t, const double* g_h, const double* g_hu, const double* g_hv,
+                    const double* g_gauge, double* d_h0, double* d_hu0, double* d_hv0, double* d_z,
+                    double* d_n) {
+  return grad(t, g_h, g_hu, g_hv, g_gauge, d_h0, d_hu0, d_hv0, d_z, d_n, false, nullptr);
+}
+
+swe_status swe_grad_device(swe_tape* t, const double* g_h, const double* g_hu, const double* g_hv,
+                           const double* g_gauge, double* d_h0, double* d_hu0, double* d_hv0,
+                           double* d_z, double* d_n, void* cuda_stream) {
+  return grad(t, g_h, g_hu, g_hv, g_gauge, d_h0, d_hu0, d_hv0, d_z, d_n, true, cuda_stream);
+}
+
+swe_status swe_tape_gauges_device(const swe_tape* t, double* gauge_h, void* cuda_stream) {
+  if (!t || (!gauge_h && t->G > 0)) return SWE_EINVAL;
+  if (t->G == 0) return SWE_OK;
+  cudaStream_t st = t->mesh->stream;
+  if (cuda_stream && (cudaStream_t)cuda_stream != st) {
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, (cudaStream_t)cuda_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    cudaEventDestroy(ev);
+    CK(e);
+  }
+  CK(cudaMemcpyAsync(gauge_h, t->gauge_dev, 8 * t->N * t->G, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
   return SWE_OK;
 }
 

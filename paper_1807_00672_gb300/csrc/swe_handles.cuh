@@ -109,7 +109,7 @@ namespace swe_host {
 inline int nscen(const swe_mesh* m) { return (int)m->scen.size(); }
 
 inline swe::Num num_of(const swe_mesh* m) {
-  return swe::make_num(m->prm.g, m->prm.courant, m->prm.h_eps);
+  return swe::make_num(m->prm.g, m->prm.courant, m->prm.h_eps, m->prm.wait_rounds);
 }
 
 template <typename Real>

@@ -54,6 +54,12 @@ constexpr int kErrNan = 1;
 constexpr int kErrDry = 2;
 constexpr int kErrTimeout = 4;
 
+// Bounded device waits: a waiting thread sleeps in try_wait for up to
+// kSuspendNs per round instead of spinning; after kWaitLimit rounds (about a
+// second) the wait gives up and the kernel latches kErrTimeout.
+constexpr uint32_t kSuspendNs = 20000;
+constexpr uint32_t kWaitLimit = 50000;
+
 struct Num {
   double g;
   double courant;
@@ -62,13 +68,19 @@ struct Num {
   // h > h_eps_f32 (no float lies in (h_eps_f32, h_eps]), so the FP32 path
   // takes every dry-depth decision as an FP64 comparison would.
   float h_eps_f32;
+  // Rounds a step's bounded waits for its copies try before giving up
+  // (kWaitLimit by default; 0 gives up at once). Waits that drain copies
+  // already in flight before a block exits always use kWaitLimit.
+  uint32_t wait_rounds;
 };
 
-// Numerics of a run; h_eps_f32 derived from h_eps on the host.
-inline Num make_num(double g, double courant, double h_eps) {
+// Numerics of a run; h_eps_f32 derived from h_eps on the host. wait: the
+// wait_rounds setting of swe_params (0 default, -1 none, else rounds).
+inline Num make_num(double g, double courant, double h_eps, int32_t wait = 0) {
   float f = (float)h_eps;
   if ((double)f > h_eps) f = std::nextafter(f, -INFINITY);
-  return Num{g, courant, h_eps, f};
+  const uint32_t rounds = wait == 0 ? kWaitLimit : (wait < 0 ? 0u : (uint32_t)wait);
+  return Num{g, courant, h_eps, f, rounds};
 }
 
 // Work of one block of the tiled kernels: the ntiles tiles tile0 + k stride
@@ -634,7 +646,7 @@ __device__ void finish_launch(Ctl* ctl, double* partial, long long part, long lo
     }
     int err = atomicOr(&ctl->err, 0);
     const double maxrate = __longlong_as_double((long long)bits);
-    if (!(maxrate > 0.0)) err |= kErrDry;
+    if (!(maxrate > 0.0) && !(err & kErrTimeout)) err |= kErrDry;  // blocks that gave up add no rate
     if (err) {
       atomicOr(&ctl->err, err);
       ctl->done = 1;
@@ -744,11 +756,6 @@ __global__ void __launch_bounds__(256) k_cell_update(DevMesh<Real> m, DevState<R
 // ---------------------------------------------------------------------------
 // TMA bulk copies, cp.async gathers and mbarriers (inline PTX).
 // ---------------------------------------------------------------------------
-// A waiting thread sleeps in try_wait for up to kSuspendNs per round instead
-// of spinning; after kWaitLimit rounds (about a second) the wait gives up.
-constexpr uint32_t kSuspendNs = 20000;
-constexpr uint32_t kWaitLimit = 50000;
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -796,9 +803,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false if it never came.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i)
+// Bounded wait for the phase with the given parity: at most `rounds` rounds
+// of try_wait; false if the phase never came.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t rounds = kWaitLimit) {
+  for (uint32_t i = 0; i < rounds; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -979,7 +987,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   };
   // Thread 0: wait for stage st's copies.
   auto wait_stage = [&](int st) -> bool {
-    const bool ok = mbar_wait(&bar[st], (parity_bits >> st) & 1u);
+    const bool ok = mbar_wait(&bar[st], (parity_bits >> st) & 1u, num.wait_rounds);
     if (ok) {
       parity_bits ^= 1u << st;
       pending &= ~(1u << st);
@@ -1065,6 +1073,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     const bool ok = (tid == 0) ? wait_stage(0) : true;
     if (__syncthreads_or(!ok)) {
       timeout = 1;
+      cp_async_wait_all();  // the early gather of tile 0 may be in flight
     } else {
       if (!early) gather_halo(0);
       cp_async_wait_all();

@@ -1,15 +1,15 @@
 // swe_step_edges_static: one FP64 step of the two-launch kernels (per-edge
 // face outputs, then the per-cell gather and update) that allocates nothing.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (allocation is not allowed there), programs that must not
-// allocate after start-up (fixed memory budgets, real-time loops), and hosts
-// whose device memory belongs to their own pool or arena, where a foreign
-// cudaMalloc would bypass that pool's accounting and may synchronise the
-// device. This entry point takes every input and output as a device pointer
-// from the caller, and keeps its scratch (the per-edge face outputs, the
-// per-block mass partial sums and the step control word) in the file-scope
-// device array below, sized at build time.
+// Some callers cannot call cudaMalloc: programs that must not allocate once
+// they are running (fixed memory budgets, real-time loops whose timing an
+// allocation would disturb), and hosts whose device memory belongs to their
+// own pool or arena, where a foreign cudaMalloc would bypass that pool's
+// accounting and may synchronise the device. This entry point takes every
+// input and output as a device pointer from the caller, and keeps its
+// scratch (the per-edge face outputs, the per-block mass partial sums and
+// the step control word) in the file-scope device array below, sized at
+// build time.
 //
 // The scratch array exists once per GPU that loads this library and stays
 // allocated until the process exits. Every call uses the same array and
@@ -18,7 +18,9 @@
 // GPU (other streams, other host threads) race on the array and give wrong
 // results: serialise them.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
+#include <utility>
 
 #include "../../include/swe.h"
 #include "swe_kernels.cuh"
@@ -79,6 +81,19 @@ __global__ void k_static_begin(swe::Ctl* ctl, double dt) {
   *ctl = c;
 }
 
+// Launches kernel<<<grid, block, 0, stream>>>(args...) and returns the
+// launch's own status.
+template <typename... Params, typename... Args>
+cudaError_t launch(void (*kernel)(Params...), int grid, int block, cudaStream_t stream,
+                   Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 }  // namespace
 
 extern "C" swe_status swe_step_edges_static(
@@ -90,8 +105,8 @@ extern "C" swe_status swe_step_edges_static(
     double* next_dt, double* mass, void* cuda_stream) {
   if (n_cells <= 0 || n_edges <= 0 || !edge_left || !edge_right || !edge_nx || !edge_ny ||
       !edge_len || !cell_face || !cell_area || !cell_perim_over_area || !gn2 || !z || !h || !hu ||
-      !hv || !h_out || !hu_out || !hv_out || !(dt >= 0.0) || !(g > 0.0) || !(courant > 0.0) ||
-      !(h_eps >= 0.0))
+      !hv || !h_out || !hu_out || !hv_out || !(dt >= 0.0) || !std::isfinite(dt) || !(g > 0.0) ||
+      !(courant > 0.0) || !(h_eps >= 0.0))
     return SWE_EINVAL;
   if (n_edges > SWE_STATIC_MAX_EDGES || n_cells > n_edges) return SWE_EINVAL;
   int dev = 0;
@@ -137,11 +152,18 @@ extern "C" swe_status swe_step_edges_static(
 
   const int ge = (int)std::min<int64_t>((n_edges + 255) / 256, g_grid_edge[dev]);
   const int gc = (int)std::min<int64_t>((n_cells + 255) / 256, g_grid_cell[dev]);
-  k_static_begin<<<1, 1, 0, stream>>>(ctl, dt);
-  swe::k_edge_flux<double><<<ge, 256, 0, stream>>>(m, s, num);
-  swe::k_cell_update<double, false><<<gc, 256, 0, stream>>>(m, s, num);
-  if (mass) swe::k_mass_sum<<<1, 256, 0, stream>>>(ctl, partial);
-  if (cudaGetLastError() != cudaSuccess) return SWE_ECUDA;
+  // Each launch's own status is checked (a CUDA error left pending by the
+  // caller's earlier work is neither reported as this call's nor cleared).
+  auto launch_failed = [](cudaError_t e) {
+    if (e == cudaSuccess) return false;
+    cudaGetLastError();  // clear this launch's error
+    return true;
+  };
+  if (launch_failed(launch(k_static_begin, 1, 1, stream, ctl, dt)) ||
+      launch_failed(launch(swe::k_edge_flux<double>, ge, 256, stream, m, s, num)) ||
+      launch_failed(launch(swe::k_cell_update<double, false>, gc, 256, stream, m, s, num)) ||
+      (mass && launch_failed(launch(swe::k_mass_sum, 1, 256, stream, ctl, partial))))
+    return SWE_ECUDA;
   if (next_dt || mass) {
     swe::Ctl c;
     if (cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||

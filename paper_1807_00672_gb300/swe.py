@@ -51,6 +51,7 @@ class Params(ctypes.Structure):
         ("stages", ctypes.c_int32),
         ("cells_per_thread", ctypes.c_int32),
         ("halo_schedule", ctypes.c_int32),
+        ("wait_rounds", ctypes.c_int32),
     ]
 
 
@@ -128,7 +129,7 @@ def _check(status: int, what: str):
 
 
 def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, courant=0.7,
-           h_eps=1e-6, stages=0, cells_per_thread=0, halo_schedule=0) -> Params:
+           h_eps=1e-6, stages=0, cells_per_thread=0, halo_schedule=0, wait_rounds=0) -> Params:
     p = Params()
     lib().swe_params_default(ctypes.byref(p))
     p.g, p.courant, p.h_eps = g, courant, h_eps
@@ -139,6 +140,7 @@ def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, coura
     p.stages = stages
     p.cells_per_thread = cells_per_thread
     p.halo_schedule = halo_schedule
+    p.wait_rounds = wait_rounds
     return p
 
 
@@ -148,9 +150,10 @@ class Mesh:
 
     def __init__(self, xy, tri, *, precision="f64", order="morton", kernel="auto", tile=0,
                  stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6,
-                 halo_schedule=0):
+                 halo_schedule=0, wait_rounds=0):
         self._build([(xy, tri)], precision, order, kernel, tile, stages, cells_per_thread,
-                    stream, g, courant, h_eps, batch=False, halo_schedule=halo_schedule)
+                    stream, g, courant, h_eps, batch=False, halo_schedule=halo_schedule,
+                    wait_rounds=wait_rounds)
 
     @classmethod
     def ensemble(cls, meshes, *, precision="f64", order="morton", kernel="auto", tile=0,
@@ -164,11 +167,11 @@ class Mesh:
         return self
 
     def _build(self, meshes, precision, order, kernel, tile, stages, cpt, stream, g, courant,
-               h_eps, batch, halo_schedule=0):
+               h_eps, batch, halo_schedule=0, wait_rounds=0):
         xys = [_f64(xy).reshape(-1, 2) for xy, _ in meshes]
         tris = [np.ascontiguousarray(t, dtype=np.int32).reshape(-1, 3) for _, t in meshes]
         self.prm = params(precision, order, kernel, tile, g, courant, h_eps, stages, cpt,
-                          halo_schedule)
+                          halo_schedule, wait_rounds)
         self.precision = precision
         h = ctypes.c_void_p()
         if batch:

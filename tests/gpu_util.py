@@ -31,25 +31,44 @@ def rel_err(a: np.ndarray, ref: np.ndarray) -> float:
     return d / scale if scale > 0 else d
 
 
-def momentum_scale(h_ref, hu_ref, hv_ref, g=9.81) -> float:
-    """Scale of the discharge error: the larger of the reference's largest
-    |(hu, hv)| and the Froude-1 discharge h_max sqrt(g h_max). A still lake
-    has |(hu, hv)| at round-off, which would make max |q_ref| meaningless as a
-    denominator; the momentum fluxes it comes from are of size g h^2 / 2."""
-    hmax = float(np.abs(h_ref).max())
-    qmax = float(np.hypot(hu_ref, hv_ref).max()) if hu_ref.size else 0.0
-    return max(qmax, hmax * np.sqrt(g * hmax))
+def froude_scale(h_ref, g=9.81) -> float:
+    """h_max sqrt(g h_max): the discharge of a Froude-1 flow at the largest
+    depth. Used as the error scale of a discharge field only where that
+    field is round-off (still water), which would make max |q_ref| a
+    meaningless denominator."""
+    hmax = float(np.abs(h_ref).max()) if h_ref.size else 0.0
+    return hmax * np.sqrt(g * hmax)
+
+
+def field_rel_err(a, ref, h_ref, g=9.81, roundoff=1e-6) -> tuple[float, str]:
+    """max |a - ref| / max |ref| per field (Eq. 4's state components); for a
+    field whose largest value is at round-off level (below roundoff times
+    the Froude-1 discharge, i.e. still water) the denominator is the
+    Froude-1 discharge instead. Returns (error, which denominator)."""
+    d = float(np.abs(a - ref).max()) if a.size else 0.0
+    fmax = float(np.abs(ref).max()) if ref.size else 0.0
+    fs = froude_scale(h_ref, g)
+    if fmax > roundoff * fs:
+        return d / fmax, "max|ref|"
+    return (d / fs if fs > 0 else d), "froude"
 
 
 def field_errors(st, ref):
-    """Per field max |gpu - oracle| over cells, divided by max |h_ref| for h
-    and by momentum_scale for hu, hv."""
+    """Per field max |gpu - oracle| over cells divided by the field's own
+    max |ref| (hu and hv on still water: by the Froude-1 discharge)."""
     h, hu, hv = st.fields()
-    qs = momentum_scale(ref.h, ref.hu, ref.hv)
-    errs = dict(h=rel_err(h, ref.h),
-                hu=float(np.abs(hu - ref.hu).max()) / qs,
-                hv=float(np.abs(hv - ref.hv).max()) / qs)
-    return errs, (h, hu, hv)
+    return errors_of((h, hu, hv), (ref.h, ref.hu, ref.hv)), (h, hu, hv)
+
+
+def errors_of(got, want):
+    """field_errors on arrays: got, want = (h, hu, hv) each."""
+    errs = {}
+    for name, a, r in zip(("h", "hu", "hv"), got, want):
+        if name == "h":
+            errs[name] = rel_err(a, r)
+        else:
+            errs[name], _ = field_rel_err(a, r, want[0])
+    return errs
 
 
 def l1_linf(a, ref, area):

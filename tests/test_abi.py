@@ -42,7 +42,7 @@ def test_strerror_and_defaults(L):
     L.swe_params_default(ctypes.byref(p))
     assert (p.g, p.courant, p.h_eps) == (9.81, 0.7, 1e-6)
     assert (p.precision, p.order, p.kernel, p.tile, p.stages, p.cells_per_thread,
-            p.halo_schedule) == (0, 1, 0, 0, 0, 0, 0)
+            p.halo_schedule, p.wait_rounds) == (0, 1, 0, 0, 0, 0, 0, 0)
 
 
 def _create(xy, tri, prm=None):
@@ -89,7 +89,7 @@ def test_invalid_meshes_rejected_on_the_host(L, bad):
 
 @pytest.mark.parametrize("field,val", [("precision", 7), ("order", 5), ("kernel", 9), ("tile", 100),
                                        ("stages", 5), ("cells_per_thread", 3),
-                                       ("halo_schedule", 2)])
+                                       ("halo_schedule", 2), ("wait_rounds", -2)])
 def test_bad_params_rejected(L, field, val):
     m = inputs.jittered_grid(3, 3, 3.0, 3.0)
     p = swe.params()

@@ -1,9 +1,10 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Bar: the FP64 path matches the oracle to 1e-11 relative after 100 steps:
-per field, the max error over cells divided by max |h_ref| for h and by the
-discharge scale max(max |q_ref|, h_max sqrt(g h_max)) for hu and hv. The FP32 path's
-L1/Linf errors against the FP64 oracle are stated and gated loosely.
+per field f in (h, hu, hv), max over cells of |f_gpu - f_oracle| divided by
+max |f_oracle|; a discharge field that is itself at round-off (still water)
+is divided by the Froude-1 discharge h_max sqrt(g h_max) instead. The FP32
+path's L1/Linf errors against the FP64 oracle are stated and gated loosely.
 """
 import math
 
