@@ -157,27 +157,56 @@ void swe_mesh_destroy(swe_mesh* mesh);
 /* Creates a state on a mesh from host arrays of n_tris values each, caller order:
  * depth h (m), discharges hu, hv (m^2/s), bed z (m), per-cell Manning n
  * (s/m^{1/3}) or NULL to use manning_const everywhere. Sets t = 0 and computes
- * the first CFL time step. Returns SWE_EDRY if no cell is wet. */
+ * the first CFL time step (Sec. 2.2, Courant 0.7) from this state. The
+ * fields are copied to the device here, once (Sec. 2.3: the state stays on
+ * the device between steps). Returns SWE_EDRY if no cell is wet, SWE_ENAN if
+ * a value is not finite. */
 swe_status swe_state_init(swe_mesh* mesh, const double* h, const double* hu, const double* hv,
                           const double* z, const double* manning, double manning_const,
                           swe_state** out);
 
+/* swe_state_init with DEVICE arrays (FP64, caller order, on the mesh's
+ * device; e.g. the data pointers of contiguous float64 torch CUDA tensors):
+ * h, hu, hv, z and manning (or NULL and manning_const). cuda_stream is the
+ * stream the caller wrote them on (NULL or the mesh's stream: no extra
+ * ordering); the library's stream waits for the work queued there so far.
+ * Nothing goes through host memory. Synchronises the library's stream before
+ * returning, so the caller may reuse the arrays at once. Same results,
+ * bitwise, as swe_state_init with the same values. */
+swe_status swe_state_init_device(swe_mesh* mesh, const double* h, const double* hu,
+                                 const double* hv, const double* z, const double* manning,
+                                 double manning_const, void* cuda_stream, swe_state** out);
+
 /* Replaces (h, hu, hv) from host arrays (caller order) and resets t = 0 and
- * the step count; bed and friction stay. */
+ * the step count; bed and friction stay. The next CFL time step is
+ * recomputed from the new state (Sec. 2.2). */
 swe_status swe_state_set(swe_state* state, const double* h, const double* hu, const double* hv);
 
-/* One step with the current CFL time step (no end-time clamp). Synchronises;
- * *dt_used (may be NULL) receives the step's dt (scenario 0's on an
- * ensemble: every scenario steps with its own CFL dt). */
+/* swe_state_set with DEVICE arrays (FP64, caller order), ordered after the
+ * work queued on cuda_stream as swe_state_init_device is. Synchronises. */
+swe_status swe_state_set_device(swe_state* state, const double* h, const double* hu,
+                                const double* hv, void* cuda_stream);
+
+/* One explicit Euler step (Eq. 4) with the current CFL time step (no
+ * end-time clamp): per face the HLLC flux of the hydrostatically
+ * reconstructed states (Sec. 2.2) in the face frame of Eq. 3, per cell the
+ * sum over its three faces and the update U - dt / Omega * sum, then the
+ * semi-implicit Manning friction (Sec. 2.2) and the CFL time step of the new
+ * state (Courant 0.7). Synchronises; *dt_used (may be NULL) receives the
+ * step's dt (scenario 0's on an ensemble: every scenario steps with its own
+ * CFL dt). */
 swe_status swe_step(swe_state* state, double* dt_used);
 
-/* Queues n_steps CFL steps without an end time and returns without
- * synchronising (device errors are reported by the next synchronising call).
- * Steps are replayed from captured CUDA graphs. */
+/* Queues n_steps steps of swe_step (Eq. 4, each with its CFL dt, Sec. 2.2)
+ * without an end time and returns without synchronising (device errors are
+ * reported by the next synchronising call). Steps are replayed from
+ * captured CUDA graphs; the host reads nothing back between them (Sec. 2.3:
+ * no transfer during the time loop). */
 swe_status swe_run(swe_state* state, int64_t n_steps);
 
-/* Steps until t == t_end exactly: each step uses min(CFL dt, t_end - t), and
- * the step that reaches t_end sets t = t_end. Synchronises once per chunk of
+/* Steps until t == t_end exactly (the simulated end time T_s of the paper's
+ * runs, Sec. 3): each step uses min(CFL dt, t_end - t), and the step that
+ * reaches t_end sets t = t_end. Synchronises once per chunk of
  * graph-replayed steps. *n_steps (may be NULL) receives the steps taken
  * (scenario 0's). On an ensemble every scenario stops at t_end on its own
  * step count; launches continue until the last one gets there. */
@@ -186,11 +215,20 @@ swe_status swe_advance(swe_state* state, double t_end, int64_t* n_steps);
 /* Waits for queued work and returns the latched device status. */
 swe_status swe_sync(swe_state* state);
 
-/* Copies the state to host arrays in caller order (any pointer may be NULL).
+/* Copies the state to host arrays in caller order (any pointer may be NULL):
+ * the one device-to-host transfer at the end of a run (Sec. 2.3).
  * *t = simulated time (scenario 0's on an ensemble), *mass = sum of area * h
  * in FP64 over every cell. Synchronises. */
 swe_status swe_copy_out(const swe_state* state, double* h, double* hu, double* hv, double* t,
                         double* mass);
+
+/* swe_copy_out into DEVICE arrays (FP64, caller order, any may be NULL; t
+ * and mass are host scalars as in swe_copy_out). The library's stream first
+ * waits for the work queued so far on cuda_stream (the caller's earlier use
+ * of the destinations); the call synchronises before returning, so the
+ * arrays are ready for any stream. Nothing goes through host memory. */
+swe_status swe_copy_out_device(const swe_state* state, double* h, double* hu, double* hv,
+                               double* t, double* mass, void* cuda_stream);
 
 /* info[0] = steps taken (scenario 0's), info[1] = cells whose depth went
  * negative and was clipped to 0 (expected 0 under the CFL step), info[2] =
@@ -256,6 +294,20 @@ swe_status swe_grad_record(swe_state* state, int64_t n_steps, int64_t checkpoint
 swe_status swe_grad(swe_tape* tape, const double* g_h, const double* g_hu, const double* g_hv,
                     const double* g_gauge, double* d_h0, double* d_hu0, double* d_hv0, double* d_z,
                     double* d_n);
+
+/* swe_grad with every seed and output in DEVICE memory (FP64, caller order,
+ * the same shapes; any may be NULL as in swe_grad), ordered after the work
+ * queued on cuda_stream. Nothing goes through host memory. Synchronises. */
+swe_status swe_grad_device(swe_tape* tape, const double* g_h, const double* g_hu,
+                           const double* g_hv, const double* g_gauge, double* d_h0,
+                           double* d_hu0, double* d_hv0, double* d_z, double* d_n,
+                           void* cuda_stream);
+
+/* Copies the gauge depths the tape recorded ([n_steps * n_gauges] FP64,
+ * gauge_h[k * n_gauges + j] after step k, as swe_grad_record gives them) to
+ * the DEVICE array gauge_h, ordered after the work queued on cuda_stream.
+ * Synchronises. */
+swe_status swe_tape_gauges_device(const swe_tape* tape, double* gauge_h, void* cuda_stream);
 
 /* info[0] = steps, info[1] = checkpoint interval, info[2] = device time of
  * the recorded forward steps (ms, CUDA events), info[3] = device time of the

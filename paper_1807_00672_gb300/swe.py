@@ -35,7 +35,8 @@ EXPORTS = (
     "swe_state_set", "swe_step", "swe_run", "swe_advance", "swe_sync", "swe_copy_out",
     "swe_state_info", "swe_next_dt", "swe_scenario_info", "swe_state_destroy", "swe_strerror",
     "swe_last_cuda_error", "swe_step_edges_static", "swe_grad_record", "swe_grad",
-    "swe_tape_info", "swe_tape_destroy", "swe_fp64_fma_rate",
+    "swe_tape_info", "swe_tape_destroy", "swe_fp64_fma_rate", "swe_state_init_device",
+    "swe_state_set_device", "swe_copy_out_device", "swe_grad_device", "swe_tape_gauges_device",
 )
 
 
@@ -106,6 +107,11 @@ def lib():
         "swe_step_edges_static": (st, [i64, i64] + [vp] * 13 + [dbl] * 4 + [vp] * 3
                                   + [vp, vp, vp]),
         "swe_fp64_fma_rate": (st, [vp, vp]),
+        "swe_state_init_device": (st, [vp, vp, vp, vp, vp, vp, dbl, vp, pp]),
+        "swe_state_set_device": (st, [vp, vp, vp, vp, vp]),
+        "swe_copy_out_device": (st, [vp, vp, vp, vp, vp, vp, vp]),
+        "swe_grad_device": (st, [vp] + [vp] * 9 + [vp]),
+        "swe_tape_gauges_device": (st, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -117,6 +123,11 @@ def lib():
 
 def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _vp(addr):
+    """A device address or stream handle (int, or None) as a void pointer."""
+    return None if addr is None else ctypes.c_void_p(int(addr))
 
 
 def _f64(a) -> np.ndarray:
@@ -238,9 +249,38 @@ class State:
         _check(s, "swe_state_init")
         self._h = hdl
 
+    @classmethod
+    def from_device(cls, mesh: Mesh, h, hu, hv, z, n=None, manning_const: float = 0.0,
+                    stream=None):
+        """swe_state_init_device: h, hu, hv, z, n are device addresses (ints)
+        of mesh.T contiguous float64 values each in caller order (n may be
+        None); stream: the CUDA stream handle (int) they were written on."""
+        self = cls.__new__(cls)
+        self.mesh = mesh
+        hdl = ctypes.c_void_p()
+        s = lib().swe_state_init_device(mesh._h, _vp(h), _vp(hu), _vp(hv), _vp(z), _vp(n),
+                                        float(manning_const), _vp(stream), ctypes.byref(hdl))
+        _check(s, "swe_state_init_device")
+        self._h = hdl
+        return self
+
     def set(self, h, hu, hv):
         h, hu, hv = (_f64(a) for a in (h, hu, hv))
         _check(lib().swe_state_set(self._h, _p(h), _p(hu), _p(hv)), "swe_state_set")
+
+    def set_device(self, h, hu, hv, stream=None):
+        """swe_state_set_device: device addresses (ints) of float64 arrays."""
+        _check(lib().swe_state_set_device(self._h, _vp(h), _vp(hu), _vp(hv), _vp(stream)),
+               "swe_state_set_device")
+
+    def copy_out_device(self, h=None, hu=None, hv=None, stream=None):
+        """swe_copy_out_device into device addresses (ints, any may be None);
+        returns (t, mass)."""
+        t = ctypes.c_double()
+        m = ctypes.c_double()
+        _check(lib().swe_copy_out_device(self._h, _vp(h), _vp(hu), _vp(hv), ctypes.byref(t),
+                                         ctypes.byref(m), _vp(stream)), "swe_copy_out_device")
+        return t.value, m.value
 
     def step(self) -> float:
         dt = ctypes.c_double()
@@ -318,16 +358,19 @@ class Tape:
     cell indices) after every step, and checkpoints every
     ``checkpoint_every`` steps. ``gauge_h`` is [n_steps, len(gauges)]."""
 
-    def __init__(self, state: State, n_steps: int, checkpoint_every: int = 50, gauges=None):
+    def __init__(self, state: State, n_steps: int, checkpoint_every: int = 50, gauges=None,
+                 host_gauges: bool = True):
         g = np.ascontiguousarray(gauges if gauges is not None else [], dtype=np.int32).reshape(-1)
         self.gauges = g
         self.n_steps = int(n_steps)
-        self.gauge_h = np.zeros((self.n_steps, g.shape[0]))
+        # host_gauges=False: the gauge depths stay on the device (gauges_device)
+        self.gauge_h = np.zeros((self.n_steps, g.shape[0])) if host_gauges else None
         self.mesh = state.mesh
         h = ctypes.c_void_p()
         s = lib().swe_grad_record(state._h, self.n_steps, int(checkpoint_every),
                                   _p(g) if g.size else None, g.shape[0],
-                                  _p(self.gauge_h) if g.size else None, ctypes.byref(h))
+                                  _p(self.gauge_h) if (g.size and host_gauges) else None,
+                                  ctypes.byref(h))
         _check(s, "swe_grad_record")
         self._h = h
 
@@ -345,6 +388,19 @@ class Tape:
                            *[_p(out[k]) for k in ("h", "hu", "hv", "z", "n")])
         _check(s, "swe_grad")
         return out
+
+    def grad_device(self, seeds, outs, stream=None):
+        """swe_grad_device: seeds = (g_h, g_hu, g_hv, g_gauge), outs = (h, hu,
+        hv, z, n), device addresses (ints) or None each."""
+        s = lib().swe_grad_device(self._h, *[_vp(a) for a in seeds], *[_vp(a) for a in outs],
+                                  _vp(stream))
+        _check(s, "swe_grad_device")
+
+    def gauges_device(self, dst, stream=None):
+        """swe_tape_gauges_device: the recorded gauge depths into a device
+        address (int) of n_steps * len(gauges) float64 values."""
+        _check(lib().swe_tape_gauges_device(self._h, _vp(dst), _vp(stream)),
+               "swe_tape_gauges_device")
 
     def info(self):
         a = np.zeros(5)
