@@ -201,7 +201,9 @@ swe_status swe_step(swe_state* state, double* dt_used);
  * without an end time and returns without synchronising (device errors are
  * reported by the next synchronising call). Steps are replayed from
  * captured CUDA graphs; the host reads nothing back between them (Sec. 2.3:
- * no transfer during the time loop). */
+ * no transfer during the time loop). n_steps = 0 takes no step and only
+ * captures (and uploads) the step graph if the state has none yet, so that
+ * the steps of a later call are replayed from its first one. */
 swe_status swe_run(swe_state* state, int64_t n_steps);
 
 /* Steps until t == t_end exactly (the simulated end time T_s of the paper's

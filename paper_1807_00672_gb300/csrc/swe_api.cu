@@ -287,6 +287,8 @@ swe_status ensure_graph(swe_state* s) {
   e = cudaGraphInstantiate(&s->graph, g, 0);
   cudaGraphDestroy(g);
   if (cuda_failed(e)) { s->graph = nullptr; return SWE_ECUDA; }
+  // upload now, so that the first replay costs what every later one does
+  CK(cudaGraphUpload(s->graph, s->mesh->stream));
   return SWE_OK;
 }
 
@@ -777,6 +779,12 @@ void scatter_any(const swe_mesh* m, const void* src, double* dst, int stride) {
   else launch_scatter<float>(m, src, dst, stride);
 }
 
+swe_status make_open_ended(swe_state* s) {
+  open_end(s);
+  CK(cudaGetLastError());
+  return SWE_OK;
+}
+
 }  // namespace swe_host
 
 extern "C" {
@@ -1022,6 +1030,7 @@ swe_status swe_step(swe_state* s, double* dt_used) {
 swe_status swe_run(swe_state* s, int64_t n_steps) {
   if (!s || n_steps < 0) return SWE_EINVAL;
   open_end(s);
+  if (n_steps == 0) return ensure_graph(s);  // prepare the graph, take no step
   return queue_steps(s, n_steps);
 }
 

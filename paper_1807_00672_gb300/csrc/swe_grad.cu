@@ -476,7 +476,7 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
       return fail(SWE_ECUDA);
   }
   const int64_t steps0 = s->host_ctl[0].steps;
-  st = swe_run(s, 0);  // end time +inf: every step takes its CFL dt
+  st = make_open_ended(s);  // end time +inf: every step takes its CFL dt
   if (st != SWE_OK) return fail(st);
   st = m->prm.precision == SWE_F64 ? record_t<double>(s, t) : record_t<float>(s, t);
   if (st != SWE_OK) return fail(st);

@@ -165,6 +165,8 @@ void launch_forward(const swe_mesh* m, const swe::DevState<double>& ds, cudaStre
 // stride 4 for interleaved cells.
 void gather_any(const swe_mesh* m, const double* src, void* dst, int stride);
 void scatter_any(const swe_mesh* m, const void* src, double* dst, int stride);
+// Makes every scenario's device end time +inf (steps take their CFL dt).
+swe_status make_open_ended(swe_state* s);
 // Copies every scenario's control word to the state's pinned mirror.
 swe_status read_ctl(const swe_state* s);
 // Other handles that use a mesh hold it: it is freed when the last goes.

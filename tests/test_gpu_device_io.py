@@ -126,7 +126,7 @@ def test_gradient_with_device_seeds_and_outputs_equals_the_host_call():
     tape.gauges_device(gh.data_ptr())
     assert np.array_equal(gh.cpu().numpy(), tape.gauge_h)
     # seeds may be left out, as in the host call
-    tape.grad_device([None, None, None, seeds[3]], ptrs(*outs))
+    tape.grad_device([None, None, None, seeds[3].data_ptr()], ptrs(*outs))
     want2 = tape.grad(g_gauge=g[3])
     assert np.array_equal(outs[4].cpu().numpy(), want2["n"])
 

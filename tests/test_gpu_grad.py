@@ -269,6 +269,13 @@ def test_adjoint_matches_dual_number_oracle_on_many_tiles(name):
 
 
 def test_adjoint_matches_central_differences_on_many_tiles():
+    """Central differences of the plain FP64 oracle steps at 307,200 cells
+    along a smooth direction, against the GPU gradient: 1e-5 relative. The
+    direction is smooth in space: a per-cell random one makes the perturbed
+    runs cross kinks of the flux (the min/max of the wave-speed estimates,
+    the upwind side of the transverse momentum) at a few of the 9 million
+    face evaluations, where a difference quotient differs from the
+    piecewise derivative by about 1e-5 whatever the step size."""
     c = large_cases()["wet"]
     N, K = 20, 7
     gauges = [1_000, 150_000, 300_000]
@@ -276,7 +283,11 @@ def test_adjoint_matches_central_differences_on_many_tiles():
     g = seeds(c, N, len(gauges), 29)
     grads = tape.grad(**g)
     dts = oracle.state_from_case(c).run(N)
-    v = directions(c, 31)
+    cen = inputs.centroids(c.mesh)
+    x, y = cen[:, 0] / c.mesh.lx, cen[:, 1] / c.mesh.ly
+    v = dict(h=0.1 * np.sin(5 * x + 1) * np.cos(3 * y), hu=0.2 * np.cos(4 * x) * np.sin(2 * y + 0.5),
+             hv=0.2 * np.sin(3 * x + 2 * y), z=0.05 * np.cos(6 * x - y),
+             n=0.005 * np.sin(2 * x + 3 * y))
 
     def loss(sign, eps):
         s = oracle.State(oracle.Mesh(c.mesh.xy, c.mesh.tri), c.h + sign * eps * v["h"],
