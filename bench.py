@@ -229,6 +229,11 @@ def main():
                     help="only record 4 steps of the workload and run one gradient (a short "
                          "command to profile the adjoint kernel under ncu); prints the tape info")
     ap.add_argument("--water-drop-test", type=int, default=4, help="Table 2 grid size (1-5)")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the FP32-vs-oracle error legs at full size")
+    ap.add_argument("--error-steps", type=int, default=1000,
+                    help="steps of the 10M workload's FP32-vs-oracle error leg")
+    ap.add_argument("--humps-steps", type=int, default=500)
     ap.add_argument("--ref-cells", type=int, default=25_000)
     ap.add_argument("--cpu-cells", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=150)
@@ -272,9 +277,10 @@ def main():
     T = mesh.T
     kernels_per_step = 2 if args.kernel == "edge" else 1
 
-    # warm-up: at least one full graph of steps, so the timed region replays
-    # an already captured graph
-    warm = max(args.warmup, 16)
+    # warm-up: the step graph is captured and uploaded first (swe_run with 0
+    # steps takes none), then exactly --warmup steps run
+    warm = args.warmup
+    st.run(0)
     st.run(warm)
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -370,15 +376,22 @@ def main():
     # The adjoint leg runs first among the extras: its backward/forward
     # ratio compares two timings of the same run, taken before the long
     # FP64 and ensemble legs.
+    errors = {}
     if rank == 0 and not args.no_extras and not args.no_adjoint:
-        out["adjoint"] = adjoint_leg(args, stream)
+        out["adjoint"] = adjoint_leg(args, stream, errors)
     if rank == 0 and not args.no_extras:
         out["fp64"] = fp64_leg(case, args, stream, ws)
-        out["error"] = error_leg(args)
+        out["humps_1m"] = humps_leg(args, stream, errors)
     if rank == 0 and not args.no_extras and not args.no_ensemble:
-        out["ensemble"] = ensemble_leg(args, stream)
+        out["ensemble"] = ensemble_leg(args, stream, errors)
     if rank == 0 and not args.no_extras and not args.no_water_drop:
         out["water_drop"] = water_drop_leg(args, stream)
+    if rank == 0 and not args.no_extras and not args.no_error:
+        errors["stoker_2500"] = stoker_error(args)
+        if args.workload == "sinusoid_10m":
+            errors["sinusoid_10m"] = fp32_error(case, mesh, steps=args.error_steps)
+    if errors:
+        out["error"] = errors
     st.close()
     mesh.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -396,6 +409,7 @@ def main():
                       f"the same recipe at {small.mesh.n_tris} triangles ({secs:.1f} s)",
             "single_thread": {"value": rate1, "cores": 1, "seconds": secs1}}
     if rank == 0:
+        out["summary"] = summary(out)
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()
@@ -428,6 +442,7 @@ def fp64_leg(case, args, stream, ws):
     mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f64", kernel=args.kernel,
                     tile=args.tile, stream=ctypes_stream(stream))
     st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+    st.run(0)
     st.run(3)
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
@@ -460,7 +475,7 @@ def fp64_leg(case, args, stream, ws):
     return out
 
 
-def ensemble_leg(args, stream):
+def ensemble_leg(args, stream, errors):
     """256 independent dam-break scenarios of log-uniform size (5k-500k
     triangles, 26.6M in all) in one mesh, FP32: the kernel shape comes from
     the autotuner (measured on every 8th scenario), then the whole ensemble
@@ -502,11 +517,41 @@ def ensemble_leg(args, stream):
            "shape": {"tile": tuned["tile"], "cells_per_thread": tuned["cells_per_thread"],
                      "stages": tuned["stages"], "halo_schedule": tuned["halo_schedule"],
                      "autotuned_on": f"{len(cases[::8])} scenarios"},
-           "autotune_trials": [(t["shape"], round(t["sec_per_step"] * 1e6, 1))
-                               for t in tuned["trials"] if "sec_per_step" in t],
+           "autotune_trials": sum(1 for t in tuned["trials"] if "sec_per_step" in t),
            "setup_s": setup_s, "scenario_steps": sorted(steps)}
+    errors["ensemble_256"] = ensemble_error(cases, mesh, st, args.ensemble_steps)
     st.close()
     mesh.close()
+    return res
+
+
+def ensemble_error(cases, mesh, st, steps, every=16):
+    """FP32 error of the ensemble against the FP64 oracle on every 16th
+    scenario, at one simulated time for all: the smallest time the sampled
+    scenarios reach in `steps` oracle steps. The ensemble restarts from its
+    initial state and advances every scenario to that time (each on its own
+    CFL steps); each sampled scenario's oracle advances to it as well."""
+    sample = list(range(0, len(cases), every))
+    t_end = min(_oracle_to(cases[i], steps=steps)[2] for i in sample)
+    cat = lambda name: np.concatenate([getattr(c, name) for c in cases])
+    st.set(cat("h"), cat("hu"), cat("hv"))
+    m0 = {i: st.scenario(i)["mass"] for i in sample}
+    st.advance(t_end)
+    got = st.fields()
+    per = []
+    for i in sample:
+        o, k, _, _ = _oracle_to(cases[i], t_end=t_end)
+        a, n = mesh.scenario_offsets[i], mesh.scenario_cells[i]
+        e = _rel_errors([f[a:a + n] for f in got], (o.h, o.hu, o.hv), o.mesh.cells()["area"])
+        info = st.scenario(i)
+        e["mass_rel_drift_fp32"] = abs(info["mass"] - m0[i]) / m0[i]
+        e["steps_oracle"], e["steps_fp32"] = int(k), int(info["steps"])
+        per.append(e)
+    res = {"scenarios_sampled": len(sample), "t": t_end, "vs": "FP64 oracle at the same simulated time"}
+    for key in per[0]:
+        if key.startswith(("l1_", "linf_", "mass_")):
+            res[key] = max(p[key] for p in per)  # worst sampled scenario
+    res["steps_oracle_min_max"] = [min(p["steps_oracle"] for p in per), max(p["steps_oracle"] for p in per)]
     return res
 
 
@@ -518,7 +563,7 @@ def adjoint_bytes_per_cell(word: int) -> float:
     return 23.5 * word + 12.0
 
 
-def adjoint_leg(args, stream):
+def adjoint_leg(args, stream, errors):
     """Gradient of the calibration loss (1,000,000 triangles fully wet, 64
     gauges, L = sum over steps and gauges of (h - h_obs)^2, observations from
     the same run with a perturbed Manning n) with respect to n, z and the
@@ -582,6 +627,8 @@ def adjoint_leg(args, stream):
             "finite": bool(all(np.isfinite(v).all() for v in r.values()))}
         tape.close()
         st.close()
+        if prec == "f32":
+            errors["calibration_1m"] = fp32_error(case, mesh, steps=N)
         mesh.close()
     for k in ("n", "z", "h"):
         ref = grads["f64"][k]
@@ -628,27 +675,148 @@ def water_drop_leg(args, stream):
     return res
 
 
-def error_leg(args, cells=50_000, steps=100):
-    """FP32 vs FP64-oracle error on the workload recipe at a reduced size."""
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    import oracle
-    from paper_1807_00672_gb300 import swe
-    case = small_case(args.workload, cells)
-    o = oracle.state_from_case(case)
-    o.run(steps)
-    area = o.mesh.cells()["area"]
-    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f32", kernel=args.kernel, tile=args.tile)
-    st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
-    st.run(steps)
-    got = st.fields()
-    res = {"triangles": mesh.T, "steps": steps, "vs": "FP64 oracle"}
-    for name, g, r in zip(("h", "hu", "hv"), got, (o.h, o.hu, o.hv)):
+def _rel_errors(got, ref, area):
+    """Per field (h, hu, hv): L1 = sum area |d| / sum area |ref| and
+    Linf = max |d| / max |ref|."""
+    res = {}
+    for name, g, r in zip(("h", "hu", "hv"), got, ref):
+        d = np.abs(np.asarray(g) - r)
         den = float((area * np.abs(r)).sum())
-        res[f"l1_{name}"] = float((area * np.abs(g - r)).sum()) / den
-        res[f"linf_{name}"] = float(np.abs(g - r).max()) / float(np.abs(r).max())
+        res[f"l1_{name}"] = float((area * d).sum()) / den if den > 0 else float(d.max())
+        mx = float(np.abs(r).max())
+        res[f"linf_{name}"] = float(d.max()) / mx if mx > 0 else float(d.max())
+    return res
+
+
+def _oracle_to(case, steps=None, t_end=None):
+    """The FP64 oracle on every host core: `steps` CFL steps, or steps to
+    t_end. Returns (state, steps taken, end time, seconds)."""
+    import oracle
+    oracle.set_threads(host_cores())
+    try:
+        t0 = time.perf_counter()
+        o = oracle.state_from_case(case)
+        if t_end is None:
+            o.run(steps)
+            k = steps
+        else:
+            k = o.advance(t_end)
+        return o, k, o.t, time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+
+
+def fp32_error(case, mesh=None, steps=None, t_end=None, stream=None):
+    """The FP32 path against the FP64 oracle at one simulated time: the
+    oracle runs `steps` CFL steps (or to t_end) from the initial state, and
+    the FP32 state advances to the time the oracle reached (swe_advance: the
+    last step is clamped to it), each with its own CFL time steps. Returns
+    L1 / Linf of h, hu, hv, the FP64-integrated mass drift of the FP32 state
+    and both step counts. `mesh`: an FP32 mesh of the case to reuse."""
+    from paper_1807_00672_gb300 import swe
+    o, k_ref, t_end, secs = _oracle_to(case, steps, t_end)
+    own = mesh is None
+    if own:
+        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f32",
+                        stream=None if stream is None else ctypes_stream(stream))
+    st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+    m0 = st.mass
+    k = st.advance(t_end)
+    got = st.fields()
+    m1 = st.mass
+    res = {"triangles": int(case.mesh.n_tris), "t": t_end, "steps_oracle": int(k_ref),
+           "steps_fp32": int(k), "vs": "FP64 oracle at the same simulated time"}
+    res.update(_rel_errors(got, (o.h, o.hu, o.hv), o.mesh.cells()["area"]))
+    res["mass_rel_drift_fp32"] = abs(m1 - m0) / m0
+    res["oracle_s"] = round(secs, 2)
+    st.close()
+    if own:
+        mesh.close()
+    return res
+
+
+def stoker_error(args):
+    """The 2,500-triangle dam break to T_s = 2 s (FP64 workload): the FP64
+    path's largest per-field error against the oracle (max |d| / max |ref|)
+    and the FP32 path's L1 / Linf."""
+    from paper_1807_00672_gb300 import inputs, swe
+    case = inputs.stoker_case()
+    o, k_ref, t, _ = _oracle_to(case, t_end=2.0)
+    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f64")
+    st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+    k = st.advance(2.0)
+    got = st.fields()
+    res = {"triangles": mesh.T, "t": 2.0, "steps_oracle": int(k_ref), "steps_fp64": int(k)}
+    res["fp64_max_rel"] = {n: float(np.abs(g - r).max() / np.abs(r).max())
+                           for n, g, r in zip(("h", "hu", "hv"), got, (o.h, o.hu, o.hv))}
     st.close()
     mesh.close()
+    res["fp32"] = fp32_error(case, t_end=2.0)
     return res
+
+
+def humps_leg(args, stream, errors):
+    """The 1,000,000-triangle workload (three Gaussian humps, n = 0.03,
+    wet/dry fronts): FP32 and FP64 cell-updates/s over graph-replayed steps
+    timed with CUDA events, with the HBM fraction at 62 and 112 algorithmic
+    bytes per cell (scalar n); and the FP32 error against the oracle after
+    --humps-steps steps (into `errors`)."""
+    import torch
+    from paper_1807_00672_gb300 import swe
+    case = make_case("humps_1m")
+    peak, kind = measured_peaks()
+    res = {"triangles": case.mesh.n_tris}
+    for prec, k in (("f32", args.humps_steps), ("f64", 100)):
+        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=prec, stream=ctypes_stream(stream))
+        st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+        st.run(0)
+        st.run(3)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.run(k, sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        st.sync()
+        ms = a.elapsed_time(b) / k
+        balg = alg_bytes_per_cell(4 if prec == "f32" else 8, False)
+        achieved = balg * mesh.T / (ms * 1e-3) / 1e9
+        res[prec] = {"value": mesh.T / (ms * 1e-3), "ms_per_step": ms, "steps": k,
+                     "hbm_frac": achieved / peak, "alg_bytes_per_cell": balg}
+        st.close()
+        if prec == "f32":
+            errors["humps_1m"] = fp32_error(case, mesh, steps=args.humps_steps)
+        mesh.close()
+    res["peak_source"] = f"{kind} HBM copy bandwidth"
+    return res
+
+
+def summary(out):
+    """The headline figures again, compact, at the end of the line."""
+    r = lambda x: None if x is None else float(f"{x:.4g}")
+    s = {"fp32_10m": {"value": r(out["value"]), "hbm_frac": r(out["roofline"]["frac"])},
+         "e2e": r(out["e2e"]["value"])}
+    if "fp64" in out:
+        s["fp64_10m"] = {"value": r(out["fp64"]["value"]), "hbm_frac": r(out["fp64"]["hbm_frac"]),
+                         "alu_frac": r(out["fp64"]["alu"].get("frac"))}
+    if "humps_1m" in out:
+        s["humps_1m"] = {p: {"value": r(out["humps_1m"][p]["value"]),
+                             "hbm_frac": r(out["humps_1m"][p]["hbm_frac"])} for p in ("f32", "f64")}
+    if "ensemble" in out:
+        s["ensemble"] = {"value": r(out["ensemble"]["value"]), "hbm_frac": r(out["ensemble"]["hbm_frac"])}
+    if "adjoint" in out:
+        a = out["adjoint"]
+        s["adjoint_backward_over_forward"] = {p: r(a[p]["backward_over_forward"])
+                                              for p in ("f32", "f64") if p in a}
+    if "error" in out:
+        e = {}
+        for cfg, v in out["error"].items():
+            v = v.get("fp32", v)
+            e[cfg] = {"l1_h": r(v.get("l1_h")), "linf_h": r(v.get("linf_h")),
+                      "l1_hu": r(v.get("l1_hu")), "mass": r(v.get("mass_rel_drift_fp32"))}
+        s["fp32_error_vs_oracle"] = e
+    return s
 
 
 def kernel_source_digest():
