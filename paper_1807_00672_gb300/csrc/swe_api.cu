@@ -60,6 +60,16 @@ namespace swe_host {
 
 thread_local std::string g_cuda_msg;
 
+int smem_optin_bytes() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return v;
+}
+
 bool cuda_failed_at(cudaError_t e, const char* what, const char* file, int line) {
   if (e == cudaSuccess) return false;
   const char* base = file;
@@ -109,7 +119,18 @@ template <typename Real, int NT, int NS, int TC, bool Early = false>
 int prepare_tiled(const swe::TileLayout& L) {
   constexpr bool comp = sizeof(Real) == 4;
   auto k = swe::k_tiled_step<Real, comp, NT, NS, TC, Early>;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess) {
+  // The limit is a property of the kernel, shared by every mesh that
+  // launches it: set it to the device's largest opt-in size (not this
+  // layout's), so that a later mesh with a smaller layout cannot lower it
+  // below what an earlier one needs.
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int cap = swe_host::smem_optin_bytes() - (int)fa.sharedSizeBytes;  // less its static part
+  if (cap <= 0 || (int)L.total > cap ||
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

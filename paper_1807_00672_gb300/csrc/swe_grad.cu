@@ -130,7 +130,18 @@ void launch_adjoint(const swe_mesh* m, const swe::Chunk* chunks, int grid,
 template <typename Real, int NT, int CPT>
 int prepare_adjoint_nt(const swe::AdjLayout& L) {
   auto k = swe::k_tiled_adjoint<Real, NT, 2, CPT>;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess) {
+  // The limit is a property of the kernel, shared by every mesh that
+  // launches it: set it to the device's largest opt-in size (not this
+  // layout's), so that a later mesh with a smaller layout cannot lower it
+  // below what an earlier one needs.
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int cap = swe_host::smem_optin_bytes() - (int)fa.sharedSizeBytes;  // less its static part
+  if (cap <= 0 || (int)L.total > cap ||
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

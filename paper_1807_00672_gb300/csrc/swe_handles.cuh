@@ -158,6 +158,10 @@ swe::DevState<Real> dev_state(const swe_state* s) {
   return d;
 }
 
+// Largest dynamic shared memory a block may opt into on the current device
+// (0 if the query fails).
+int smem_optin_bytes();
+
 // One forward step of the mesh's kernel on explicitly given state buffers.
 void launch_forward(const swe_mesh* m, const swe::DevState<float>& ds, cudaStream_t st);
 void launch_forward(const swe_mesh* m, const swe::DevState<double>& ds, cudaStream_t st);

@@ -1024,6 +1024,43 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     for (int q = q_h; q < nh; q += NT) copy_cell(q, hl[q]);
   };
 
+  // FP64: the staged cells (h, hu, hv, z) become (h, u, v, z) in place once
+  // they have landed, u = hu / h on a wet cell (one reciprocal for both
+  // components) and 0 on a dry one, so that the face loop divides nothing
+  // (the same values the faces would form, once per cell instead of once
+  // per face side). Each thread converts its own cells of the tile, keeping
+  // their (hu, hv) in registers for the update, and the halo cells it
+  // gathered itself.
+  constexpr bool kVel = sizeof(Real) == 8;
+  Real own_q[CPT][2], next_q[CPT][2];
+  auto to_velocity = [&](Real* c, Real& hu, Real& hv) {
+    const V4<Real> x = ld4(c);
+    Real u, v;
+    velocity(x.x, x.y, x.z, num, u, v);
+    hu = x.y;
+    hv = x.z;
+    st4(c, x.x, u, v, x.w);
+  };
+  auto own_velocities = [&](int st, Real (&q)[CPT][2]) {
+    Real* xc = reinterpret_cast<Real*>(smem + st * L.stage + L.off_cells);
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      const int j = tid + cc * NT;
+      if (TC % NT != 0 && j >= TC) break;
+      to_velocity(xc + 4 * j, q[cc][0], q[cc][1]);
+    }
+  };
+  auto halo_velocities = [&](int st) {
+    Real* xc = reinterpret_cast<Real*>(smem + st * L.stage + L.off_cells) + 4 * TC;
+    Real a, b;
+    if (hreg) {
+      if (q_h < (int)L.halo_cap) to_velocity(xc + 4 * q_h, a, b);
+      return;
+    }
+    const int nh = s_nh[st];
+    for (int q = q_h; q < nh; q += NT) to_velocity(xc + 4 * q, a, b);
+  };
+
   NoMass<Real> mass;  // integrated on demand (k_cfl_tiled), not every step
   Real rate = Real(0);
   Real chk = Real(0);  // non-zero once a new value is NaN or infinite
@@ -1077,6 +1114,10 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     } else {
       if (!early) gather_halo(0);
       cp_async_wait_all();
+      if constexpr (kVel) {
+        own_velocities(0, own_q);
+        halo_velocities(0);
+      }
       __syncthreads();
     }
   }
@@ -1159,23 +1200,18 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
           // Wall (side A is the tile cell owning the edge) or padding record;
           // these are the last records of a tile.
           if (a == kSideWall) continue;
-          const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));
-          Real uA, vA;
-          velocity(A.x, A.y, A.z, num, uA, vA);
-          face_flux<Real>(A.x, uA, vA, A.w, A.x, uA, vA, A.w, true, nx, ny, len, num, c0, cA1, cA2,
-                          cB1, cB2);
+          const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));  // (h, u, v, z)
+          face_flux<Real>(A.x, A.y, A.z, A.w, A.x, A.y, A.z, A.w, true, nx, ny, len, num, c0, cA1,
+                          cA2, cB1, cB2);
           st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
           continue;
         }
         const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : a;
         const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : b;
-        const V4<Real> A = ld4(xc + 4 * ia);
+        const V4<Real> A = ld4(xc + 4 * ia);  // (h, u, v, z)
         const V4<Real> B = ld4(xc + 4 * ib);
-        Real uA, vA, uB, vB;
-        velocity(A.x, A.y, A.z, num, uA, vA);
-        velocity(B.x, B.y, B.z, num, uB, vB);
-        face_flux<Real>(A.x, uA, vA, A.w, B.x, uB, vB, B.w, false, nx, ny, len, num, c0, cA1, cA2, cB1,
-                        cB2);
+        face_flux<Real>(A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, false, nx, ny, len, num, c0, cA1, cA2,
+                        cB1, cB2);
         if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
         if (b < 0) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, Real(0));
       }
@@ -1188,6 +1224,9 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       break;
     }
     if (!early && has_next) gather_halo((k + 1) % NS);
+    if constexpr (kVel) {
+      if (has_next) own_velocities((k + 1) % NS, next_q);
+    }
 
     // cell updates of tile k
 #pragma unroll
@@ -1230,10 +1269,19 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
         }
       }
       const V4<Real> c = ld4(xc + 4 * j);
+      // FP64: the staged cell holds (h, u, v, z); its (hu, hv) are in registers
+      const Real qx = kVel ? own_q[cc][0] : c.y, qy = kVel ? own_q[cc][1] : c.z;
       Real a1, b1, c1;
-      cell_finish<Real, Comp>(c.x, c.y, c.z, c_area[cc], c_irP[cc], c_gn2[cc], dt, R, num, a1, b1,
-                              c1, mass, rate, chk, neg);
+      cell_finish<Real, Comp>(c.x, qx, qy, c_area[cc], c_irP[cc], c_gn2[cc], dt, R, num, a1, b1, c1,
+                              mass, rate, chk, neg);
       st4(U1 + 4 * (int64_t)(base + j), a1, b1, c1, c.w);
+    }
+    if constexpr (kVel) {
+#pragma unroll
+      for (int cc = 0; cc < CPT; ++cc) {
+        own_q[cc][0] = next_q[cc][0];
+        own_q[cc][1] = next_q[cc][1];
+      }
     }
     if (early) {
       const bool ok_end = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
@@ -1244,6 +1292,9 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       }
     } else {
       cp_async_wait_all();
+      if constexpr (kVel) {
+        if (has_next) halo_velocities((k + 1) % NS);
+      }
       __syncthreads();
     }
   }

@@ -306,3 +306,27 @@ def test_fp32_10m_sinusoid_sampled_cells():
         assert np.abs(got[cells] - w).max() <= 2e-6 * scale
     assert np.all(h1 >= 0) and np.all(np.isfinite(h1))
     assert abs(st.mass - m0) <= 1e-6 * m0
+
+
+def test_meshes_of_different_layouts_in_any_order():
+    """A tiled kernel's shared-memory limit is shared by every mesh that
+    launches it: a mesh created after another one, with a smaller layout,
+    must not stop the first one's steps (nor graph captures of new states
+    on it)."""
+    big = inputs.humps_case(nx=120, ny=60, lx=4_000.0, ly=2_000.0, seed=19)
+    small = inputs.random_flow_case(nx=6, ny=4, seed=3)
+    for prec in ("f64", "f32"):
+        ensure_built()
+        mb = swe.Mesh(big.mesh.xy, big.mesh.tri, precision=prec)
+        a = swe.State(mb, big.h, big.hu, big.hv, big.z, big.n)
+        a.run(20)
+        ms = swe.Mesh(small.mesh.xy, small.mesh.tri, precision=prec)
+        b = swe.State(ms, small.h, small.hu, small.hv, small.z, small.n)
+        b.run(20)
+        c = swe.State(mb, big.h, big.hu, big.hv, big.z, big.n)  # new graph on the big mesh
+        c.run(20)
+        a.set(big.h, big.hu, big.hv)
+        a.run(20)
+        for x, y in zip(a.fields(), c.fields()):
+            assert np.array_equal(x, y)
+        assert a.info()["err"] == 0 and c.info()["err"] == 0
