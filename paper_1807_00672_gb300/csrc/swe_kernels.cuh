@@ -200,14 +200,54 @@ __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& 
 template <typename Real>
 struct Ops;
 
+// FP64 reciprocal and inverse cube root by Newton-Raphson iteration (the
+// textbook method: each step about squares the relative error), written
+// with fused multiply-adds:
+//   1/b:       y <- y + y (1 - b y), from the hardware approximation of the
+//              leading bits (rcp.approx.ftz.f64, relative error about 2^-20);
+//              two steps reach the last bit;
+//   x^{-1/3}:  y <- y + (y / 3) (1 - x y^3), from an FP32 seed
+//              2^{-log2(x) / 3} (ex2/lg2 approximations, about 2^-21); two
+//              steps reach within a few ulps.
+// Both are checked against IEEE division and cbrt by a GPU test. Square
+// roots stay IEEE sqrt (cheaper on this hardware than any refinement tried).
+__device__ __forceinline__ double rcp_approx64(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double rcp_nr(double b) {
+  double y = rcp_approx64(b);
+  double e = fma(-b, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-b, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ float ex2_approx(float x);
+__device__ __forceinline__ float lg2_approx(float x);
+__device__ __forceinline__ double icbrt_nr(double x) {
+  double y = (double)ex2_approx(-lg2_approx((float)x) * (1.0f / 3.0f));
+  const double third = 1.0 / 3.0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double y3 = y * y * y;
+    y = fma(y * third, fma(-x, y3, 1.0), y);
+  }
+  return y;
+}
+
 template <>
 struct Ops<double> {
-  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double div(double a, double b) { return a * rcp_nr(b); }
+  static __device__ __forceinline__ double rcp(double b) { return rcp_nr(b); }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ bool wet(double h, const Num& n) { return h > n.h_eps; }
-  // dt g n^2 |q| / h^{7/3}
+  // dt g n^2 |q| / h^{7/3}, h^{-7/3} = y^7 with y = h^{-1/3}
   static __device__ __forceinline__ double friction(double dt, double gn2, double q, double h) {
-    return dt * gn2 * q / (h * h * cbrt(h));
+    const double y = icbrt_nr(h);
+    const double y2 = y * y;
+    const double y7 = (y2 * y2) * (y2 * y);
+    return dt * gn2 * q * y7;
   }
 };
 
@@ -247,6 +287,7 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 template <>
 struct Ops<float> {
   static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
+  static __device__ __forceinline__ float rcp(float b) { return rcp_approx(b); }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrt_approx(x); }
   static __device__ __forceinline__ bool wet(float h, const Num& n) { return h > n.h_eps_f32; }
   static __device__ __forceinline__ float friction(float dt, float gn2, float q, float h) {
@@ -391,7 +432,7 @@ template <typename Real>
 __device__ __forceinline__ void velocity(Real h, Real hu, Real hv, const Num& num, Real& u, Real& v) {
   const bool w = Ops<Real>::wet(h, num);
   if constexpr (sizeof(Real) == 8) {
-    const double r = w ? 1.0 / h : 0.0;  // one division for both components
+    const double r = w ? rcp_nr(h) : 0.0;  // one reciprocal for both components
     u = hu * r;
     v = hv * r;
   } else {
@@ -522,6 +563,70 @@ __device__ __forceinline__ void face_flux_f32(const V4<float>& A, const V4<float
   } else {
     cB1 = 0.0f;
     cB2 = 0.0f;
+  }
+}
+
+// FP64 face of the tiled kernel: the straight-line form of face_flux_f32
+// (clamped-speed HLL, dry-bed speeds by substitution, transverse momentum
+// upwinded by the sign of F0, contributions from (gx, gy) = l n; the same
+// flux as face_flux up to rounding) on cells whose velocities were formed
+// once per cell: A, B are (h, u, v, z), u = v = 0 on a dry cell. Wall: B is
+// ignored (mirror of A).
+template <bool Wall>
+__device__ __forceinline__ void face_flux_f64(const V4<double>& A, const V4<double>& B, double nx,
+                                              double ny, double len, const Num& num, double& c0,
+                                              double& cA1, double& cA2, double& cB1, double& cB2) {
+  const double g = num.g, eps = num.h_eps;
+  const double gx = len * nx, gy = len * ny;
+  const double unA = A.y * nx + A.z * ny;
+  const double utA = A.z * nx - A.y * ny;
+  double hB, zB, unB, utB;
+  if (Wall) {
+    hB = A.x; zB = A.w; unB = -unA; utB = utA;
+  } else {
+    hB = B.x; zB = B.w;
+    unB = B.y * nx + B.z * ny;
+    utB = B.z * nx - B.y * ny;
+  }
+  // hydrostatic reconstruction
+  const double zs = fmax(A.w, zB);
+  const double xA = A.x + A.w - zs, xB = hB + zB - zs;
+  const double hAs = xA > eps ? xA : 0.0;
+  const double hBs = xB > eps ? xB : 0.0;
+  // HLLC wave speeds, a dry side entering with un_B - 2 c_B (A dry) or
+  // un_A + 2 c_A (B dry)
+  const double hg = 0.5 * g;
+  const double cA = sqrt(g * hAs), cB = sqrt(g * hBs);
+  const double vnA = hAs > 0.0 ? unA : unB - 2.0 * cB;
+  const double vnB = hBs > 0.0 ? unB : unA + 2.0 * cA;
+  const double us = (vnA + vnB) * 0.5 + cA - cB;
+  const double cs = (cA + cB) * 0.5 + (vnA - vnB) * 0.25;
+  const double Sm = fmin(fmin(vnA - cA, us - cs), 0.0);
+  const double Sp = fmax(fmax(vnB + cB, us + cs), 0.0);
+  // HLL fluxes with the clamped speeds; e = g/2 h*^2 serves the flux and
+  // the bed pressure g/2 (h^2 - h*^2)
+  const double qA = hAs * unA, qB = hBs * unB;
+  const double eA = hg * hAs * hAs, eB = hg * hBs * hBs;
+  const double FA1 = qA * unA + eA;
+  const double FB1 = qB * unB + eB;
+  const double inv = rcp_nr(fmax(Sp - Sm, 1e-300));
+  const double SS = Sm * Sp;
+  double F0 = (Sp * qA - Sm * qB + SS * (hBs - hAs)) * inv;
+  const double F1 = (Sp * FA1 - Sm * FB1 + SS * (qB - qA)) * inv;
+  double F2 = F0 * (F0 >= 0.0 ? utA : utB);
+  if (Wall) { F0 = 0.0; F2 = 0.0; }
+  const double t1 = F2 * gy, t2 = F2 * gx;
+  c0 = len * F0;
+  const double FA = F1 + (hg * A.x * A.x - eA);
+  cA1 = FA * gx - t1;
+  cA2 = FA * gy + t2;
+  if (!Wall) {
+    const double FB = F1 + (hg * hB * hB - eB);
+    cB1 = FB * gx - t1;
+    cB2 = FB * gy + t2;
+  } else {
+    cB1 = 0.0;
+    cB2 = 0.0;
   }
 }
 
@@ -1201,8 +1306,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
           // these are the last records of a tile.
           if (a == kSideWall) continue;
           const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));  // (h, u, v, z)
-          face_flux<Real>(A.x, A.y, A.z, A.w, A.x, A.y, A.z, A.w, true, nx, ny, len, num, c0, cA1,
-                          cA2, cB1, cB2);
+          face_flux_f64<true>(A, A, nx, ny, len, num, c0, cA1, cA2, cB1, cB2);
           st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
           continue;
         }
@@ -1210,8 +1314,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
         const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : b;
         const V4<Real> A = ld4(xc + 4 * ia);  // (h, u, v, z)
         const V4<Real> B = ld4(xc + 4 * ib);
-        face_flux<Real>(A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w, false, nx, ny, len, num, c0, cA1, cA2,
-                        cB1, cB2);
+        face_flux_f64<false>(A, B, nx, ny, len, num, c0, cA1, cA2, cB1, cB2);
         if (a < 0) st4(slots + 4 * (-1 - a), c0, cA1, cA2, Real(0));
         if (b < 0) st4(slots + 4 * (-1 - b), -c0, -cB1, -cB2, Real(0));
       }
