@@ -811,7 +811,8 @@ def humps_leg(args, stream, errors):
 def summary(out):
     """The headline figures again, compact, at the end of the line."""
     r = lambda x: None if x is None else float(f"{x:.4g}")
-    s = {"fp32_10m": {"value": r(out["value"]), "hbm_frac": r(out["roofline"]["frac"])},
+    main_key = f"{out['dtype']}_{out['config']['workload']}"
+    s = {main_key: {"value": r(out["value"]), "hbm_frac": r(out["roofline"]["frac"])},
          "e2e": r(out["e2e"]["value"])}
     if "fp64" in out:
         s["fp64_10m"] = {"value": r(out["fp64"]["value"]), "hbm_frac": r(out["fp64"]["hbm_frac"]),

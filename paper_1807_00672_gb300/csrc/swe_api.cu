@@ -568,6 +568,8 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   L.add(4 * Tp);  // perm
   L.add(w * Tp);  // area
   L.add(w * Tp);  // irP
+  const bool with_rarea = kernel == SWE_KERNEL_TILED && p.precision == SWE_F64;
+  if (with_rarea) L.add(w * Tp);  // 1 / area
   if (kernel == SWE_KERNEL_EDGE) {
     L.add(4 * E); L.add(4 * E);
     L.add(w * E); L.add(w * E); L.add(w * E);
@@ -596,6 +598,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   m->perm = (int32_t*)m->arena.take(4 * Tp);
   m->area = m->arena.take(w * Tp);
   m->irP = m->arena.take(w * Tp);
+  if (with_rarea) m->rarea = m->arena.take(w * Tp);
   if (kernel == SWE_KERNEL_EDGE) {
     m->eL = (int32_t*)m->arena.take(4 * E);
     m->eR = (int32_t*)m->arena.take(4 * E);
@@ -627,7 +630,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   // Concatenated host arrays, uploaded one at a time.
   if (st == SWE_OK) {
     std::vector<int32_t> perm(Tp, -1);
-    std::vector<double> area(Tp, 0.0), irp(Tp, 0.0);
+    std::vector<double> area(Tp, 0.0), irp(Tp, 0.0), rarea;
     for (int i = 0; i < n; ++i) {
       const Scenario& sc = m->scen[i];
       for (int64_t j = 0; j < sc.ncells; ++j) {
@@ -639,6 +642,12 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     chk(upload(m, perm, m->perm));
     chk(upload_real(m, area, m->area));
     chk(upload_real(m, irp, m->irP));
+    if (with_rarea) {
+      rarea.assign(Tp, 0.0);  // padding cells: 0 (never updated)
+      for (int64_t j = 0; j < Tp; ++j)
+        if (area[j] > 0.0) rarea[j] = 1.0 / area[j];
+      chk(upload_real(m, rarea, m->rarea));
+    }
   }
   if (st == SWE_OK && kernel == SWE_KERNEL_EDGE) {
     const swe::HostMesh& h0 = hm[0];

@@ -73,6 +73,7 @@ struct swe_mesh {
   int32_t* perm = nullptr;  // internal cell -> caller cell (-1 for padding)
   void* area = nullptr;
   void* irP = nullptr;
+  void* rarea = nullptr;  // 1 / area, FP64 tiled meshes
   int32_t *eL = nullptr, *eR = nullptr, *cf[3] = {nullptr, nullptr, nullptr};
   void *nx = nullptr, *ny = nullptr, *len = nullptr;
   int64_t *toff = nullptr, *hoff = nullptr;
@@ -119,6 +120,7 @@ swe::DevMesh<Real> dev_mesh(const swe_mesh* m) {
   d.E = m->E;
   d.area = (const Real*)m->area;
   d.irP = (const Real*)m->irP;
+  d.rarea = (const Real*)m->rarea;
   d.eL = m->eL;
   d.eR = m->eR;
   d.nx = (const Real*)m->nx;

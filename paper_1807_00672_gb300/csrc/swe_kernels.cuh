@@ -102,6 +102,7 @@ struct DevMesh {
   // cells (internal order; the tiled layout pads them to whole tiles)
   const Real* area;
   const Real* irP;  // perimeter / area
+  const Real* rarea;  // 1 / area (FP64 tiled layout only, else null)
   // two-launch layout
   const int32_t* eL;
   const int32_t* eR;
@@ -588,32 +589,39 @@ __device__ __forceinline__ void face_flux_f64(const V4<double>& A, const V4<doub
     unB = B.y * nx + B.z * ny;
     utB = B.z * nx - B.y * ny;
   }
-  // hydrostatic reconstruction
+  // hydrostatic reconstruction. Comparisons against non-negative constants
+  // and sign tests are made on the IEEE bit patterns (as 64-bit integers they
+  // order non-negative doubles as their values, and every negative value,
+  // -0 included, below them), which keeps them off the FP64 pipe.
   const double zs = fmax(A.w, zB);
   const double xA = A.x + A.w - zs, xB = hB + zB - zs;
-  const double hAs = xA > eps ? xA : 0.0;
-  const double hBs = xB > eps ? xB : 0.0;
+  const long long beps = __double_as_longlong(eps);
+  const bool wA = __double_as_longlong(xA) > beps, wB = __double_as_longlong(xB) > beps;
+  const double hAs = wA ? xA : 0.0;  // x > h_eps, else dry
+  const double hBs = wB ? xB : 0.0;
   // HLLC wave speeds, a dry side entering with un_B - 2 c_B (A dry) or
   // un_A + 2 c_A (B dry)
   const double hg = 0.5 * g;
   const double cA = sqrt(g * hAs), cB = sqrt(g * hBs);
-  const double vnA = hAs > 0.0 ? unA : unB - 2.0 * cB;
-  const double vnB = hBs > 0.0 ? unB : unA + 2.0 * cA;
+  const double vnA = wA ? unA : unB - 2.0 * cB;
+  const double vnB = wB ? unB : unA + 2.0 * cA;
   const double us = (vnA + vnB) * 0.5 + cA - cB;
   const double cs = (cA + cB) * 0.5 + (vnA - vnB) * 0.25;
-  const double Sm = fmin(fmin(vnA - cA, us - cs), 0.0);
-  const double Sp = fmax(fmax(vnB + cB, us + cs), 0.0);
+  const double m1 = fmin(vnA - cA, us - cs), p1 = fmax(vnB + cB, us + cs);
+  const double Sm = __double_as_longlong(m1) < 0 ? m1 : 0.0;  // min(m1, 0)
+  const double Sp = __double_as_longlong(p1) > 0 ? p1 : 0.0;  // max(p1, 0)
   // HLL fluxes with the clamped speeds; e = g/2 h*^2 serves the flux and
   // the bed pressure g/2 (h^2 - h*^2)
   const double qA = hAs * unA, qB = hBs * unB;
   const double eA = hg * hAs * hAs, eB = hg * hBs * hBs;
   const double FA1 = qA * unA + eA;
   const double FB1 = qB * unB + eB;
-  const double inv = rcp_nr(fmax(Sp - Sm, 1e-300));
+  const double span = Sp - Sm;  // >= 0
+  const double inv = rcp_nr(__double_as_longlong(span) > __double_as_longlong(1e-300) ? span : 1e-300);
   const double SS = Sm * Sp;
   double F0 = (Sp * qA - Sm * qB + SS * (hBs - hAs)) * inv;
   const double F1 = (Sp * FA1 - Sm * FB1 + SS * (qB - qA)) * inv;
-  double F2 = F0 * (F0 >= 0.0 ? utA : utB);
+  double F2 = F0 * (__double_as_longlong(F0) >= 0 ? utA : utB);  // side A where F0 >= +0
   if (Wall) { F0 = 0.0; F2 = 0.0; }
   const double t1 = F2 * gy, t2 = F2 * gx;
   c0 = len * F0;
@@ -633,15 +641,16 @@ __device__ __forceinline__ void face_flux_f64(const V4<double>& A, const V4<doub
 // Per-cell end of the step: residual -> Euler update (Eq. 4) -> friction ->
 // next-step CFL rate. R: the residual (for Comp, the compensated face sum
 // rounded once, and U - a R is then one FMA). Writes the new state and
-// accumulates mass/rate.
-template <typename Real, bool Comp, typename Acc>
+// accumulates mass/rate. Recip: `area` holds 1 / area (a = dt / area is then
+// one product; no mass is accumulated).
+template <typename Real, bool Comp, typename Acc, bool Recip = false>
 __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area, Real irP, Real gn2,
                                             Real dt, const Real R[3], const Num& num, Real& h1,
                                             Real& hu1, Real& hv1, Acc& mass, Real& rate, Real& chk,
                                             int& neg) {
   using O = Ops<Real>;
   const Real zero = Real(0);
-  const Real a = O::div(dt, area);
+  const Real a = Recip ? dt * area : O::div(dt, area);
   Real out[3];
   if constexpr (Comp && sizeof(Real) == 4) {
     out[0] = fma_rn(-a, R[0], h);
@@ -677,7 +686,7 @@ __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area,
   // chk stays 0 unless a value is NaN or infinite (0 x that = NaN)
   chk = fma_rn(hs + qx + qy, Real(0), chk);
   h1 = hs; hu1 = qx; hv1 = qy;
-  mass.add(area, hs);
+  if constexpr (!Recip) mass.add(area, hs);
 }
 
 // ---------------------------------------------------------------------------
@@ -1267,7 +1276,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     for (int cc = 0; cc < CPT; ++cc) {
       const int j = tid + cc * NT;
       if (TC % NT != 0 && j >= TC) break;
-      c_area[cc] = m.area[base + j];
+      c_area[cc] = kVel ? m.rarea[base + j] : m.area[base + j];  // FP64: 1 / area
       c_irP[cc] = m.irP[base + j];
       c_gn2[cc] = s.gn2[base + j];
     }
@@ -1375,8 +1384,8 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       // FP64: the staged cell holds (h, u, v, z); its (hu, hv) are in registers
       const Real qx = kVel ? own_q[cc][0] : c.y, qy = kVel ? own_q[cc][1] : c.z;
       Real a1, b1, c1;
-      cell_finish<Real, Comp>(c.x, qx, qy, c_area[cc], c_irP[cc], c_gn2[cc], dt, R, num, a1, b1, c1,
-                              mass, rate, chk, neg);
+      cell_finish<Real, Comp, NoMass<Real>, kVel>(c.x, qx, qy, c_area[cc], c_irP[cc], c_gn2[cc], dt,
+                                                  R, num, a1, b1, c1, mass, rate, chk, neg);
       st4(U1 + 4 * (int64_t)(base + j), a1, b1, c1, c.w);
     }
     if constexpr (kVel) {
