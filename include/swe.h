@@ -264,7 +264,8 @@ void swe_state_destroy(swe_state* state);
  * state and to the gauge depths, the gradient of L with respect to the
  * initial state, the bed z and Manning's n. swe_grad can be called any
  * number of times on one tape (different seeds). Requires a single-scenario
- * mesh built with SWE_KERNEL_TILED (SWE_ESTATE otherwise). Results are in
+ * mesh built with SWE_KERNEL_TILED and without ghost cells (SWE_ESTATE
+ * otherwise). Results are in
  * the mesh precision; FP64 is the reference for accuracy. The adjoint runs
  * on the mesh's tiles: 256-cell tiles (swe_params.tile = 256) give the faster
  * adjoint, since at 512 cells its shared memory fits half as many blocks per
@@ -371,6 +372,92 @@ swe_status swe_step_edges_static(int64_t n_cells, int64_t n_edges, const int32_t
                                  const double* hv, double g, double courant, double h_eps,
                                  double dt, double* h_out, double* hu_out, double* hv_out,
                                  double* next_dt, double* mass, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Domain decomposition: one mesh split into sub-domains, for one step per
+ * sub-domain on its own GPU (or several on one) with a halo exchange and a
+ * global time step between steps. The paper names several GPUs on one mesh
+ * as future work (Sec. 5); the step itself is Sec. 2.2's.
+ *
+ * swe_partition_create orders the cells by the Morton code of their
+ * centroids and cuts that order into n_parts contiguous ranges of (nearly)
+ * equal size. Part p's local mesh holds its own cells plus one ring of
+ * ghost cells (cells of other parts sharing an edge with one of its cells),
+ * in ascending global order, each triangle with its global node order: every
+ * face of an owned cell is then oriented, and every cell's faces ordered, as
+ * in the whole mesh, so a step of the local mesh (swe_mesh_create_part)
+ * updates the owned cells bit for bit as the whole mesh's step does, when
+ * the ghosts hold their owners' current values and the step's dt is the
+ * global one. Per step: swe_run(state, 1) on every part; for every ordered
+ * pair (from, to), swe_state_halo_pack on `from` with the from-side list of
+ * swe_partition_exchange, move the buffer, swe_state_halo_unpack on `to`
+ * with the to-side list; swe_state_dt_device on every part, a min over the
+ * parts' values (NCCL all-reduce on several GPUs), swe_state_set_dt_min_device
+ * on every part. The mass of the whole mesh is the FP64 sum of the parts'
+ * swe_copy_out masses (ghosts excluded).
+ * --------------------------------------------------------------------------- */
+typedef struct swe_partition swe_partition;
+
+/* Builds the partition of a mesh (host arrays as for swe_mesh_create) into
+ * n_parts (1 <= n_parts <= n_tris) sub-domains. Host only; copies nothing
+ * it keeps but the plan. SWE_EMESH for an invalid mesh. */
+swe_status swe_partition_create(const double* xy, int64_t n_nodes, const int32_t* tri,
+                                int64_t n_tris, int32_t n_parts, swe_partition** out);
+
+/* sizes[0] = local cells of part `part` (owned and ghost), sizes[1] = ghost
+ * cells among them, sizes[2] = local nodes. */
+swe_status swe_partition_sizes(const swe_partition* plan, int32_t part, int64_t* sizes);
+
+/* Part `part`'s local mesh, into caller arrays sized by swe_partition_sizes
+ * (any may be NULL): cells [local cells] = global cell index of each local
+ * cell (ascending), ghost [local cells] = 1 for a ghost cell, else 0,
+ * local_xy [2 * local nodes] = coordinates of the local nodes taken from xy
+ * (the whole mesh's node array; needed only with local_xy), local_tri
+ * [3 * local cells] = local node ids of each local triangle. */
+swe_status swe_partition_local_mesh(const swe_partition* plan, int32_t part, const double* xy,
+                                    int32_t* cells, uint8_t* ghost, double* local_xy,
+                                    int32_t* local_tri);
+
+/* The cells owned by part `from` that part `to` holds as ghosts, in
+ * ascending global order: *n of them; from_cells[k] = its local index in
+ * `from`, to_cells[k] = its local index in `to` (either may be NULL: call
+ * once with both NULL to size them). from == to gives *n = 0. */
+swe_status swe_partition_exchange(const swe_partition* plan, int32_t from, int32_t to, int64_t* n,
+                                  int32_t* from_cells, int32_t* to_cells);
+
+void swe_partition_destroy(swe_partition* plan);
+
+/* swe_mesh_create for a sub-domain's local mesh: ghost [n_tris] (host,
+ * caller order) marks the ghost cells, which take part in the faces of the
+ * owned cells but not in the CFL time step nor in the mass integral (their
+ * own updates are overwritten by the halo exchange). Needs SWE_KERNEL_TILED
+ * (or AUTO), else SWE_EINVAL. */
+swe_status swe_mesh_create_part(const double* xy, int64_t n_nodes, const int32_t* tri,
+                                int64_t n_tris, const uint8_t* ghost, const swe_params* params,
+                                void* cuda_stream, swe_mesh** out);
+
+/* Queues, on the mesh's stream, buf[3 k + f] = field f (h, hu, hv; FP64) of
+ * local cell cells[k] of the current state, k < n. cells and buf are DEVICE
+ * arrays; entries outside [0, n_tris) are skipped. SWE_ESTATE unless the
+ * mesh came from swe_mesh_create_part. No synchronisation. */
+swe_status swe_state_halo_pack(const swe_state* state, const int32_t* cells, int64_t n,
+                               double* buf);
+
+/* Queues the reverse: field f of local cell cells[k] of the current state =
+ * buf[3 k + f] (DEVICE arrays), k < n. No synchronisation. */
+swe_status swe_state_halo_unpack(swe_state* state, const int32_t* cells, int64_t n,
+                                 const double* buf);
+
+/* Queues a copy of the CFL time step of the current state (Sec. 2.2,
+ * Courant 0.7, over its non-ghost cells) to the DEVICE double *dt.
+ * Single-scenario meshes. No synchronisation. */
+swe_status swe_state_dt_device(const swe_state* state, double* dt);
+
+/* Queues: the next step uses the smallest of the n DEVICE doubles dts[0..n)
+ * as its time step (the global CFL step of a decomposed mesh). Makes the
+ * state open-ended (no end time). Single-scenario meshes. No
+ * synchronisation. */
+swe_status swe_state_set_dt_min_device(swe_state* state, const double* dts, int32_t n);
 
 /* Measurement helper (no counterpart in the paper): FP64 fused multiply-add
  * throughput of the current device, for the FP64 path's arithmetic roofline.

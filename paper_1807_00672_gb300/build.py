@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["swe_api.cu", "mesh_build.cpp", "swe_noalloc.cu", "swe_grad.cu", "swe_peak.cu"]
+SOURCES = ["swe_api.cu", "mesh_build.cpp", "swe_noalloc.cu", "swe_grad.cu", "swe_peak.cu",
+           "partition.cpp", "swe_part.cu"]
 HEADERS = ["swe_kernels.cuh", "swe_adjoint.cuh", "swe_handles.cuh", "mesh_build.h"]
 
 

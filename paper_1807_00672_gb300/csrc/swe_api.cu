@@ -420,7 +420,7 @@ swe_status resolve_params(const swe_params* params, swe_params& p) {
 // Builds a mesh of n scenarios (swe_mesh_create_batch).
 swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nodes,
                         const int32_t* const* tri, const int64_t* n_tris, const swe_params* params,
-                        void* cuda_stream, swe_mesh** out) {
+                        void* cuda_stream, swe_mesh** out, const uint8_t* ghost = nullptr) {
   if (!out) return SWE_EINVAL;
   *out = nullptr;
   if (n <= 0 || !xy || !n_nodes || !tri || !n_tris) return SWE_EINVAL;
@@ -570,6 +570,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   L.add(w * Tp);  // irP
   const bool with_rarea = kernel == SWE_KERNEL_TILED && p.precision == SWE_F64;
   if (with_rarea) L.add(w * Tp);  // 1 / area
+  if (ghost) L.add(4 * T);        // caller cell -> internal cell
   if (kernel == SWE_KERNEL_EDGE) {
     L.add(4 * E); L.add(4 * E);
     L.add(w * E); L.add(w * E); L.add(w * E);
@@ -599,6 +600,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   m->area = m->arena.take(w * Tp);
   m->irP = m->arena.take(w * Tp);
   if (with_rarea) m->rarea = m->arena.take(w * Tp);
+  if (ghost) m->iperm = (int32_t*)m->arena.take(4 * T);
   if (kernel == SWE_KERNEL_EDGE) {
     m->eL = (int32_t*)m->arena.take(4 * E);
     m->eR = (int32_t*)m->arena.take(4 * E);
@@ -637,9 +639,18 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
         perm[sc.cell0 + j] = (int32_t)(sc.caller0 + hm[i].perm[j]);
         area[sc.cell0 + j] = hm[i].area[j];
         irp[sc.cell0 + j] = hm[i].perim[j] / hm[i].area[j];
+        // a ghost cell (a copy of another sub-domain's cell) is marked by
+        // perimeter / area = 0: it adds nothing to the CFL rate or the mass
+        if (ghost && ghost[sc.caller0 + hm[i].perm[j]]) irp[sc.cell0 + j] = 0.0;
       }
     }
     chk(upload(m, perm, m->perm));
+    if (ghost) {
+      std::vector<int32_t> iperm(T, -1);
+      for (int64_t j = 0; j < Tp; ++j)
+        if (perm[j] >= 0) iperm[perm[j]] = (int32_t)j;
+      chk(upload(m, iperm, m->iperm));
+    }
     chk(upload_real(m, area, m->area));
     chk(upload_real(m, irp, m->irP));
     if (with_rarea) {
@@ -854,6 +865,21 @@ const char* swe_last_cuda_error(void) { return g_cuda_msg.c_str(); }
 swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tris,
                            const swe_params* params, void* cuda_stream, swe_mesh** out) {
   return create_batch(1, &xy, &n_nodes, &tri, &n_tris, params, cuda_stream, out);
+}
+
+swe_status swe_mesh_create_part(const double* xy, int64_t n_nodes, const int32_t* tri,
+                                int64_t n_tris, const uint8_t* ghost, const swe_params* params,
+                                void* cuda_stream, swe_mesh** out) {
+  if (!out) return SWE_EINVAL;
+  *out = nullptr;
+  if (!ghost) return SWE_EINVAL;
+  swe_params p;
+  swe_status st = resolve_params(params, p);
+  if (st != SWE_OK) return st;
+  if (p.kernel != SWE_KERNEL_TILED) return SWE_EINVAL;
+  st = create_batch(1, &xy, &n_nodes, &tri, &n_tris, &p, cuda_stream, out, ghost);
+  if (st == SWE_OK) (*out)->ghosts = true;
+  return st;
 }
 
 swe_status swe_mesh_create_batch(int32_t n_scenarios, const double* const* xy,

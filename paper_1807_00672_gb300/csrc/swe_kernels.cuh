@@ -1474,7 +1474,7 @@ __global__ void __launch_bounds__(256) k_cfl_tiled(DevMesh<Real> m, DevState<Rea
         rate = fmax(rate, lam * m.irP[i]);
       }
       if (!isfinite(hh + qx + qy)) bad = 1;
-      mass.add(m.area[i], hh);
+      if (m.irP[i] != Real(0)) mass.add(m.area[i], hh);  // 0: a ghost (or padding) cell
     }
   }
   finish_launch<256>(ctl, s.partial, ch.part, ctl->part0, (int)ctl->nparts, mass.value(),

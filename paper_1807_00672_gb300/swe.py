@@ -37,6 +37,10 @@ EXPORTS = (
     "swe_last_cuda_error", "swe_step_edges_static", "swe_grad_record", "swe_grad",
     "swe_tape_info", "swe_tape_destroy", "swe_fp64_fma_rate", "swe_state_init_device",
     "swe_state_set_device", "swe_copy_out_device", "swe_grad_device", "swe_tape_gauges_device",
+    "swe_partition_create", "swe_partition_sizes", "swe_partition_local_mesh",
+    "swe_partition_exchange", "swe_partition_destroy", "swe_mesh_create_part",
+    "swe_state_halo_pack", "swe_state_halo_unpack", "swe_state_dt_device",
+    "swe_state_set_dt_min_device",
 )
 
 
@@ -112,6 +116,16 @@ def lib():
         "swe_copy_out_device": (st, [vp, vp, vp, vp, vp, vp, vp]),
         "swe_grad_device": (st, [vp] + [vp] * 9 + [vp]),
         "swe_tape_gauges_device": (st, [vp, vp, vp]),
+        "swe_partition_create": (st, [vp, i64, vp, i64, ctypes.c_int32, pp]),
+        "swe_partition_sizes": (st, [vp, ctypes.c_int32, vp]),
+        "swe_partition_local_mesh": (st, [vp, ctypes.c_int32, vp, vp, vp, vp, vp]),
+        "swe_partition_exchange": (st, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp]),
+        "swe_partition_destroy": (None, [vp]),
+        "swe_mesh_create_part": (st, [vp, i64, vp, i64, vp, P, vp, pp]),
+        "swe_state_halo_pack": (st, [vp, vp, i64, vp]),
+        "swe_state_halo_unpack": (st, [vp, vp, i64, vp]),
+        "swe_state_dt_device": (st, [vp, vp]),
+        "swe_state_set_dt_min_device": (st, [vp, vp, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -211,6 +225,32 @@ class Mesh:
         self.scenario_cells = [int(x) for x in counts]
         self.scenario_offsets = [0] + list(np.cumsum(counts)[:-1].astype(int))
 
+    @classmethod
+    def part(cls, xy, tri, ghost, *, precision="f64", order="morton", tile=0, stages=0,
+             cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6):
+        """A sub-domain's local mesh with ghost cells (swe_mesh_create_part);
+        ghost: one flag per triangle, nonzero for a ghost."""
+        self = cls.__new__(cls)
+        xy = _f64(xy).reshape(-1, 2)
+        tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        gh = np.ascontiguousarray(ghost, dtype=np.uint8).reshape(-1)
+        if gh.shape[0] != tri.shape[0]:
+            raise ValueError("one ghost flag per triangle")
+        self.prm = params(precision, order, "tiled", tile, g, courant, h_eps, stages,
+                          cells_per_thread)
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(lib().swe_mesh_create_part(_p(xy), xy.shape[0], _p(tri), tri.shape[0], _p(gh),
+                                          ctypes.byref(self.prm), stream, ctypes.byref(h)),
+               "swe_mesh_create_part")
+        self._h = h
+        c = np.zeros(4, dtype=np.int64)
+        lib().swe_mesh_counts(self._h, _p(c))
+        self.V, self.T, self.E, self.Eb = (int(x) for x in c)
+        self.scenario_cells = [self.T]
+        self.scenario_offsets = [0]
+        return self
+
     @property
     def n_scenarios(self) -> int:
         return len(self.scenario_cells)
@@ -272,6 +312,26 @@ class State:
         """swe_state_set_device: device addresses (ints) of float64 arrays."""
         _check(lib().swe_state_set_device(self._h, _vp(h), _vp(hu), _vp(hv), _vp(stream)),
                "swe_state_set_device")
+
+    def halo_pack(self, cells, n, buf):
+        """swe_state_halo_pack: device addresses (ints) of n int32 local cell
+        ids and of a 3 n float64 buffer."""
+        _check(lib().swe_state_halo_pack(self._h, _vp(cells), int(n), _vp(buf)),
+               "swe_state_halo_pack")
+
+    def halo_unpack(self, cells, n, buf):
+        """swe_state_halo_unpack (device addresses as for halo_pack)."""
+        _check(lib().swe_state_halo_unpack(self._h, _vp(cells), int(n), _vp(buf)),
+               "swe_state_halo_unpack")
+
+    def dt_device(self, dst):
+        """swe_state_dt_device: the current CFL dt into a device double."""
+        _check(lib().swe_state_dt_device(self._h, _vp(dst)), "swe_state_dt_device")
+
+    def set_dt_min_device(self, dts, n):
+        """swe_state_set_dt_min_device: next dt = min of n device doubles."""
+        _check(lib().swe_state_set_dt_min_device(self._h, _vp(dts), int(n)),
+               "swe_state_set_dt_min_device")
 
     def copy_out_device(self, h=None, hu=None, hv=None, stream=None):
         """swe_copy_out_device into device addresses (ints, any may be None);
@@ -426,3 +486,57 @@ def fp64_fma_rate(stream=None) -> float:
     r = ctypes.c_double()
     _check(lib().swe_fp64_fma_rate(stream, ctypes.byref(r)), "swe_fp64_fma_rate")
     return r.value
+
+
+class Partition:
+    """swe_partition: the mesh (xy, tri) cut into n_parts sub-domains, each a
+    local mesh of its own cells plus one ring of ghost cells, and the halo
+    exchange lists between them."""
+
+    def __init__(self, xy, tri, n_parts: int):
+        self.xy = _f64(xy).reshape(-1, 2)
+        t = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        h = ctypes.c_void_p()
+        _check(lib().swe_partition_create(_p(self.xy), self.xy.shape[0], _p(t), t.shape[0],
+                                          int(n_parts), ctypes.byref(h)), "swe_partition_create")
+        self._h = h
+        self.n_parts = int(n_parts)
+        self.n_tris = t.shape[0]
+
+    def local(self, part: int) -> dict:
+        """cells (global ids, ascending), ghost flags, local xy and tri."""
+        sz = np.zeros(3, dtype=np.int64)
+        _check(lib().swe_partition_sizes(self._h, int(part), _p(sz)), "swe_partition_sizes")
+        n, _, nv = (int(x) for x in sz)
+        cells = np.zeros(n, dtype=np.int32)
+        ghost = np.zeros(n, dtype=np.uint8)
+        xy = np.zeros((nv, 2))
+        tri = np.zeros((n, 3), dtype=np.int32)
+        _check(lib().swe_partition_local_mesh(self._h, int(part), _p(self.xy), _p(cells),
+                                              _p(ghost), _p(xy), _p(tri)),
+               "swe_partition_local_mesh")
+        return dict(cells=cells, ghost=ghost, xy=xy, tri=tri)
+
+    def exchange(self, src: int, dst: int):
+        """(src-side local ids, dst-side local ids) of the cells owned by
+        part src that part dst holds as ghosts."""
+        n = ctypes.c_int64()
+        _check(lib().swe_partition_exchange(self._h, int(src), int(dst), ctypes.byref(n), None,
+                                            None), "swe_partition_exchange")
+        a = np.zeros(n.value, dtype=np.int32)
+        b = np.zeros(n.value, dtype=np.int32)
+        if n.value:
+            _check(lib().swe_partition_exchange(self._h, int(src), int(dst), ctypes.byref(n),
+                                                _p(a), _p(b)), "swe_partition_exchange")
+        return a, b
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().swe_partition_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
