@@ -26,6 +26,8 @@ ones under gloo.
 """
 from __future__ import annotations
 
+import contextlib
+
 import numpy as np
 import torch
 
@@ -47,26 +49,36 @@ class GpuSubdomain:
         self.cells = loc["cells"]
         self.ghost = loc["ghost"].astype(bool)
         self.device = torch.device("cuda", torch.cuda.current_device())
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        h = self.stream.cuda_stream
+        # The library's kernels and every torch operation on this part's
+        # buffers share one (non-default) stream: packs, unpacks, the time
+        # step reductions and the steps are ordered by it.
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        if not self.stream.cuda_stream:
+            raise ValueError("a sub-domain needs a non-default CUDA stream")
         self.mesh = swe.Mesh.part(loc["xy"], loc["tri"], loc["ghost"], precision=precision,
-                                  tile=tile, stream=swe._vp(h))
+                                  tile=tile, stream=swe._vp(self.stream.cuda_stream))
         h0, hu0, hv0, z, n = (np.asarray(f, dtype=np.float64)[self.cells] for f in fields)
         self.state = swe.State(self.mesh, h0, hu0, hv0, z, n)
         # exchange lists: cells this part sends to each peer, and where each
         # peer's cells land here
         self.send, self.recv, self.buf = {}, {}, {}
-        for q in range(plan.n_parts):
-            if q == part:
-                continue
-            a, _ = plan.exchange(part, q)
-            _, b = plan.exchange(q, part)
-            if a.size:
-                self.send[q] = torch.from_numpy(a).to(self.device)
-                self.buf[q] = torch.empty(3 * a.size, dtype=torch.float64, device=self.device)
-            if b.size:
-                self.recv[q] = torch.from_numpy(b).to(self.device)
-        self._dt = torch.empty(1, dtype=torch.float64, device=self.device)
+        with torch.cuda.stream(self.stream):
+            for q in range(plan.n_parts):
+                if q == part:
+                    continue
+                a, _ = plan.exchange(part, q)
+                _, b = plan.exchange(q, part)
+                if a.size:
+                    self.send[q] = torch.from_numpy(a).to(self.device)
+                    self.buf[q] = torch.empty(3 * a.size, dtype=torch.float64, device=self.device)
+                if b.size:
+                    self.recv[q] = torch.from_numpy(b).to(self.device)
+            self._dt = torch.empty(1, dtype=torch.float64, device=self.device)
+        self.stream.synchronize()
+
+    def stream_context(self):
+        """Makes this part's stream torch's current one (for collectives)."""
+        return torch.cuda.stream(self.stream)
 
     # --- the sub-domain interface of run_distributed ----------------------
     def step(self):
@@ -78,7 +90,9 @@ class GpuSubdomain:
         return self.buf[peer]
 
     def recv_buffer(self, peer: int) -> torch.Tensor:
-        return torch.empty(3 * self.recv[peer].numel(), dtype=torch.float64, device=self.device)
+        with torch.cuda.stream(self.stream):
+            return torch.empty(3 * self.recv[peer].numel(), dtype=torch.float64,
+                               device=self.device)
 
     def unpack(self, peer: int, buf: torch.Tensor):
         ids = self.recv[peer]
@@ -116,10 +130,13 @@ class LocalRun:
         self.plan = swe.Partition(xy, tri, n_parts)
         self.n_tris = self.plan.n_tris
         dev = torch.device("cuda", torch.cuda.current_device())
-        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        # one stream for every part: each part's work is ordered after the
+        # packs of its peers and the reductions
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
         self.parts = [GpuSubdomain(self.plan, p, fields, precision=precision, tile=tile,
                                    stream=self.stream) for p in range(n_parts)]
-        self._dts = torch.empty(n_parts, dtype=torch.float64, device=dev)
+        with torch.cuda.stream(self.stream):
+            self._dts = torch.empty(n_parts, dtype=torch.float64, device=dev)
         self._global_dt()  # the first step already takes the global CFL step
 
     def _global_dt(self):
@@ -162,6 +179,12 @@ def run_distributed(sub, n_steps: int, dist, group=None):
     point-to-point send/receive, ordered by peer so that every pair's
     transfers match; the global time step is an all-reduce (min), taken
     once before the first step as well."""
+    ctx = sub.stream_context() if hasattr(sub, "stream_context") else contextlib.nullcontext()
+    with ctx:
+        _run_distributed(sub, n_steps, dist, group)
+
+
+def _run_distributed(sub, n_steps, dist, group):
     dt = sub.dt().clone()
     dist.all_reduce(dt, op=dist.ReduceOp.MIN, group=group)
     sub.set_dt(dt)
@@ -185,6 +208,8 @@ def run_distributed(sub, n_steps: int, dist, group=None):
 
 def global_mass(sub, dist, group=None) -> float:
     """FP64 all-reduce (sum) of the sub-domains' owned masses."""
-    m = torch.tensor([float(sub.mass())], dtype=torch.float64, device=sub.dt().device)
-    dist.all_reduce(m, op=dist.ReduceOp.SUM, group=group)
-    return float(m.item())
+    ctx = sub.stream_context() if hasattr(sub, "stream_context") else contextlib.nullcontext()
+    with ctx:
+        m = torch.tensor([float(sub.mass())], dtype=torch.float64, device=sub.dt().device)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM, group=group)
+        return float(m.item())
