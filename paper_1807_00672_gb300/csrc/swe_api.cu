@@ -229,14 +229,16 @@ void launch_one_step(const swe_state* s, cudaStream_t st) {
   else launch_forward(s->mesh, dev_state<float>(s), st);
 }
 
+// CFL step (kind swe::kCflOnly) or mass only (swe::kMassOnly, tiled
+// meshes) of the current state.
 template <typename Real>
-void launch_cfl(const swe_state* s) {
+void launch_cfl(const swe_state* s, int kind = swe::kCflOnly) {
   const swe_mesh* m = s->mesh;
   if (m->kernel == SWE_KERNEL_EDGE)
     swe::k_cfl<Real><<<m->grid_cfl, 256, 0, m->stream>>>(dev_mesh<Real>(m), dev_state<Real>(s), num_of(m));
   else
     swe::k_cfl_tiled<Real><<<(int)m->nchunks, 256, 0, m->stream>>>(dev_mesh<Real>(m), dev_state<Real>(s),
-                                                                  num_of(m), m->tile);
+                                                                  num_of(m), m->tile, kind);
 }
 
 template <typename Real>
@@ -383,6 +385,7 @@ swe_status reset_and_cfl(swe_state* s) {
     c.t_end = std::numeric_limits<double>::infinity();
     c.part0 = m->scen[i].chunk0;
     c.nparts = m->scen[i].nchunks;
+    c.subdomain = m->ghosts ? 1 : 0;
     s->host_ctl[i] = c;
   }
   s->open_ended = true;
@@ -744,13 +747,13 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
 }
 
 // Integrates every scenario's mass into its control word. The tiled step
-// does not integrate it; k_cfl_tiled does, from the current state (it also
-// recomputes the CFL dt of that same state, which leaves it unchanged).
+// does not integrate it; k_cfl_tiled does, from the current state, leaving
+// the step control (time step, end-time clamp, stop flag) as it is.
 void refresh_mass(const swe_state* s) {
   const swe_mesh* m = s->mesh;
   if (m->kernel == SWE_KERNEL_TILED) {
-    if (m->prm.precision == SWE_F64) launch_cfl<double>(s);
-    else launch_cfl<float>(s);
+    if (m->prm.precision == SWE_F64) launch_cfl<double>(s, swe::kMassOnly);
+    else launch_cfl<float>(s, swe::kMassOnly);
   }
   swe::k_mass_sum<<<nscen(m), 256, 0, m->stream>>>(s->ctl, s->partial);
 }

@@ -45,7 +45,8 @@ struct Ctl {
   int clamped;       // dt == t_end - t
   int err;           // latched error bits
   unsigned int ticket;  // blocks of this scenario finished in the current launch
-  int pad_;
+  int subdomain;     // 1: a sub-domain of a decomposed mesh (its CFL step may be
+                     // +inf when none of its own cells is wet; not an error here)
 };
 // A mesh holds one or more independent scenarios (an ensemble); each has its
 // own control word, and a launch's blocks each work for one scenario.
@@ -703,15 +704,22 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// What a launch that ends with finish_launch did.
+enum LaunchKind { kStepped = 0, kCflOnly = 1, kMassOnly = 2 };
+
 // Every thread of the block calls this once at the end of an update launch.
 // The block is one of `nblocks` working for the scenario of `ctl`; its mass
 // partial sum goes to partial[part], the scenario's partials being
-// partial[part0 .. part0 + nblocks). stepped: the launch advanced the state
-// by ctl->dt (false: CFL/mass only). err: kErr* bits seen by this thread.
+// partial[part0 .. part0 + nblocks). kind: kStepped, the launch advanced the
+// state by ctl->dt; kCflOnly, the CFL step of the current state is set
+// (initialisation); kMassOnly, only the mass partials are refreshed and the
+// step control (time, time step, stop flag) stays as it is. err: kErr* bits
+// seen by this thread.
 template <int NT>
 __device__ void finish_launch(Ctl* ctl, double* partial, long long part, long long part0,
                               int nblocks, double mass, double rate, int err_bits, int neg,
-                              bool stepped, double courant) {
+                              int kind, double courant) {
+  const bool stepped = kind == kStepped;
   __shared__ double s_mass[NT / 32];
   __shared__ double s_rate[NT / 32];
   __shared__ int s_bad[NT / 32];
@@ -750,6 +758,7 @@ __device__ void finish_launch(Ctl* ctl, double* partial, long long part, long lo
     ctl->nparts = nblocks;
     const unsigned long long bits = atomicExch(&ctl->rate_bits, 0ull);
     ctl->ticket = 0u;
+    if (kind == kMassOnly) return;  // errors this launch saw are latched above
     double t = ctl->t;
     if (stepped) {
       ctl->dt_last = ctl->dt;
@@ -760,7 +769,9 @@ __device__ void finish_launch(Ctl* ctl, double* partial, long long part, long lo
     }
     int err = atomicOr(&ctl->err, 0);
     const double maxrate = __longlong_as_double((long long)bits);
-    if (!(maxrate > 0.0) && !(err & kErrTimeout)) err |= kErrDry;  // blocks that gave up add no rate
+    // blocks that gave up add no rate; a sub-domain with no wet cell of its
+    // own gets dt_cfl = +inf (the global minimum decides)
+    if (!(maxrate > 0.0) && !(err & kErrTimeout) && !ctl->subdomain) err |= kErrDry;
     if (err) {
       atomicOr(&ctl->err, err);
       ctl->done = 1;
@@ -864,7 +875,7 @@ __global__ void __launch_bounds__(256) k_cell_update(DevMesh<Real> m, DevState<R
     hv1[i] = c1;
   }
   finish_launch<256>(ctl, s.partial, blockIdx.x, 0, gridDim.x, mass.value(), (double)rate,
-                     chk != Real(0) ? kErrNan : 0, neg, true, num.courant);
+                     chk != Real(0) ? kErrNan : 0, neg, kStepped, num.courant);
 }
 
 // ---------------------------------------------------------------------------
@@ -1418,8 +1429,8 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       if ((pending >> i) & 1u) mbar_wait(&bar[i], (parity_bits >> i) & 1u);
   }
   finish_launch<NT>(ctl, s.partial, ch.part, ctl->part0, (int)ctl->nparts, mass.value(),
-                    (double)rate, (chk != Real(0) ? kErrNan : 0) | (timeout ? kErrTimeout : 0), neg, true,
-                    num.courant);
+                    (double)rate, (chk != Real(0) ? kErrNan : 0) | (timeout ? kErrTimeout : 0), neg,
+                    kStepped, num.courant);
 }
 
 // CFL rate and mass of the current state, no step (initialisation), one
@@ -1447,14 +1458,15 @@ __global__ void __launch_bounds__(256) k_cfl(DevMesh<Real> m, DevState<Real> s, 
     mass.add(m.area[i], hh);
   }
   finish_launch<256>(ctl, s.partial, blockIdx.x, 0, gridDim.x, mass.value(), (double)rate,
-                     bad ? kErrNan : 0, 0, false, num.courant);
+                     bad ? kErrNan : 0, 0, kCflOnly, num.courant);
 }
 
 // The same on interleaved cells, over the tiled layout's work chunks (every
-// scenario of the mesh). TC: cells per tile.
+// scenario of the mesh). TC: cells per tile. kind: kCflOnly (set the CFL
+// step) or kMassOnly (mass on demand, step control untouched).
 template <typename Real>
 __global__ void __launch_bounds__(256) k_cfl_tiled(DevMesh<Real> m, DevState<Real> s, Num num,
-                                                   int TC) {
+                                                   int TC, int kind) {
   using O = Ops<Real>;
   const Chunk ch = m.chunks[blockIdx.x];
   Ctl* ctl = s.ctl + ch.scen;
@@ -1478,7 +1490,7 @@ __global__ void __launch_bounds__(256) k_cfl_tiled(DevMesh<Real> m, DevState<Rea
     }
   }
   finish_launch<256>(ctl, s.partial, ch.part, ctl->part0, (int)ctl->nparts, mass.value(),
-                     (double)rate, bad ? kErrNan : 0, 0, false, num.courant);
+                     (double)rate, bad ? kErrNan : 0, 0, kind, num.courant);
 }
 
 // Mass integral of each scenario's latest launch: the sum of its per-block

@@ -72,6 +72,12 @@ __global__ void k_dt_set_min(swe::Ctl* ctl, const double* dts, int n) {
   if (ctl->done) return;  // an error is latched: no further step
   double m = dts[0];
   for (int i = 1; i < n; ++i) m = fmin(m, dts[i]);
+  if (!(m < INFINITY)) {  // no wet cell in any sub-domain
+    atomicOr(&ctl->err, swe::kErrDry);
+    ctl->done = 1;
+    ctl->dt = 0.0;
+    return;
+  }
   ctl->dt = m;
   ctl->dt_cfl = m;
   ctl->clamped = 0;
