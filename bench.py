@@ -214,6 +214,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--cpt", type=int, default=0, help="cells per thread of the tiled kernel")
+    ap.add_argument("--halo-schedule", type=int, default=0,
+                    help="tiled kernel variant: 0 default, 1 early halo gather, 2 pipelined")
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=0, help="solver steps per e2e call (0 = --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -272,7 +274,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=args.precision, kernel=args.kernel,
                     tile=args.tile, stages=args.stages, cells_per_thread=args.cpt,
-                    stream=ctypes_stream(stream))
+                    halo_schedule=args.halo_schedule, stream=ctypes_stream(stream))
     st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
     T = mesh.T
     kernels_per_step = 2 if args.kernel == "edge" else 1

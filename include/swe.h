@@ -88,13 +88,16 @@ typedef struct {
   int32_t stages;     /* shared-memory pipeline stages of SWE_KERNEL_TILED (2 or 3);
                          0 = default (2) */
   int32_t cells_per_thread;  /* cells each thread updates per tile (1 or 2); 0 = default (2) */
-  int32_t halo_schedule;     /* when SWE_KERNEL_TILED gathers a tile's halo cells: 0 = default,
-                                after the previous tile's face loop; 1 = at the start of the
-                                previous tile, so the gather overlaps its whole face loop
-                                (faster on some ensembles, slower on single large meshes: a
-                                choice for the autotuner). 1 applies to FP32 meshes with 2
-                                stages whose halo lists fit one entry per thread, and is
-                                ignored otherwise. Results are identical. */
+  int32_t halo_schedule;     /* schedule of the SWE_KERNEL_TILED step: 0 = default, a tile's
+                                halo cells gathered after the previous tile's face loop;
+                                1 = gathered at the start of the previous tile, so the gather
+                                overlaps its whole face loop; 2 = pipelined: the cell updates
+                                of a tile overlap the face loop of the next one, one block
+                                barrier per tile instead of two (two sets of face slots).
+                                Which is faster depends on the mesh: a choice for the
+                                autotuner. 1 and 2 apply to FP32 meshes with 2 stages whose
+                                halo lists fit one entry per thread, and are ignored
+                                otherwise. Results are identical. */
   int32_t wait_rounds;       /* bounded device waits of SWE_KERNEL_TILED steps (a block waiting
                                 for its tile copies) give up after this many rounds of at most
                                 20 us and latch SWE_ETIMEOUT: 0 = default (50,000 rounds,

@@ -22,10 +22,12 @@ import time
 from . import swe
 
 # (tile, cells_per_thread, stages[, halo_schedule]); threads per block =
-# tile / cells_per_thread; a missing halo_schedule is 0.
+# tile / cells_per_thread; a missing halo_schedule is 0 (2: the pipelined
+# kernel, FP32 only; in FP64 those shapes run as schedule 0 or are skipped).
 CANDIDATES = (
     (256, 2, 2), (256, 2, 2, 1), (256, 2, 3), (256, 1, 2), (256, 1, 3),
     (512, 2, 2), (512, 2, 2, 1), (128, 1, 2), (128, 2, 3),
+    (256, 1, 2, 2), (512, 2, 2, 2), (512, 1, 2, 2),
 )
 
 

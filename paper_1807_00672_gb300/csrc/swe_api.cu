@@ -142,18 +142,48 @@ int prepare_tiled(const swe::TileLayout& L) {
   return n;
 }
 
+// Opts the pipelined FP32 kernel (halo_schedule 2) into its dynamic shared
+// memory; resident blocks per SM.
+template <int NT, int TC>
+int prepare_pipe(const swe::TileLayout& L) {
+  auto k = swe::k_tiled_step_pipe<NT, TC>;
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int cap = swe_host::smem_optin_bytes() - (int)fa.sharedSizeBytes;
+  if (cap <= 0 || (int)L.total > cap ||
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 template <typename Real, int NT, int CPT>
 int blocks_per_sm_tiled_nt(const swe_mesh* m) {
   constexpr int TC = NT * CPT;
-  // the Early kernel (halo_schedule 1) exists for FP32 with 2 stages only
-  if constexpr (sizeof(Real) == 4)
+  // the Early kernel (halo_schedule 1) and the pipelined one (2) exist for
+  // FP32 with 2 stages only
+  if constexpr (sizeof(Real) == 4) {
+    if (m->layout.pipe) return prepare_pipe<NT, TC>(m->layout);
     if (m->layout.early) return prepare_tiled<Real, NT, 2, TC, true>(m->layout);
+  }
   return m->stages == 3 ? prepare_tiled<Real, NT, 3, TC>(m->layout)
                         : prepare_tiled<Real, NT, 2, TC>(m->layout);
 }
 
 template <typename Real, int CPT>
 int blocks_per_sm_tiled_cpt(const swe_mesh* m) {
+  if constexpr (sizeof(Real) == 4 && CPT == 1) {
+    if (m->tile == 512) return m->layout.pipe ? prepare_pipe<512, 512>(m->layout) : 0;
+  }
   switch (m->tile / CPT) {
     case 32: return blocks_per_sm_tiled_nt<Real, 32, CPT>(m);
     case 64: return blocks_per_sm_tiled_nt<Real, 64, CPT>(m);
@@ -187,20 +217,34 @@ void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe:
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if constexpr (sizeof(Real) == 4) {
-    if (L.early) {
-      cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, true>, dm, ds, num, L);
+    if (L.pipe) {
+      cudaLaunchKernelEx(&cfg, swe::k_tiled_step_pipe<NT, TC>, dm, ds, num, L);
       return;
     }
   }
-  if (m->stages == 3)
-    cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 3, TC>, dm, ds, num, L);
-  else
-    cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC>, dm, ds, num, L);
+  if constexpr (NT <= 256) {  // 512 threads exist only for the pipelined kernel
+    if constexpr (sizeof(Real) == 4) {
+      if (L.early) {
+        cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, true>, dm, ds, num, L);
+        return;
+      }
+    }
+    if (m->stages == 3)
+      cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 3, TC>, dm, ds, num, L);
+    else
+      cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC>, dm, ds, num, L);
+  }
 }
 
 template <typename Real, bool Comp, int CPT>
 void launch_tiled_cpt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe::DevState<Real>& ds,
                       const swe::Num& num, cudaStream_t st) {
+  if constexpr (sizeof(Real) == 4 && CPT == 1) {
+    if (m->tile == 512) {  // 512 threads: the pipelined kernel only
+      launch_tiled_nt<Real, Comp, 512, 1>(m, dm, ds, num, st);
+      return;
+    }
+  }
   switch (m->tile / CPT) {
     case 32: launch_tiled_nt<Real, Comp, 32, CPT>(m, dm, ds, num, st); break;
     case 64: launch_tiled_nt<Real, Comp, 64, CPT>(m, dm, ds, num, st); break;
@@ -410,10 +454,14 @@ swe_status resolve_params(const swe_params* params, swe_params& p) {
     p.tile = (p.precision == SWE_F32 && p.cells_per_thread == 2) ? kDefaultTileF32 : kDefaultTileF64;
   if (p.cells_per_thread != 1 && p.cells_per_thread != 2) return SWE_EINVAL;
   const int nt = p.tile / p.cells_per_thread;
-  if (p.tile % p.cells_per_thread != 0 || (nt != 32 && nt != 64 && nt != 128 && nt != 256)) return SWE_EINVAL;
   if (p.stages == 0) p.stages = 2;
+  // 512 threads per block: only the pipelined FP32 kernel, one cell per thread
+  const bool nt512 = nt == 512 && p.halo_schedule == 2 && p.precision == SWE_F32 &&
+                     p.cells_per_thread == 1 && p.stages == 2;
+  if (p.tile % p.cells_per_thread != 0 || (nt != 32 && nt != 64 && nt != 128 && nt != 256 && !nt512))
+    return SWE_EINVAL;
   if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
-  if (p.halo_schedule != 0 && p.halo_schedule != 1) return SWE_EINVAL;
+  if (p.halo_schedule < 0 || p.halo_schedule > 2) return SWE_EINVAL;
   if (p.wait_rounds < -1) return SWE_EINVAL;
   if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
   if (p.kernel == SWE_KERNEL_AUTO) p.kernel = SWE_KERNEL_TILED;
@@ -524,9 +572,15 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   // order as slots free up, balances the SMs (longest-processing-time order).
   std::vector<swe::Chunk> chunks;
   if (kernel == SWE_KERNEL_TILED) {
+    const bool want_pipe = p.halo_schedule == 2 && p.precision == SWE_F32 && m->stages == 2;
     m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)geo_arrays, (uint32_t)tile,
                                       (uint32_t)m->stages, (uint32_t)rec_cap, (uint32_t)halo_cap,
-                                      (uint32_t)(tile / m->cpt));
+                                      (uint32_t)(tile / m->cpt), want_pipe ? 2u : 1u);
+    if (want_pipe && !m->layout.hreg)  // the pipelined kernel needs halo indices in registers
+      m->layout = swe::make_tile_layout((uint32_t)w, (uint32_t)geo_arrays, (uint32_t)tile,
+                                        (uint32_t)m->stages, (uint32_t)rec_cap, (uint32_t)halo_cap,
+                                        (uint32_t)(tile / m->cpt));
+    m->layout.pipe = (want_pipe && m->layout.hreg) ? 1u : 0u;
     m->layout.early =
         (m->layout.hreg && p.halo_schedule == 1 && p.precision == SWE_F32 && m->stages == 2) ? 1u : 0u;
     const int occ = (p.precision == SWE_F64) ? blocks_per_sm_tiled<double>(m)

@@ -966,13 +966,17 @@ struct TileLayout {
   uint32_t off_slots, off_bars, total;
   uint32_t hreg;   // 1: halo lists read from DevMesh::hpad into registers, not staged
   uint32_t early;  // 1 (with hreg): launch the Early kernel (halo_schedule 1)
+  uint32_t slot_bytes;  // one set of face slots
+  uint32_t pipe;   // 1 (with hreg, FP32, 2 stages, two slot sets): launch
+                   // k_tiled_step_pipe (halo_schedule 2)
 };
 
 // nt: threads per block. When no tile has more halo cells than the block has
 // threads, each thread prefetches at most one halo index into a register and
 // the stages hold no halo list.
 inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, uint32_t ns,
-                                   uint32_t rec_cap, uint32_t halo_cap, uint32_t nt) {
+                                   uint32_t rec_cap, uint32_t halo_cap, uint32_t nt,
+                                   uint32_t slot_sets = 1) {
   auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
   TileLayout L{};
   L.rec_cap = rec_cap;
@@ -993,7 +997,8 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
   L.off_hidx = o; o += L.hreg ? 0u : a16(halo_cap * 4);
   L.stage = o;
   o = ns * L.stage;
-  L.off_slots = o; o += a16(3 * tc * 4 * w);
+  L.slot_bytes = a16(3 * tc * 4 * w);
+  L.off_slots = o; o += slot_sets * L.slot_bytes;
   L.off_bars = o; o += a16(ns * 8);
   L.total = o;
   return L;
@@ -1423,6 +1428,250 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   }
   // After a timed-out wait, let every copy still in flight land before the
   // block's shared memory is released (bounded as well).
+  if (timeout && tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+      if ((pending >> i) & 1u) mbar_wait(&bar[i], (parity_bits >> i) & 1u);
+  }
+  finish_launch<NT>(ctl, s.partial, ch.part, ctl->part0, (int)ctl->nparts, mass.value(),
+                    (double)rate, (chk != Real(0) ? kErrNan : 0) | (timeout ? kErrTimeout : 0), neg,
+                    kStepped, num.courant);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 tiled step with one block barrier per tile (halo_schedule 2). The
+// same tiles, records, halo prefetch and arithmetic as k_tiled_step (the
+// same bits), software-pipelined across tiles: iteration k updates the
+// cells of tile k-1 and then computes the face records of tile k, with two
+// sets of face slots (tile k-1's are read while tile k's are written). The
+// tile's own cells (h, hu, hv, z) and its area, perimeter/area and g n^2
+// are taken into registers in the iteration of its faces, so its stage is
+// free again when tile k+1's copies are queued at the start of iteration k.
+// Needs the layout's hreg (halo indices in registers) and two slot sets;
+// 2 stages.
+// ---------------------------------------------------------------------------
+// Resident blocks per SM the pipelined kernel is compiled for: 1,024
+// threads per SM with one cell per thread (4 blocks of 256 fit its shared
+// memory at 256-cell tiles; up to 64 registers), else as k_tiled_step.
+template <int NT, int TC>
+constexpr int pipe_min_blocks() { return (TC == NT ? 1024 : 768) / NT; }
+
+template <int NT, int TC>
+__global__ void __launch_bounds__(NT, pipe_min_blocks<NT, TC>())
+    k_tiled_step_pipe(DevMesh<float> m, DevState<float> s, Num num, TileLayout L) {
+  using Real = float;
+  constexpr int NS = 2;
+  constexpr int CPT = TC / NT;
+  static_assert((TC & (TC - 1)) == 0 && NT <= TC && NT % 32 == 0 && TC % NT == 0, "tile shape");
+  __shared__ int s_nrec[NS];
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bars);
+  auto slot_set = [&](int k) {  // [3 TC][4]: face k of cell j at k TC + j
+    return reinterpret_cast<Real*>(smem + L.off_slots + (k & 1) * L.slot_bytes);
+  };
+
+  const Chunk ch = m.chunks[blockIdx.x];
+  const int t_first = ch.tile0, n_tiles = ch.ntiles, t_step = ch.stride;
+  const int cell_end = ch.cell_end;
+  Ctl* ctl = s.ctl + ch.scen;
+  const int tid = threadIdx.x;
+  const Real* __restrict__ U = nullptr;
+  Real* __restrict__ U1 = nullptr;
+  Real dt = Real(0);
+
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  uint32_t parity_bits = 0, pending = 0;  // thread 0: per stage
+  int64_t o_r0 = 0, o_r1 = 0;             // thread 0: next tile's record offsets
+  auto load_offsets = [&](int t) {
+    o_r0 = m.toff[t];
+    o_r1 = m.toff[t + 1];
+  };
+  auto issue_mesh = [&](int st) {
+    unsigned char* p = smem + st * L.stage;
+    const int64_t r0 = o_r0;
+    const uint32_t nrec = (uint32_t)(o_r1 - r0);
+    s_nrec[st] = (int)nrec;
+    fence_proxy_async();
+    mbar_expect_tx_only(&bar[st], nrec * 16u);
+    bulk_g2s(p + L.off_tS, m.trec + r0, nrec * 16, &bar[st]);
+    pending |= 1u << st;
+  };
+  auto issue_cells = [&](int st, int t) {
+    unsigned char* p = smem + st * L.stage;
+    const uint32_t cells = TC * 4 * (uint32_t)sizeof(Real);
+    mbar_expect_tx(&bar[st], cells);
+    bulk_g2s(p + L.off_cells, U + 4 * (int64_t)t * TC, cells, &bar[st]);
+  };
+  auto wait_stage = [&](int st) -> bool {
+    const bool ok = mbar_wait(&bar[st], (parity_bits >> st) & 1u, num.wait_rounds);
+    if (ok) {
+      parity_bits ^= 1u << st;
+      pending &= ~(1u << st);
+    }
+    return ok;
+  };
+  constexpr int W = NT / 32;
+  const int q_h = (tid & 31) * W + (tid >> 5);
+  int32_t h_q = 0;
+  auto load_halo = [&](int t) {
+    if (q_h < (int)L.halo_cap) h_q = __ldg(m.hpad + (int64_t)t * L.halo_cap + q_h);
+  };
+  auto gather_halo = [&](int st) {
+    Real* xc = reinterpret_cast<Real*>(smem + st * L.stage + L.off_cells) + 4 * TC;
+    if (q_h < (int)L.halo_cap) cp_async16(xc + 4 * q_h, U + 4 * (int64_t)h_q);
+  };
+
+  NoMass<Real> mass;
+  Real rate = Real(0), chk = Real(0);
+  int neg = 0, timeout = 0;
+  if (tid == 0 && n_tiles > 0) {
+    load_offsets(t_first);
+    issue_mesh(0);
+  }
+  if (n_tiles > 0) load_halo(t_first);
+  pdl_trigger();
+  pdl_wait();
+  if (ctl->done) {
+    if (tid == 0 && n_tiles > 0) {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar[0])) : "memory");
+      mbar_wait(&bar[0], 0u);
+    }
+    return;
+  }
+  {
+    const int cur = ctl->cur;
+    dt = Real(ctl->dt);
+    U = cur ? s.h[1] : s.h[0];
+    U1 = cur ? s.h[0] : s.h[1];
+  }
+  if (n_tiles > 0) {
+    if (tid == 0) {
+      issue_cells(0, t_first);
+      if (n_tiles > 1) load_offsets(t_first + t_step);
+    }
+    gather_halo(0);
+    if (n_tiles > 1) load_halo(t_first + t_step);
+    const bool ok = (tid == 0) ? wait_stage(0) : true;
+    cp_async_wait_all();
+    if (__syncthreads_or(!ok)) timeout = 1;
+  }
+  // The thread's cells of the tile whose faces were computed last: state
+  // and per-cell constants, used by the next iteration's cell updates.
+  V4<Real> cst[CPT];
+  Real c_area[CPT], c_irP[CPT], c_gn2[CPT];  // tile k-1's, used in iteration k
+  Real n_area[CPT], n_irP[CPT], n_gn2[CPT];  // tile k's, loaded at the start of iteration k
+  int prev_base = 0, prev_nc = 0;
+  for (int k = 0; !timeout && k <= n_tiles; ++k) {
+    const int st = k & 1;
+    const int tile = t_first + k * t_step;
+    const bool has_tile = k < n_tiles, has_next = k + 1 < n_tiles;
+    // Tile k+1: copies into the other stage (free since the barrier that
+    // ended iteration k-1) and its halo gather, from indices in registers.
+    if (has_next) {
+      if (tid == 0) {
+        issue_mesh(st ^ 1);
+        issue_cells(st ^ 1, tile + t_step);
+        if (k + 2 < n_tiles) load_offsets(tile + 2 * t_step);
+      }
+      gather_halo(st ^ 1);
+      if (k + 2 < n_tiles) load_halo(tile + 2 * t_step);
+    }
+    // tile k's per-cell constants (global loads, consumed next iteration)
+    if (has_tile) {
+      const int base = tile * TC;
+#pragma unroll
+      for (int cc = 0; cc < CPT; ++cc) {
+        const int j = tid + cc * NT;
+        n_area[cc] = m.area[base + j];
+        n_irP[cc] = m.irP[base + j];
+        n_gn2[cc] = s.gn2[base + j];
+      }
+    }
+    // cell updates of tile k-1 (its slots were completed by the last barrier)
+    if (k >= 1) {
+      const Real* slots = slot_set(k - 1);
+#pragma unroll
+      for (int cc = 0; cc < CPT; ++cc) {
+        const int j = tid + cc * NT;
+        if (j >= prev_nc) break;
+        const V4<Real> f0 = ld4(slots + 4 * j);
+        const V4<Real> f1 = ld4(slots + 4 * (TC + j));
+        const V4<Real> f2 = ld4(slots + 4 * (2 * TC + j));
+        Real R[3];
+        Real s1, e1, s2, e2;
+        two_sum(f0.x, f1.x, s1, e1);
+        two_sum(s1, f2.x, s2, e2);
+        R[0] = add_rn(s2, add_rn(e1, e2));
+        float2 p1, q1, p2, q2;
+        two_sum2(make_float2(f0.z, f0.w), make_float2(f1.z, f1.w), p1, q1);
+        two_sum2(p1, make_float2(f2.z, f2.w), p2, q2);
+        const float2 r = add2(p2, add2(q1, q2));
+        R[1] = r.x;
+        R[2] = r.y;
+        const V4<Real> c = cst[cc];
+        Real a1, b1, c1;
+        cell_finish<Real, true>(c.x, c.y, c.z, c_area[cc], c_irP[cc], c_gn2[cc], dt, R, num, a1, b1,
+                                c1, mass, rate, chk, neg);
+        st4(U1 + 4 * (int64_t)(prev_base + j), a1, b1, c1, c.w);
+      }
+    }
+    if (has_tile) {
+      const unsigned char* p = smem + st * L.stage;
+      const Real* xc = reinterpret_cast<const Real*>(p + L.off_cells);
+      const int32_t* rS = reinterpret_cast<const int32_t*>(p + L.off_tS);
+      Real* slots = slot_set(k);
+      const int base = tile * TC;
+      const int nrec = s_nrec[st];
+      // face records of tile k, the highest threads first
+      for (int r = NT - 1 - tid; r < nrec; r += NT) {
+        int32_t packed;
+        float fnx, fny, flen;
+        rec_f32(rS, r, packed, fnx, fny, flen);
+        const int a = packed >> 16;
+        const int b = (int)(int16_t)(packed & 0xffff);
+        float c0, cA1, cA2, cB1, cB2;
+        if (b == kSideWall) {
+          if (a == kSideWall) continue;  // padding record
+          const V4<Real> A = ld4(xc + 4 * ((-1 - a) & (TC - 1)));
+          face_flux_f32<true>(A, A, fnx, fny, flen, num, c0, cA1, cA2, cB1, cB2);
+          st4(slots + 4 * (-1 - a), c0, 0.0f, cA1, cA2);
+          continue;
+        }
+        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : a;
+        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : b;
+        const V4<Real> A = ld4(xc + 4 * ia);
+        const V4<Real> B = ld4(xc + 4 * ib);
+        face_flux_f32<false>(A, B, fnx, fny, flen, num, c0, cA1, cA2, cB1, cB2);
+        if (a < 0) st4(slots + 4 * (-1 - a), c0, 0.0f, cA1, cA2);
+        if (b < 0) st4(slots + 4 * (-1 - b), -c0, 0.0f, cB1, cB2);
+      }
+      // this tile's own cells and constants, for the next iteration
+#pragma unroll
+      for (int cc = 0; cc < CPT; ++cc) {
+        const int j = tid + cc * NT;
+        cst[cc] = ld4(xc + 4 * j);
+        c_area[cc] = n_area[cc];
+        c_irP[cc] = n_irP[cc];
+        c_gn2[cc] = n_gn2[cc];
+      }
+      prev_base = base;
+      prev_nc = min(TC, cell_end - base);
+    }
+    // tile k+1's copies and halo must have landed before its faces; tile
+    // k's slots must be complete before its cell updates
+    const bool ok = (tid == 0 && has_next) ? wait_stage(st ^ 1) : true;
+    cp_async_wait_all();
+    if (__syncthreads_or(!ok)) {
+      timeout = 1;
+      break;
+    }
+  }
   if (timeout && tid == 0) {
 #pragma unroll
     for (int i = 0; i < NS; ++i)

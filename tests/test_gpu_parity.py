@@ -27,7 +27,8 @@ KERNELS = [("tiled", "morton", 256), ("tiled", "morton", 128), ("tiled", "none",
 # tiled kernel shapes: (cells per tile, cells per thread, stages)
 # (tile, cells_per_thread, stages, halo_schedule)
 TILED_SHAPES = [(256, 2, 3, 0), (256, 1, 2, 0), (256, 1, 3, 0), (128, 1, 2, 0), (512, 2, 2, 0),
-                (64, 1, 3, 0), (256, 2, 2, 1), (64, 1, 3, 1)]
+                (64, 1, 3, 0), (256, 2, 2, 1), (64, 1, 3, 1), (256, 1, 2, 2), (512, 2, 2, 2),
+                (64, 1, 2, 2)]
 
 
 def small_cases():
@@ -330,3 +331,27 @@ def test_meshes_of_different_layouts_in_any_order():
         for x, y in zip(a.fields(), c.fields()):
             assert np.array_equal(x, y)
         assert a.info()["err"] == 0 and c.info()["err"] == 0
+
+
+@pytest.mark.parametrize("tile,cpt", [(256, 1), (512, 2), (128, 2), (32, 1), (512, 1)])
+def test_pipelined_fp32_step_equals_the_two_barrier_step_bitwise(tile, cpt):
+    """halo_schedule 2 (one block barrier per tile: the cell updates of a
+    tile overlap the face loop of the next) computes every face and cell with
+    the same arithmetic as the default kernel: the same bits, for any
+    number of tiles per block and a ragged last tile."""
+    ensure_built()
+    for case in (inputs.humps_case(nx=71, ny=29, lx=2_000.0, ly=1_000.0, seed=61),
+                 inputs.random_flow_case(nx=37, ny=23, seed=41)):
+        out = []
+        for sched in (0, 2):
+            # 512-cell tiles with one cell per thread exist only pipelined: the
+            # two-barrier reference runs them with two cells per thread
+            c = 2 if (sched == 0 and tile // cpt == 512) else cpt
+            mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f32", kernel="tiled", tile=tile,
+                            cells_per_thread=c, halo_schedule=sched)
+            st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+            st.run(37)
+            out.append(st.fields() + (st.t,))
+            assert st.info()["err"] == 0
+        for x, y in zip(out[0], out[1]):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
