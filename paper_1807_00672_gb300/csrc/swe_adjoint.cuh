@@ -57,184 +57,22 @@ __device__ __forceinline__ void cell_vjp(Real h1, Real q1x, Real q1y, Real lh, R
   }
 }
 
-// Vector-Jacobian product of one face. Inputs: both sides' cell states
-// (h, hu, hv, z) as the forward step read them, the wall flag, the geometry,
-// and rho = dL/dR of side A (the face adds c_A to R_A) and side B (the face
-// subtracts c_B from R_B). Outputs gA, gB = dL/d(h, hu, hv, z) of each side
-// through this face (gB = 0 for a wall: the mirror folds into A).
-template <typename Real>
-__device__ __forceinline__ void face_vjp(Real hA, Real huA, Real hvA, Real zA, Real hB, Real huB,
-                                         Real hvB, Real zB, bool wall, Real nx, Real ny, Real len,
-                                         const Num& num, Real rA0, Real rA1, Real rA2, Real rB0,
-                                         Real rB1, Real rB2, Real gA[4], Real gB[4]) {
-  using O = Ops<Real>;
-  const Real zero = Real(0), half = Real(0.5);
-  const Real g = Real(num.g);
-  // ---- forward, keeping what the reverse sweep needs
-  Real uA, vA, uB, vB;
-  velocity(hA, huA, hvA, num, uA, vA);
-  const bool wetcA = O::wet(hA, num);
-  const Real unA = uA * nx + vA * ny;
-  const Real utA = vA * nx - uA * ny;
-  Real unB, utB;
-  bool wetcB = false;
-  if (wall) {
-    hB = hA; zB = zA; unB = -unA; utB = utA;
-  } else {
-    velocity(hB, huB, hvB, num, uB, vB);
-    wetcB = O::wet(hB, num);
-    unB = uB * nx + vB * ny;
-    utB = vB * nx - uB * ny;
-  }
-  const bool zsA = zA >= zB;  // max(zA, zB) taken from A on a tie
-  const Real zs = zsA ? zA : zB;
-  Real hAs = fmax(zero, hA + zA - zs);
-  Real hBs = fmax(zero, hB + zB - zs);
-  const bool actA = O::wet(hAs, num), actB = O::wet(hBs, num);
-  if (!actA) hAs = zero;
-  if (!actB) hBs = zero;
-  // HLLC (same case analysis as the forward)
-  const bool wetA = hAs > zero, wetB = hBs > zero;
-  const Real cA = O::sqrt_(g * hAs);
-  const Real cB = O::sqrt_(g * hBs);
-  const Real us = (unA + unB) * half + cA - cB;
-  const Real cs = (cA + cB) * half + (unA - unB) * Real(0.25);
-  const bool firstA = (unA - cA) <= (us - cs);
-  const bool firstB = (unB + cB) >= (us + cs);
-  const Real SA = wetA ? (wetB ? (firstA ? unA - cA : us - cs) : unA - cA) : unB - Real(2) * cB;
-  const Real SB = wetA ? (wetB ? (firstB ? unB + cB : us + cs) : unA + Real(2) * cA) : unB + cB;
-  const Real qA = hAs * unA, qB = hBs * unB;
-  const Real FA1 = qA * unA + half * g * hAs * hAs;
-  const Real FB1 = qB * unB + half * g * hBs * hBs;
-  const Real inv = O::div(Real(1), SB - SA);
-  const Real N0 = SB * qA - SA * qB + SA * SB * (hBs - hAs);
-  const Real N1 = SB * FA1 - SA * FB1 + SA * SB * (qB - qA);
-  const Real H0 = N0 * inv;
-  const Real numS = SA * hBs * (unB - SB) - SB * hAs * (unA - SA);
-  const bool selA = numS <= zero;  // contact speed >= 0: transverse momentum from A
-  const bool left = SA >= zero, right = SB <= zero, dry = !wetA && !wetB;
-
-  // ---- reverse sweep
-  // residual contributions: A gets +l (F0, Fx + PA nx, Fy + PA ny), B gets -l (F0, Fx + PB nx, ...)
-  const Real bF0 = wall ? zero : len * (rA0 - rB0);
-  const Real bFx = len * (rA1 - rB1);
-  const Real bFy = len * (rA2 - rB2);
-  const Real bPA = len * (rA1 * nx + rA2 * ny);
-  const Real bPB = wall ? zero : -len * (rB1 * nx + rB2 * ny);
-  const Real bF1 = bFx * nx + bFy * ny;
-  const Real bF2 = wall ? zero : bFy * nx - bFx * ny;
-  Real bhAs = -g * hAs * bPA, bhBs = -g * hBs * bPB;
-  Real bhA = g * hA * bPA, bhB = g * hB * bPB;
-  Real bunA = zero, butA = zero, bunB = zero, butB = zero;
-  if (!dry) {
-    if (left) {
-      const Real bqA = bF0 + bF1 * unA + bF2 * utA;
-      bunA += bF1 * qA + bqA * hAs;
-      butA += bF2 * qA;
-      bhAs += bF1 * g * hAs + bqA * unA;
-    } else if (right) {
-      const Real bqB = bF0 + bF1 * unB + bF2 * utB;
-      bunB += bF1 * qB + bqB * hBs;
-      butB += bF2 * qB;
-      bhBs += bF1 * g * hBs + bqB * unB;
-    } else {
-      const Real ut = selA ? utA : utB;
-      if (selA) butA += bF2 * H0; else butB += bF2 * H0;
-      const Real bH0 = bF0 + bF2 * ut;
-      const Real bN0 = bH0 * inv, bN1 = bF1 * inv;
-      const Real binv = bH0 * N0 + bF1 * N1;
-      const Real bD = -binv * inv * inv;  // D = SB - SA
-      Real bSB = bD, bSA = -bD;
-      const Real dh = hBs - hAs, dq = qB - qA, SS = SA * SB;
-      bSB += bN0 * (qA + SA * dh) + bN1 * (FA1 + SA * dq);
-      bSA += bN0 * (SB * dh - qB) + bN1 * (SB * dq - FB1);
-      Real bqA = bN0 * SB - bN1 * SS;
-      Real bqB = bN1 * SS - bN0 * SA;
-      bhBs += bN0 * SS;
-      bhAs -= bN0 * SS;
-      const Real bFA1 = bN1 * SB, bFB1 = -bN1 * SA;
-      bqA += bFA1 * unA;
-      bunA += bFA1 * qA;
-      bhAs += bFA1 * g * hAs;
-      bqB += bFB1 * unB;
-      bunB += bFB1 * qB;
-      bhBs += bFB1 * g * hBs;
-      bhAs += bqA * unA;
-      bunA += bqA * hAs;
-      bhBs += bqB * unB;
-      bunB += bqB * hBs;
-      Real bcA = zero, bcB = zero;
-      if (wetA && wetB) {
-        Real bus = zero, bcs = zero;
-        if (firstA) { bunA += bSA; bcA -= bSA; } else { bus += bSA; bcs -= bSA; }
-        if (firstB) { bunB += bSB; bcB += bSB; } else { bus += bSB; bcs += bSB; }
-        bunA += half * bus + Real(0.25) * bcs;
-        bunB += half * bus - Real(0.25) * bcs;
-        bcA += bus + half * bcs;
-        bcB += half * bcs - bus;
-      } else if (wetA) {  // B dry: SA = unA - cA, SB = unA + 2 cA
-        bunA += bSA + bSB;
-        bcA += Real(2) * bSB - bSA;
-      } else {            // A dry: SA = unB - 2 cB, SB = unB + cB
-        bunB += bSA + bSB;
-        bcB += bSB - Real(2) * bSA;
-      }
-      if (wetA) bhAs += bcA * O::div(half * g, cA);
-      if (wetB) bhBs += bcB * O::div(half * g, cB);
-    }
-  }
-  // reconstruction h* = h + z - max(zA, zB) where it stays wet
-  Real bzA = zero, bzB = zero, bzs = zero;
-  if (actA) { bhA += bhAs; bzA += bhAs; bzs -= bhAs; }
-  if (actB) { bhB += bhBs; bzB += bhBs; bzs -= bhBs; }
-  if (zsA) bzA += bzs; else bzB += bzs;
-  if (wall) {  // B mirrors A: hB = hA, zB = zA, unB = -unA, utB = utA
-    bhA += bhB;
-    bzA += bzB;
-    bunA -= bunB;
-    butA += butB;
-  }
-  // face frame -> x, y velocities -> conserved variables
-  const Real buA = bunA * nx - butA * ny;
-  const Real bvA = bunA * ny + butA * nx;
-  gA[0] = bhA;
-  gA[1] = zero;
-  gA[2] = zero;
-  gA[3] = bzA;
-  if (wetcA) {
-    const Real r = O::div(Real(1), hA);
-    gA[1] = buA * r;
-    gA[2] = bvA * r;
-    gA[0] -= (buA * uA + bvA * vA) * r;
-  }
-  gB[0] = zero; gB[1] = zero; gB[2] = zero; gB[3] = zero;
-  if (!wall) {
-    const Real buB = bunB * nx - butB * ny;
-    const Real bvB = bunB * ny + butB * nx;
-    gB[0] = bhB;
-    gB[3] = bzB;
-    if (wetcB) {
-      const Real r = O::div(Real(1), hB);
-      gB[1] = buB * r;
-      gB[2] = bvB * r;
-      gB[0] -= (buB * uB + bvB * vB) * r;
-    }
-  }
-}
-
-// Vector-Jacobian product of one face in the clamped form of the flux that
-// the FP32 step computes (face_flux_f32): one HLL formula with the clamped
-// speeds S- = min(S_A, 0), S+ = max(S_B, 0), the dry side's normal velocity
-// replaced by un_B - 2 c_B (or un_A + 2 c_A) in the wave-speed estimates,
-// the transverse momentum upwinded by the sign of F0. It is the same
-// function of the inputs as the case analysis of face_vjp (the clamped
-// speeds reproduce the supersonic cases: with S_A >= 0, S- = 0 and F = F_A,
-// whose derivative with respect to S_A is 0, as face_vjp takes it), so the
-// derivatives agree away from ties; it has no case branches. Ties follow the
-// same conventions: max(zA, zB) and the speed estimates take the first
-// argument, S_A = 0 counts as S_A >= 0 and S_B = 0 as S_B <= 0. A and B are
-// the sides' cells (h, hu, hv, z) as the forward step read them; for a wall
-// B is ignored (the mirror of A folds into gA).
+// Vector-Jacobian product of one face, with both sides' contributions:
+// inputs the sides' cells (h, hu, hv, z) as the forward step read them, the
+// geometry, and rho = dL/dR of side A (the face adds c_A to R_A) and side B
+// (the face subtracts c_B from R_B); outputs gA, gB = dL/d(h, hu, hv, z) of
+// each side through this face. The face is the clamped form of the flux the
+// tiled steps compute (face_flux_f32, face_flux_f64): one HLL formula with
+// the clamped speeds S- = min(S_A, 0), S+ = max(S_B, 0), the dry side's
+// normal velocity replaced by un_B - 2 c_B (or un_A + 2 c_A) in the
+// wave-speed estimates, the transverse momentum upwinded by the sign of F0.
+// It is the same function of the inputs as the HLLC case analysis (the
+// clamped speeds reproduce the supersonic cases: with S_A >= 0, S- = 0 and
+// F = F_A, whose derivative with respect to S_A is 0), so the derivatives
+// agree with the case analysis's away from ties; it has no case branches.
+// Ties follow fixed conventions: max(zA, zB) and the speed estimates take
+// the first argument, S_A = 0 counts as S_A >= 0 and S_B = 0 as S_B <= 0.
+// For a wall B is ignored (the mirror of A folds into gA, gB = 0).
 template <typename Real, bool Wall>
 __device__ __forceinline__ void face_vjp_clamped(const V4<Real>& A, const V4<Real>& B, Real nx,
                                                  Real ny, Real len, const Num& num, Real rA0,
@@ -440,17 +278,11 @@ inline AdjLayout make_adj_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc, u
 //   (C) each cell: dL/dU^n = mu + its three slots in face order, the z parts
 //       added to the running dL/dz, and its dL/d(g n^2) accumulated.
 // (A) of the next tile runs right after (C), so two block barriers per tile.
-#ifndef SWE_ADJ_CLAMPED_F64
-#define SWE_ADJ_CLAMPED_F64 0
-#endif
 template <typename Real, int NT, int NS, int CPT>
 __global__ void __launch_bounds__(NT)
     k_tiled_adjoint(DevMesh<Real> m, AdjArgs<Real> A, Num num, AdjLayout L) {
   using O = Ops<Real>;
   constexpr int TC = NT * CPT;
-  // FP32 differentiates the clamped form its step computes; FP64 the case
-  // analysis of its step (face_vjp)
-  constexpr bool kClampedVjp = sizeof(Real) == 4 || SWE_ADJ_CLAMPED_F64;
   __shared__ int s_nrec[NS], s_nh[NS];
   extern __shared__ __align__(128) unsigned char smem[];
   Real* rho = reinterpret_cast<Real*>(smem + L.off_rho);      // [ext][4]
@@ -649,42 +481,26 @@ __global__ void __launch_bounds__(NT)
       const int a = packed >> 16;
       if (a == kSideWall) continue;  // padding record
       const int b = (int)(int16_t)(packed & 0xffff);
-      if constexpr (kClampedVjp) {
-        Real gA[4], gB[4];
-        if (b == kSideWall) {  // wall: side A is the tile cell owning the edge
-          const int ia = (-1 - a) & (TC - 1);
-          const V4<Real> UA = ld4(sun + 4 * ia);
-          const V4<Real> RA = ld4(rho + 4 * ia);
-          face_vjp_clamped<Real, true>(UA, UA, nx, ny, len, num, RA.x, RA.y, RA.z, Real(0), Real(0),
-                                       Real(0), gA, gB);
-          st4(slots + 4 * (-1 - a), gA[0], gA[1], gA[2], gA[3]);
-          continue;
-        }
-        const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : a;
-        const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : b;
+      Real gA[4], gB[4];
+      if (b == kSideWall) {  // wall: side A is the tile cell owning the edge
+        const int ia = (-1 - a) & (TC - 1);
         const V4<Real> UA = ld4(sun + 4 * ia);
-        const V4<Real> UB = ld4(sun + 4 * ib);
         const V4<Real> RA = ld4(rho + 4 * ia);
-        const V4<Real> RB = ld4(rho + 4 * ib);
-        face_vjp_clamped<Real, false>(UA, UB, nx, ny, len, num, RA.x, RA.y, RA.z, RB.x, RB.y, RB.z,
-                                      gA, gB);
-        if (a < 0) st4(slots + 4 * (-1 - a), gA[0], gA[1], gA[2], gA[3]);
-        if (b < 0) st4(slots + 4 * (-1 - b), gB[0], gB[1], gB[2], gB[3]);
+        face_vjp_clamped<Real, true>(UA, UA, nx, ny, len, num, RA.x, RA.y, RA.z, Real(0), Real(0),
+                                     Real(0), gA, gB);
+        st4(slots + 4 * (-1 - a), gA[0], gA[1], gA[2], gA[3]);
         continue;
       }
-      const bool wall = (b == kSideWall);
       const int ia = a < 0 ? ((-1 - a) & (TC - 1)) : a;
-      const int ib = wall ? ia : (b < 0 ? ((-1 - b) & (TC - 1)) : b);
+      const int ib = b < 0 ? ((-1 - b) & (TC - 1)) : b;
       const V4<Real> UA = ld4(sun + 4 * ia);
       const V4<Real> UB = ld4(sun + 4 * ib);
       const V4<Real> RA = ld4(rho + 4 * ia);
       const V4<Real> RB = ld4(rho + 4 * ib);
-      Real gA[4], gB[4];
-      const Real zero = Real(0);
-      face_vjp<Real>(UA.x, UA.y, UA.z, UA.w, UB.x, UB.y, UB.z, UB.w, wall, nx, ny, len, num, RA.x,
-                     RA.y, RA.z, wall ? zero : RB.x, wall ? zero : RB.y, wall ? zero : RB.z, gA, gB);
+      face_vjp_clamped<Real, false>(UA, UB, nx, ny, len, num, RA.x, RA.y, RA.z, RB.x, RB.y, RB.z,
+                                    gA, gB);
       if (a < 0) st4(slots + 4 * (-1 - a), gA[0], gA[1], gA[2], gA[3]);
-      if (b < 0 && !wall) st4(slots + 4 * (-1 - b), gB[0], gB[1], gB[2], gB[3]);
+      if (b < 0) st4(slots + 4 * (-1 - b), gB[0], gB[1], gB[2], gB[3]);
     }
     const bool ok = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
     if (__syncthreads_or(!ok)) {
