@@ -467,12 +467,20 @@ def fp64_leg(case, args, stream, ws):
     # (ncu count of the kernel, profiles/fp64_ops.txt) against the measured
     # FP64 fused multiply-add rate (and the nominal 1.25 TFLOP/s).
     fpc = profiled_fp64_flops(args)
+    ipc = profiled_fp64_flops(args, field=3)
     rate = swe.fp64_fma_rate(ctypes_stream(stream))
     alu = {"bound": "alu", "unit": "TFLOP/s", "peak": rate, "peak_source": "measured DFMA rate",
            "peak_nominal": 1.25, "flops_per_cell": fpc}
     if fpc is not None:
         alu["achieved"] = fpc * mesh.T / (ms * 1e-3) / 1e12
         alu["frac"] = alu["achieved"] / rate
+    if ipc is not None:
+        # The FP64 pipe issues one DADD, DMUL or DFMA per slot; its slot rate
+        # is the measured DFMA rate / 2. DADD and DMUL count one flop for a
+        # whole slot, so for a pipe-bound kernel the instruction fraction is
+        # the measure of how busy the FP64 units are kept.
+        alu["fp64_inst_per_cell"] = ipc
+        alu["pipe_frac"] = ipc * mesh.T / (ms * 1e-3) / (rate * 1e12 / 2.0)
     out["alu"] = alu
     return out
 
@@ -818,7 +826,8 @@ def summary(out):
          "e2e": r(out["e2e"]["value"])}
     if "fp64" in out:
         s["fp64_10m"] = {"value": r(out["fp64"]["value"]), "hbm_frac": r(out["fp64"]["hbm_frac"]),
-                         "alu_frac": r(out["fp64"]["alu"].get("frac"))}
+                         "alu_frac": r(out["fp64"]["alu"].get("frac")),
+                         "fp64_pipe_frac": r(out["fp64"]["alu"].get("pipe_frac"))}
     if "humps_1m" in out:
         s["humps_1m"] = {p: {"value": r(out["humps_1m"][p]["value"]),
                              "hbm_frac": r(out["humps_1m"][p]["hbm_frac"])} for p in ("f32", "f64")}
@@ -872,9 +881,10 @@ def profiled_traffic(args):
     return None
 
 
-def profiled_fp64_flops(args):
-    """FP64 flops per cell of the FP64 step from the committed ncu count, if it
-    was taken on the kernel source as it is now and on the default shape."""
+def profiled_fp64_flops(args, field: int = 2):
+    """FP64 flops (field 2) or FP64 pipe instructions (field 3) per cell of the
+    FP64 step from the committed ncu count, if it was taken on the kernel
+    source as it is now and on the default shape."""
     path = os.path.join(ROOT, "profiles", "fp64_ops.txt")
     if not os.path.exists(path) or args.kernel == "edge" or args.tile not in (0, 256):
         return None
@@ -882,8 +892,11 @@ def profiled_fp64_flops(args):
     with open(path) as f:
         for line in f:
             parts = line.split()
-            if len(parts) >= 4 and parts[0] == args.workload and parts[1] == digest:
-                return float(parts[2])
+            if len(parts) >= 5 and parts[0] == args.workload and parts[1] == digest:
+                try:
+                    return float(parts[field])
+                except ValueError:
+                    return None
     return None
 
 

@@ -95,3 +95,21 @@ def test_sub_domains_whose_own_cells_are_all_dry():
         assert np.array_equal(a, b)
     assert run.mass() == pytest.approx(ref.mass, rel=1e-13)
     run.close()
+
+
+def test_many_small_sub_domains_on_one_gpu():
+    """132 cells in 11 sub-domains of 12 cells (most cells of a part have a
+    ghost neighbour): bitwise equal to the whole mesh, FP64 and FP32."""
+    pytest.importorskip("torch")
+    from paper_1807_00672_gb300.partition import LocalRun
+    ensure_built()
+    case = inputs.random_flow_case(nx=11, ny=6, lx=110.0, ly=60.0, seed=11)
+    for prec in ("f64", "f32"):
+        whole = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=prec)
+        ref = swe.State(whole, *fields(case))
+        run = LocalRun(case.mesh.xy, case.mesh.tri, fields(case), 11, precision=prec)
+        ref.run(30)
+        run.run(30)
+        for a, b in zip(run.fields(), ref.fields()):
+            assert np.array_equal(a, b), prec
+        run.close()

@@ -176,3 +176,20 @@ def test_two_gloo_ranks_equal_the_whole_mesh_bitwise():
         assert np.array_equal(hv, ref.hv[ids])
         assert m == pytest.approx(ref.mass(), rel=1e-13)
     assert np.all(seen == 1)
+
+
+def test_as_many_parts_as_cells_and_one_part():
+    """Degenerate cuts: one part (no ghost, local = whole mesh) and one cell
+    per part (every neighbour a ghost); decomposed oracle runs still equal
+    the whole mesh bitwise."""
+    case = inputs.random_flow_case(nx=3, ny=2, lx=30.0, ly=20.0, seed=3)   # 12 cells
+    T = case.mesh.n_tris
+    one = swe.Partition(case.mesh.xy, case.mesh.tri, 1).local(0)
+    assert one["ghost"].sum() == 0 and np.array_equal(one["cells"], np.arange(T))
+    ref = oracle.state_from_case(case)
+    dts = ref.run(15)
+    got, subs = _local_decomposed_run(case, T, 15)
+    assert all((~s.ghost).sum() == 1 for s in subs)
+    assert np.array_equal(np.array(subs[0].dts), dts)
+    for a, b in zip(got, (ref.h, ref.hu, ref.hv)):
+        assert np.array_equal(a, b)
