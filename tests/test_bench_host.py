@@ -34,7 +34,7 @@ def test_counter_lookups_follow_the_key_and_the_shape(tmp_path, monkeypatch):
     prof.mkdir()
     (prof / "traffic.txt").write_text(f"# comment\nsinusoid_10m {digest} 686274816 ncu ...\n"
                                       "sinusoid_10m 0000000000000000 1 ncu ...\n")
-    (prof / "fp64_ops.txt").write_text(f"sinusoid_10m {digest} 377.55 ncu ...\n")
+    (prof / "fp64_ops.txt").write_text(f"sinusoid_10m {digest} 377.55 254.90 ncu ...\n")
     args = types.SimpleNamespace(precision="f32", kernel="auto", tile=0, cpt=0, stages=0,
                                  workload="sinusoid_10m")
     assert bench.profiled_traffic(args) == 686274816.0
@@ -42,6 +42,7 @@ def test_counter_lookups_follow_the_key_and_the_shape(tmp_path, monkeypatch):
     assert bench.profiled_traffic(args) is None
     args.precision, args.tile = "f64", 0
     assert bench.profiled_fp64_flops(args) == 377.55
+    assert bench.profiled_fp64_flops(args, field=3) == 254.90
     args.workload = "calibration_1m"
     assert bench.profiled_fp64_flops(args) is None
     # a code change lapses every line
