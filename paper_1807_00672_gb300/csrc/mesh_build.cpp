@@ -35,6 +35,30 @@ inline uint64_t spread_bits(uint64_t x) {
 
 }  // namespace
 
+std::vector<int32_t> morton_order(const double* xy, int64_t V, const int32_t* tri, int64_t T) {
+  double x0 = xy[0], x1 = xy[0], y0 = xy[1], y1 = xy[1];
+  for (int64_t v = 0; v < V; ++v) {
+    x0 = std::min(x0, xy[2 * v]); x1 = std::max(x1, xy[2 * v]);
+    y0 = std::min(y0, xy[2 * v + 1]); y1 = std::max(y1, xy[2 * v + 1]);
+  }
+  double span = std::max(x1 - x0, y1 - y0);
+  if (!(span > 0.0)) span = 1.0;
+  const double q = 4194303.0;  // 22 bits per axis
+  std::vector<uint64_t> key(T);
+  for (int64_t i = 0; i < T; ++i) {
+    int32_t a = tri[3 * i], b = tri[3 * i + 1], c = tri[3 * i + 2];
+    double cx = (xy[2 * a] + xy[2 * b] + xy[2 * c]) / 3.0;
+    double cy = (xy[2 * a + 1] + xy[2 * b + 1] + xy[2 * c + 1]) / 3.0;
+    uint64_t ix = (uint64_t)std::min(q, std::max(0.0, (cx - x0) / span * q));
+    uint64_t iy = (uint64_t)std::min(q, std::max(0.0, (cy - y0) / span * q));
+    key[i] = spread_bits(ix) | (spread_bits(iy) << 1);
+  }
+  std::vector<int32_t> order(T);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t p, int32_t r) { return key[p] < key[r]; });
+  return order;
+}
+
 int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t T, int order,
                     int32_t tile, bool with_edges, HostMesh& m) {
   if (!xy || !tri_in || V <= 0 || T <= 0) return T == 0 ? -2 : -1;
@@ -145,25 +169,7 @@ int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t 
   m.perm.resize(T);
   std::iota(m.perm.begin(), m.perm.end(), 0);
   if (order == 1) {
-    double x0 = xy[0], x1 = xy[0], y0 = xy[1], y1 = xy[1];
-    for (int64_t v = 0; v < V; ++v) {
-      x0 = std::min(x0, xy[2 * v]); x1 = std::max(x1, xy[2 * v]);
-      y0 = std::min(y0, xy[2 * v + 1]); y1 = std::max(y1, xy[2 * v + 1]);
-    }
-    double span = std::max(x1 - x0, y1 - y0);
-    if (!(span > 0.0)) span = 1.0;
-    const double q = 4194303.0;  // 22 bits per axis
-    std::vector<uint64_t> key(T);
-    for (int64_t i = 0; i < T; ++i) {
-      int32_t a = tri[3 * i], b = tri[3 * i + 1], c = tri[3 * i + 2];
-      double cx = (xy[2 * a] + xy[2 * b] + xy[2 * c]) / 3.0;
-      double cy = (xy[2 * a + 1] + xy[2 * b + 1] + xy[2 * c + 1]) / 3.0;
-      uint64_t ix = (uint64_t)std::min(q, std::max(0.0, (cx - x0) / span * q));
-      uint64_t iy = (uint64_t)std::min(q, std::max(0.0, (cy - y0) / span * q));
-      key[i] = spread_bits(ix) | (spread_bits(iy) << 1);
-    }
-    std::stable_sort(m.perm.begin(), m.perm.end(),
-                     [&](int32_t p, int32_t r) { return key[p] < key[r]; });
+    m.perm = morton_order(xy, V, tri.data(), T);
   } else if (order != 0) {
     return -1;
   }

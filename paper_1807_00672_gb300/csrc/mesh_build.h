@@ -41,6 +41,11 @@ struct HostMesh {
   int64_t null_records = 0;
 };
 
+// Cells ordered by the Z-order (Morton) code of their centroids, 22 bits per
+// axis over the nodes' bounding square; ties keep the caller order. Node ids
+// must be valid.
+std::vector<int32_t> morton_order(const double* xy, int64_t V, const int32_t* tri, int64_t T);
+
 // Returns 0 or a negative status: -1 bad arguments, -2 invalid mesh.
 // order: 0 = caller order, 1 = Morton order of centroids.
 // tile > 0 also builds the tiled layout; with_edges builds the two-launch one.

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/swe.h"
+#include "mesh_build.h"
 
 struct swe_partition {
   int32_t nparts = 0;
@@ -37,16 +38,6 @@ struct swe_partition {
 };
 
 namespace {
-
-inline uint64_t spread(uint64_t x) {
-  x &= 0xffffffffull;
-  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
-  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
-  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
-  x = (x | (x << 2)) & 0x3333333333333333ull;
-  x = (x | (x << 1)) & 0x5555555555555555ull;
-  return x;
-}
 
 // Local index of global cell c in a part (its cells are ascending), or -1.
 int64_t local_index(const swe_partition::Part& p, int32_t c) {
@@ -101,27 +92,9 @@ swe_status swe_partition_create(const double* xy, int64_t n_nodes, const int32_t
     j = r;
   }
 
-  // Morton order of the centroids, split into contiguous ranges.
-  double x0 = xy[0], x1 = xy[0], y0 = xy[1], y1 = xy[1];
-  for (int64_t v = 0; v < n_nodes; ++v) {
-    x0 = std::min(x0, xy[2 * v]); x1 = std::max(x1, xy[2 * v]);
-    y0 = std::min(y0, xy[2 * v + 1]); y1 = std::max(y1, xy[2 * v + 1]);
-  }
-  double span = std::max(x1 - x0, y1 - y0);
-  if (!(span > 0.0)) span = 1.0;
-  const double q = 4194303.0;  // 22 bits per axis
-  std::vector<uint64_t> key(T);
-  for (int64_t i = 0; i < T; ++i) {
-    const int32_t a = tri[3 * i], b = tri[3 * i + 1], c = tri[3 * i + 2];
-    const double cx = (xy[2 * a] + xy[2 * b] + xy[2 * c]) / 3.0;
-    const double cy = (xy[2 * a + 1] + xy[2 * b + 1] + xy[2 * c + 1]) / 3.0;
-    const uint64_t ix = (uint64_t)std::min(q, std::max(0.0, (cx - x0) / span * q));
-    const uint64_t iy = (uint64_t)std::min(q, std::max(0.0, (cy - y0) / span * q));
-    key[i] = spread(ix) | (spread(iy) << 1);
-  }
-  std::vector<int32_t> order(T);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int32_t p, int32_t r) { return key[p] < key[r]; });
+  // Morton order of the centroids (as the library's cell renumbering),
+  // split into contiguous ranges.
+  const std::vector<int32_t> order = swe::morton_order(xy, n_nodes, tri, T);
 
   swe_partition* P = new swe_partition();
   P->nparts = n_parts;
