@@ -377,7 +377,11 @@ def main():
 
     # The adjoint leg runs first among the extras: its backward/forward
     # ratio compares two timings of the same run, taken before the long
-    # FP64 and ensemble legs.
+    # FP64 and ensemble legs. The extras are single-GPU measurements: with
+    # several ranks (replicas) they are skipped, so the other GPUs are not
+    # held while rank 0 runs them.
+    if ws > 1:
+        args.no_extras = True
     errors = {}
     if rank == 0 and not args.no_extras and not args.no_adjoint:
         out["adjoint"] = adjoint_leg(args, stream, errors)
