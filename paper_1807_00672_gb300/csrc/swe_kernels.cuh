@@ -8,11 +8,12 @@
 //
 // Determinism: every face contribution is written to its own slot and each
 // cell sums its three faces in a fixed order; the grid-wide CFL rate is an
-// integer max on non-negative IEEE bit patterns; the mass integral is a
-// per-block sum finished by the last block in block order. No float atomics.
+// integer max on non-negative IEEE bit patterns; the mass integral is a set
+// of per-block sums added up in a fixed order (k_mass_sum). No float atomics.
 //
-// Precision. The FP64 path uses IEEE division and square root throughout.
-// The FP32 path uses the hardware's approximate reciprocal and reciprocal
+// Precision. The FP64 path uses IEEE square roots, and reciprocals,
+// quotients and h^{-1/3} by Newton-Raphson iteration to within a few ulps
+// (rcp_nr, icbrt_nr). The FP32 path uses the hardware's approximate reciprocal and reciprocal
 // square root and exp2/log2 for h^{-7/3}; its face sums and Euler update are
 // compensated (TwoSum with exact FMA products); its dry-depth tests decide
 // exactly as an FP64 comparison of the same value would (see Num::h_eps_f32);
