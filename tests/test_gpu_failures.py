@@ -63,3 +63,28 @@ def test_gradient_recording_reports_timeout():
     with pytest.raises(swe.SweError) as ei:
         swe.Tape(st, 5, 2, [0, 3])
     assert ei.value.status == swe.SWE_ETIMEOUT
+
+
+@pytest.mark.parametrize("kernel", ["tiled", "edge"])
+def test_negative_input_depths_are_clipped_and_counted(kernel):
+    """A negative depth injected into the initial state is not a fault: the
+    first step clips it at 0 and counts it (swe_state_info), as the oracle
+    does; the state then matches the oracle's to 1e-11 and stays >= 0."""
+    ensure_built()
+    case = inputs.random_flow_case(nx=37, ny=23, seed=41)
+    # a dry disc (no inflow within 10 steps) whose inner cells hold -1 cm
+    c = inputs.centroids(case.mesh)
+    r = np.hypot(c[:, 0] - 60.0, c[:, 1] - 40.0)
+    for f in (case.h, case.hu, case.hv):
+        f[r < 40.0] = 0.0
+    case.h[r < 15.0] = -0.01
+    ref, _ = oracle_run(case, 10)
+    assert ref.neg == int((case.h < 0).sum()) > 0
+    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f64", kernel=kernel)
+    st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+    st.run(10)
+    info = st.info()
+    assert info["neg"] == ref.neg and info["err"] == 0
+    errs, (h, _, _) = field_errors(st, ref)
+    assert max(errs.values()) <= 1e-11, errs
+    assert np.all(h >= 0.0)
