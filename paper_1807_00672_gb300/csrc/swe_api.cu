@@ -268,9 +268,10 @@ void set_edge_grids(swe_mesh* m) {
   m->grid_cfl = grid_for(m->T, 256, m->sms * occ_cfl);
 }
 
-void launch_one_step(const swe_state* s, cudaStream_t st) {
-  if (s->mesh->prm.precision == SWE_F64) launch_forward(s->mesh, dev_state<double>(s), st);
-  else launch_forward(s->mesh, dev_state<float>(s), st);
+void launch_one_step(swe_state* s, cudaStream_t st) {
+  if (s->mesh->prm.precision == SWE_F64) launch_forward(s->mesh, dev_state<double>(s), st, s->walk_back);
+  else launch_forward(s->mesh, dev_state<float>(s), st, s->walk_back);
+  s->walk_back = !s->walk_back;
 }
 
 // CFL step (kind swe::kCflOnly) or mass only (swe::kMassOnly, tiled
@@ -642,6 +643,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     }
     L.add(4 * H);
     L.add(sizeof(swe::Chunk) * C);
+    L.add(sizeof(swe::Chunk) * C);  // the same chunks walked backwards
     if (m->layout.hreg) L.add(4 * tiles * (int64_t)m->layout.halo_cap);
   }
   if (cudaMalloc((void**)&m->arena.base, L.total) != cudaSuccess) {
@@ -678,6 +680,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     }
     m->hidx = (int32_t*)m->arena.take(4 * H);
     m->chunks = (swe::Chunk*)m->arena.take(sizeof(swe::Chunk) * C);
+    m->chunks_back = (swe::Chunk*)m->arena.take(sizeof(swe::Chunk) * C);
     if (m->layout.hreg)
       m->hpad = (int32_t*)m->arena.take(4 * tiles * (int64_t)m->layout.halo_cap);
   }
@@ -776,6 +779,16 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     }
     chk(upload(m, hidx, m->hidx));
     chk(upload(m, chunks, m->chunks));
+    // Every chunk's tiles in the opposite order (last tile first, negative
+    // stride). Steps alternate between the two walks, so that a step starts
+    // on the tiles the previous one finished with, whose records and cells
+    // are still in L2. The order of the tiles does not change any result.
+    std::vector<swe::Chunk> back(chunks);
+    for (swe::Chunk& c : back) {
+      c.tile0 += (c.ntiles - 1) * c.stride;
+      c.stride = -c.stride;
+    }
+    chk(upload(m, back, m->chunks_back));
     if (m->layout.hreg) {
       // tile t's halo list at t * halo_cap, padded with the tile's first cell
       const int64_t hc = m->layout.halo_cap;
@@ -846,9 +859,11 @@ void release_mesh(swe_mesh* m) {
 }
 
 template <typename Real>
-static void launch_forward_t(const swe_mesh* m, const swe::DevState<Real>& ds, cudaStream_t st) {
+static void launch_forward_t(const swe_mesh* m, const swe::DevState<Real>& ds, cudaStream_t st,
+                             bool back) {
   constexpr bool comp = sizeof(Real) == 4;
-  const swe::DevMesh<Real> dm = dev_mesh<Real>(m);
+  swe::DevMesh<Real> dm = dev_mesh<Real>(m);
+  if (back && m->chunks_back) dm.chunks = m->chunks_back;
   const swe::Num num = num_of(m);
   if (m->kernel == SWE_KERNEL_EDGE) {
     swe::k_edge_flux<Real><<<m->grid_edge, 256, 0, st>>>(dm, ds, num);
@@ -860,11 +875,11 @@ static void launch_forward_t(const swe_mesh* m, const swe::DevState<Real>& ds, c
   }
 }
 
-void launch_forward(const swe_mesh* m, const swe::DevState<float>& ds, cudaStream_t st) {
-  launch_forward_t<float>(m, ds, st);
+void launch_forward(const swe_mesh* m, const swe::DevState<float>& ds, cudaStream_t st, bool back) {
+  launch_forward_t<float>(m, ds, st, back);
 }
-void launch_forward(const swe_mesh* m, const swe::DevState<double>& ds, cudaStream_t st) {
-  launch_forward_t<double>(m, ds, st);
+void launch_forward(const swe_mesh* m, const swe::DevState<double>& ds, cudaStream_t st, bool back) {
+  launch_forward_t<double>(m, ds, st, back);
 }
 
 void gather_any(const swe_mesh* m, const double* src, void* dst, int stride) {

@@ -84,6 +84,7 @@ struct swe_mesh {
   void *tg0 = nullptr, *tg1 = nullptr, *tg2 = nullptr;
   void* trec = nullptr;  // FP32: interleaved records {packed sides, nx, ny, l}
   swe::Chunk* chunks = nullptr;  // work of each block of the tiled kernels
+  swe::Chunk* chunks_back = nullptr;  // the same chunks, tiles last to first
   int grid_edge = 1, grid_cell = 1, grid_cfl = 1, max_grid = 1;
   // Handles that use this mesh (states). swe_mesh_destroy while some are
   // alive only marks the mesh; the last of them to go frees it.
@@ -105,6 +106,7 @@ struct swe_state {
   cudaStream_t capture = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool open_ended = true;  // the device t_end is +inf for every scenario
+  bool walk_back = false;  // the next step walks the chunks backwards
 };
 
 namespace swe_host {
@@ -167,8 +169,11 @@ swe::DevState<Real> dev_state(const swe_state* s) {
 int smem_optin_bytes();
 
 // One forward step of the mesh's kernel on explicitly given state buffers.
-void launch_forward(const swe_mesh* m, const swe::DevState<float>& ds, cudaStream_t st);
-void launch_forward(const swe_mesh* m, const swe::DevState<double>& ds, cudaStream_t st);
+// One step; back: walk every chunk's tiles last to first (same results).
+void launch_forward(const swe_mesh* m, const swe::DevState<float>& ds, cudaStream_t st,
+                    bool back = false);
+void launch_forward(const swe_mesh* m, const swe::DevState<double>& ds, cudaStream_t st,
+                    bool back = false);
 // Caller order (FP64) -> internal order in the mesh precision, and back;
 // stride 4 for interleaved cells.
 void gather_any(const swe_mesh* m, const double* src, void* dst, int stride);

@@ -89,7 +89,9 @@ inline Num make_num(double g, double courant, double h_eps, int32_t wait = 0) {
 // (k = 0, 1, ...) of scenario scen, whose cells end at cell_end. The chunks
 // of one scenario interleave (stride = their count), so the blocks resident
 // at any moment sweep neighbouring tiles together and a tile's halo cells
-// are mostly still in L2 from the neighbours' copies. part: the chunk's
+// are mostly still in L2 from the neighbours' copies. The same chunks walked
+// backwards (tile0 the last tile, stride negative) serve every other step.
+// part: the chunk's
 // mass partial slot (the scenario's slots are contiguous from its
 // control word's part0).
 struct Chunk {
