@@ -182,8 +182,18 @@ swe_status swe_state_init_device(swe_mesh* mesh, const double* h, const double* 
 
 /* Replaces (h, hu, hv) from host arrays (caller order) and resets t = 0 and
  * the step count; bed and friction stay. The next CFL time step is
- * recomputed from the new state (Sec. 2.2). */
+ * recomputed from the new state (Sec. 2.2). Arrays in page-locked host
+ * memory (cudaHostAlloc, cudaHostRegister) are read by one kernel across
+ * the host link; other host memory goes through a device staging buffer.
+ * The arrays are no longer used when the call returns. */
 swe_status swe_state_set(swe_state* state, const double* h, const double* hu, const double* hv);
+
+/* swe_state_set from FP32 host arrays (caller order), for callers that keep
+ * the fields of an SWE_F32 state in FP32: the values are those the state
+ * holds (swe_state_set rounds FP64 values to the nearest FP32), so the
+ * state equals swe_state_set's with the same values in FP64, in half the
+ * bytes. An SWE_F64 state widens them exactly. */
+swe_status swe_state_set_f32(swe_state* state, const float* h, const float* hu, const float* hv);
 
 /* swe_state_set with DEVICE arrays (FP64, caller order), ordered after the
  * work queued on cuda_stream as swe_state_init_device is. Synchronises. */
@@ -223,9 +233,17 @@ swe_status swe_sync(swe_state* state);
 /* Copies the state to host arrays in caller order (any pointer may be NULL):
  * the one device-to-host transfer at the end of a run (Sec. 2.3).
  * *t = simulated time (scenario 0's on an ensemble), *mass = sum of area * h
- * in FP64 over every cell. Synchronises. */
+ * in FP64 over every cell. Synchronises. Arrays in page-locked host memory
+ * are written by one kernel across the host link; other host memory is
+ * written through a device staging buffer. */
 swe_status swe_copy_out(const swe_state* state, double* h, double* hu, double* hv, double* t,
                         double* mass);
+
+/* swe_copy_out into FP32 host arrays: exact for an SWE_F32 state (its
+ * values are FP32), rounded to the nearest FP32 for an SWE_F64 state. t and
+ * mass as in swe_copy_out (FP64). */
+swe_status swe_copy_out_f32(const swe_state* state, float* h, float* hu, float* hv, double* t,
+                            double* mass);
 
 /* swe_copy_out into DEVICE arrays (FP64, caller order, any may be NULL; t
  * and mass are host scalars as in swe_copy_out). The library's stream first

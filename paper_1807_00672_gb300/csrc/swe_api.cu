@@ -54,6 +54,39 @@ __global__ void k_gather_gn2(const double* __restrict__ n, const int32_t* __rest
   }
 }
 
+// Caller-order fields (Host = double or float; any of f0, f1, f2 may be
+// null) -> the state's cells: d_k[iperm[c] stride] = Real(f_k[c]) for the
+// caller cells c in [0, n). The sources are read in caller order (coalesced,
+// which suits page-locked host memory read across the host link) and
+// converted by round to nearest (Real narrower than Host) or exactly.
+template <typename Real, typename Host>
+__global__ void k_put_fields(const Host* __restrict__ f0, const Host* __restrict__ f1,
+                             const Host* __restrict__ f2, const int32_t* __restrict__ iperm,
+                             int64_t n, Real* d0, Real* d1, Real* d2, int stride) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = (int64_t)iperm[c] * stride;
+    if (f0) d0[j] = Real(f0[c]);
+    if (f1) d1[j] = Real(f1[c]);
+    if (f2) d2[j] = Real(f2[c]);
+  }
+}
+
+// The reverse over caller cells [c0, c1): f_k[c] = Host(d_k[iperm[c] stride])
+// (any f_k may be null), written in caller order.
+template <typename Real, typename Host>
+__global__ void k_take_fields(const Real* s0, const Real* s1, const Real* s2,
+                              const int32_t* __restrict__ iperm, int64_t c0, int64_t c1, Host* f0,
+                              Host* f1, Host* f2, int stride) {
+  for (int64_t c = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < c1;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = (int64_t)iperm[c] * stride;
+    if (f0) f0[c] = Host(s0[j]);
+    if (f1) f1[c] = Host(s1[j]);
+    if (f2) f2[c] = Host(s2[j]);
+  }
+}
+
 }  // namespace swe
 
 namespace swe_host {
@@ -386,24 +419,60 @@ void open_end(swe_state* s) {
   s->open_ended = true;
 }
 
-// (h, hu, hv) in caller order -> buffer 0. Host arrays go through the
-// staging buffer; device arrays (on_device) are gathered from directly.
-swe_status upload_state_fields(swe_state* s, const double* h, const double* hu, const double* hv,
-                               bool on_device = false) {
+// Device address of a caller host array that kernels may read and write
+// directly: page-locked host memory (cudaHostAlloc, cudaHostRegister) is
+// mapped into the device's address space. Null for any other memory.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+template <typename Host>
+void launch_put(const swe_mesh* m, const Host* const f[3], void* const d[3], int stride) {
+  if (!f[0] && !f[1] && !f[2]) return;
+  const int grid = grid_for(m->T, 256, m->sms * 16);
+  if (m->prm.precision == SWE_F64)
+    swe::k_put_fields<double, Host><<<grid, 256, 0, m->stream>>>(
+        f[0], f[1], f[2], m->iperm, m->T, (double*)d[0], (double*)d[1], (double*)d[2], stride);
+  else
+    swe::k_put_fields<float, Host><<<grid, 256, 0, m->stream>>>(
+        f[0], f[1], f[2], m->iperm, m->T, (float*)d[0], (float*)d[1], (float*)d[2], stride);
+}
+
+// Caller-order arrays (any may be null) -> the state's arrays dst[k] (cells
+// `stride` apart). Device arrays (on_device) and page-locked host arrays are
+// read by one kernel across the host link; other host arrays go through the
+// staging buffer (T doubles), one at a time.
+template <typename Host>
+swe_status put_fields(const swe_state* s, const Host* const src[3], void* const dst[3], int stride,
+                      bool on_device) {
   const swe_mesh* m = s->mesh;
-  const double* src[3] = {h, hu, hv};
-  void* dst[3] = {s->h[0], s->hu[0], s->hv[0]};
+  const Host* direct[3] = {nullptr, nullptr, nullptr};
+  for (int k = 0; k < 3; ++k)
+    if (src[k]) direct[k] = on_device ? src[k] : (const Host*)mapped_host(src[k]);
+  launch_put<Host>(m, direct, dst, stride);
   for (int k = 0; k < 3; ++k) {
-    const double* from = src[k];
-    if (!on_device) {
-      CK(cudaMemcpyAsync(s->stage, src[k], m->T * 8, cudaMemcpyHostToDevice, m->stream));
-      from = s->stage;
-    }
-    if (m->prm.precision == SWE_F64) launch_gather<double>(m, from, dst[k], s->stride);
-    else launch_gather<float>(m, from, dst[k], s->stride);
+    if (!src[k] || direct[k]) continue;
+    CK(cudaMemcpyAsync(s->stage, src[k], m->T * sizeof(Host), cudaMemcpyHostToDevice, m->stream));
+    const Host* one[3] = {nullptr, nullptr, nullptr};
+    one[k] = (const Host*)s->stage;
+    launch_put<Host>(m, one, dst, stride);
   }
   CK(cudaGetLastError());
   return SWE_OK;
+}
+
+// (h, hu, hv) in caller order -> buffer 0.
+template <typename Host>
+swe_status upload_state_fields(swe_state* s, const Host* h, const Host* hu, const Host* hv,
+                               bool on_device = false) {
+  const Host* src[3] = {h, hu, hv};
+  void* dst[3] = {s->h[0], s->hu[0], s->hv[0]};
+  return put_fields<Host>(s, src, dst, s->stride, on_device);
 }
 
 // Orders the mesh stream after the work queued so far on the caller's
@@ -628,7 +697,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   L.add(w * Tp);  // irP
   const bool with_rarea = kernel == SWE_KERNEL_TILED && p.precision == SWE_F64;
   if (with_rarea) L.add(w * Tp);  // 1 / area
-  if (ghost) L.add(4 * T);        // caller cell -> internal cell
+  L.add(4 * T);                   // caller cell -> internal cell
   if (kernel == SWE_KERNEL_EDGE) {
     L.add(4 * E); L.add(4 * E);
     L.add(w * E); L.add(w * E); L.add(w * E);
@@ -659,7 +728,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   m->area = m->arena.take(w * Tp);
   m->irP = m->arena.take(w * Tp);
   if (with_rarea) m->rarea = m->arena.take(w * Tp);
-  if (ghost) m->iperm = (int32_t*)m->arena.take(4 * T);
+  m->iperm = (int32_t*)m->arena.take(4 * T);
   if (kernel == SWE_KERNEL_EDGE) {
     m->eL = (int32_t*)m->arena.take(4 * E);
     m->eR = (int32_t*)m->arena.take(4 * E);
@@ -705,7 +774,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
       }
     }
     chk(upload(m, perm, m->perm));
-    if (ghost) {
+    {
       std::vector<int32_t> iperm(T, -1);
       for (int64_t j = 0; j < Tp; ++j)
         if (perm[j] >= 0) iperm[perm[j]] = (int32_t)j;
@@ -823,15 +892,6 @@ void refresh_mass(const swe_state* s) {
     else launch_cfl<float>(s, swe::kMassOnly);
   }
   swe::k_mass_sum<<<nscen(m), 256, 0, m->stream>>>(s->ctl, s->partial);
-}
-
-// Scatters buffer b of field k (0 h, 1 hu, 2 hv) to caller order in dst
-// (T doubles of device memory).
-void scatter_field(const swe_state* s, int k, int b, double* dst) {
-  const swe_mesh* m = s->mesh;
-  const void* src = (k == 0) ? s->h[b] : (k == 1) ? s->hu[b] : s->hv[b];
-  if (m->prm.precision == SWE_F64) launch_scatter<double>(m, src, dst, s->stride);
-  else launch_scatter<float>(m, src, dst, s->stride);
 }
 
 }  // namespace
@@ -1081,25 +1141,18 @@ swe_status state_init(swe_mesh* m, const double* h, const double* hu, const doub
     else
       swe::k_gather_gn2<float><<<gg, 256, 0, m->stream>>>(manning, m->perm, (float*)s->gn2, m->Tp, m->prm.g);
   }
-  const double* fields[2] = {z, gn2.empty() ? nullptr : gn2.data()};
-  void* dsts[2] = {s->z, s->gn2};
-  for (int k = 0; k < 2 && st == SWE_OK; ++k) {
-    if (!fields[k]) continue;  // g n^2 already gathered on the device
-    const double* from = fields[k];
-    if (!(on_device && k == 0)) {  // host array: through the staging buffer
-      if (cuda_failed(cudaMemcpyAsync(s->stage, fields[k], T * 8, cudaMemcpyHostToDevice, m->stream))) {
-        st = SWE_ECUDA;
-        break;
-      }
-      from = s->stage;
-    }
-    const int sd = (k == 0) ? s->stride : 1;  // z lives in the cells, gn2 is its own array
-    if (m->prm.precision == SWE_F64) launch_gather<double>(m, from, dsts[k], sd);
-    else launch_gather<float>(m, from, dsts[k], sd);
+  if (st == SWE_OK) {  // z lives in the cells, g n^2 is its own array
+    const double* zf[3] = {z, nullptr, nullptr};
+    void* zd[3] = {s->z, nullptr, nullptr};
+    st = put_fields<double>(s, zf, zd, s->stride, on_device);
   }
-  if (st == SWE_OK && cuda_failed(cudaGetLastError())) st = SWE_ECUDA;
+  if (st == SWE_OK && !gn2.empty()) {  // else g n^2 was gathered on the device
+    const double* nf[3] = {gn2.data(), nullptr, nullptr};
+    void* nd[3] = {s->gn2, nullptr, nullptr};
+    st = put_fields<double>(s, nf, nd, 1, false);
+  }
   if (st == SWE_OK && cuda_failed(cudaStreamSynchronize(m->stream))) st = SWE_ECUDA;
-  if (st == SWE_OK) st = upload_state_fields(s, h, hu, hv, on_device);
+  if (st == SWE_OK) st = upload_state_fields<double>(s, h, hu, hv, on_device);
   if (st == SWE_OK) st = reset_and_cfl(s);
   if (st != SWE_OK) {
     swe_state_destroy(s);
@@ -1127,7 +1180,14 @@ swe_status swe_state_init_device(swe_mesh* m, const double* h, const double* hu,
 
 swe_status swe_state_set(swe_state* s, const double* h, const double* hu, const double* hv) {
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
-  swe_status st = upload_state_fields(s, h, hu, hv);
+  swe_status st = upload_state_fields<double>(s, h, hu, hv);
+  if (st != SWE_OK) return st;
+  return reset_and_cfl(s);
+}
+
+swe_status swe_state_set_f32(swe_state* s, const float* h, const float* hu, const float* hv) {
+  if (!s || !h || !hu || !hv) return SWE_EINVAL;
+  swe_status st = upload_state_fields<float>(s, h, hu, hv);
   if (st != SWE_OK) return st;
   return reset_and_cfl(s);
 }
@@ -1136,7 +1196,7 @@ swe_status swe_state_set_device(swe_state* s, const double* h, const double* hu,
                                 void* cuda_stream) {
   if (!s || !h || !hu || !hv) return SWE_EINVAL;
   swe_status st = wait_for_caller(s->mesh, cuda_stream);
-  if (st == SWE_OK) st = upload_state_fields(s, h, hu, hv, true);
+  if (st == SWE_OK) st = upload_state_fields<double>(s, h, hu, hv, true);
   if (st != SWE_OK) return st;
   return reset_and_cfl(s);
 }
@@ -1192,9 +1252,30 @@ swe_status swe_sync(swe_state* s) {
 
 namespace {
 
-// swe_copy_out and swe_copy_out_device (to_device: h, hu, hv are device
-// arrays, written by the scatter kernels or device-to-device copies).
-swe_status copy_out(const swe_state* s, double* h, double* hu, double* hv, double* t, double* mass,
+template <typename Host>
+void launch_take(const swe_state* s, int b, int64_t c0, int64_t c1, Host* const f[3]) {
+  const swe_mesh* m = s->mesh;
+  if (c1 <= c0 || (!f[0] && !f[1] && !f[2])) return;
+  const int grid = grid_for(c1 - c0, 256, m->sms * 16);
+  if (m->prm.precision == SWE_F64)
+    swe::k_take_fields<double, Host><<<grid, 256, 0, m->stream>>>(
+        (const double*)s->h[b], (const double*)s->hu[b], (const double*)s->hv[b], m->iperm, c0, c1,
+        f[0], f[1], f[2], s->stride);
+  else
+    swe::k_take_fields<float, Host><<<grid, 256, 0, m->stream>>>(
+        (const float*)s->h[b], (const float*)s->hu[b], (const float*)s->hv[b], m->iperm, c0, c1,
+        f[0], f[1], f[2], s->stride);
+}
+
+// swe_copy_out[_f32] and swe_copy_out_device (to_device: h, hu, hv are
+// device arrays). Each scenario's cells are read from the buffer its
+// control word names (scenarios that stopped at different step counts sit
+// in different buffers); consecutive scenarios in the same buffer form one
+// range of caller cells. Device arrays and page-locked host arrays are
+// written by one kernel per range; other host arrays through the staging
+// buffer, one field at a time.
+template <typename Host>
+swe_status copy_out(const swe_state* s, Host* h, Host* hu, Host* hv, double* t, double* mass,
                     bool to_device) {
   if (!s) return SWE_EINVAL;
   const swe_mesh* m = s->mesh;
@@ -1202,33 +1283,34 @@ swe_status copy_out(const swe_state* s, double* h, double* hu, double* hv, doubl
   if (mass) refresh_mass(s);
   swe_status st = read_ctl(s);
   if (st != SWE_OK) return st;
-  bool same = true;
-  for (int i = 1; i < n; ++i) same = same && s->host_ctl[i].cur == s->host_ctl[0].cur;
-  double* dst[3] = {h, hu, hv};
-  for (int k = 0; k < 3; ++k) {
-    if (!dst[k]) continue;
-    const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (same && to_device) {
-      scatter_field(s, k, s->host_ctl[0].cur, dst[k]);
-    } else if (same) {
-      scatter_field(s, k, s->host_ctl[0].cur, s->stage);
-      CK(cudaMemcpyAsync(dst[k], s->stage, m->T * 8, kind, m->stream));
-    } else {
-      // Scenarios that stopped at different step counts sit in different
-      // buffers: copy each one's range from the buffer it is in.
-      for (int b = 0; b < 2; ++b) {
-        scatter_field(s, k, b, s->stage);
-        for (int i = 0; i < n; ++i) {
-          if (s->host_ctl[i].cur != b) continue;
-          const Scenario& sc = m->scen[i];
-          CK(cudaMemcpyAsync(dst[k] + sc.caller0, s->stage + sc.caller0, sc.ncells * 8, kind,
-                             m->stream));
-        }
-      }
-    }
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(m->stream));
+  struct Range {
+    int64_t c0, c1;
+    int b;
+  };
+  std::vector<Range> ranges;
+  for (int i = 0; i < n; ++i) {
+    const Scenario& sc = m->scen[i];
+    const int b = s->host_ctl[i].cur;
+    if (!ranges.empty() && ranges.back().b == b && ranges.back().c1 == sc.caller0)
+      ranges.back().c1 = sc.caller0 + sc.ncells;
+    else
+      ranges.push_back({sc.caller0, sc.caller0 + sc.ncells, b});
   }
+  Host* dst[3] = {h, hu, hv};
+  Host* direct[3] = {nullptr, nullptr, nullptr};
+  for (int k = 0; k < 3; ++k)
+    if (dst[k]) direct[k] = to_device ? dst[k] : (Host*)mapped_host(dst[k]);
+  for (const Range& r : ranges) launch_take<Host>(s, r.b, r.c0, r.c1, direct);
+  for (int k = 0; k < 3; ++k) {
+    if (!dst[k] || direct[k]) continue;
+    Host* one[3] = {nullptr, nullptr, nullptr};
+    one[k] = (Host*)s->stage;
+    for (const Range& r : ranges) launch_take<Host>(s, r.b, r.c0, r.c1, one);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dst[k], s->stage, m->T * sizeof(Host), cudaMemcpyDeviceToHost, m->stream));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(m->stream));
   if (t) *t = s->host_ctl[0].t;
   if (mass) {
     double sum = 0.0;
@@ -1244,7 +1326,12 @@ extern "C" {
 
 swe_status swe_copy_out(const swe_state* s, double* h, double* hu, double* hv, double* t,
                         double* mass) {
-  return copy_out(s, h, hu, hv, t, mass, false);
+  return copy_out<double>(s, h, hu, hv, t, mass, false);
+}
+
+swe_status swe_copy_out_f32(const swe_state* s, float* h, float* hu, float* hv, double* t,
+                            double* mass) {
+  return copy_out<float>(s, h, hu, hv, t, mass, false);
 }
 
 swe_status swe_copy_out_device(const swe_state* s, double* h, double* hu, double* hv, double* t,
@@ -1253,7 +1340,7 @@ swe_status swe_copy_out_device(const swe_state* s, double* h, double* hu, double
   // the destinations may still be in use by the caller's earlier work
   swe_status st = wait_for_caller(s->mesh, cuda_stream);
   if (st != SWE_OK) return st;
-  return copy_out(s, h, hu, hv, t, mass, true);
+  return copy_out<double>(s, h, hu, hv, t, mass, true);
 }
 
 swe_status swe_state_info(const swe_state* s, int64_t* info) {

@@ -74,7 +74,7 @@ struct swe_mesh {
   void* area = nullptr;
   void* irP = nullptr;
   void* rarea = nullptr;  // 1 / area, FP64 tiled meshes
-  int32_t* iperm = nullptr;  // caller cell -> internal cell (meshes with ghost cells)
+  int32_t* iperm = nullptr;  // caller cell -> internal cell
   bool ghosts = false;       // swe_mesh_create_part: some cells are ghosts
   int32_t *eL = nullptr, *eR = nullptr, *cf[3] = {nullptr, nullptr, nullptr};
   void *nx = nullptr, *ny = nullptr, *len = nullptr;

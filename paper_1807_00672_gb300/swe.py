@@ -40,7 +40,7 @@ EXPORTS = (
     "swe_partition_create", "swe_partition_sizes", "swe_partition_local_mesh",
     "swe_partition_exchange", "swe_partition_destroy", "swe_mesh_create_part",
     "swe_state_halo_pack", "swe_state_halo_unpack", "swe_state_dt_device",
-    "swe_state_set_dt_min_device",
+    "swe_state_set_dt_min_device", "swe_state_set_f32", "swe_copy_out_f32",
 )
 
 
@@ -98,6 +98,8 @@ def lib():
         "swe_advance": (st, [vp, dbl, vp]),
         "swe_sync": (st, [vp]),
         "swe_copy_out": (st, [vp, vp, vp, vp, vp, vp]),
+        "swe_state_set_f32": (st, [vp, vp, vp, vp]),
+        "swe_copy_out_f32": (st, [vp, vp, vp, vp, vp, vp]),
         "swe_state_info": (st, [vp, vp]),
         "swe_next_dt": (st, [vp, vp]),
         "swe_scenario_info": (st, [vp, ctypes.c_int32, vp, vp, vp, vp]),
@@ -146,6 +148,10 @@ def _vp(addr):
 
 def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
 
 
 def _check(status: int, what: str):
@@ -308,6 +314,12 @@ class State:
         h, hu, hv = (_f64(a) for a in (h, hu, hv))
         _check(lib().swe_state_set(self._h, _p(h), _p(hu), _p(hv)), "swe_state_set")
 
+    def set_f32(self, h, hu, hv):
+        """swe_state_set_f32 from float32 arrays (page-locked ones, e.g.
+        views of pinned torch tensors, are read directly by the device)."""
+        h, hu, hv = (_f32(a) for a in (h, hu, hv))
+        _check(lib().swe_state_set_f32(self._h, _p(h), _p(hu), _p(hv)), "swe_state_set_f32")
+
     def set_device(self, h, hu, hv, stream=None):
         """swe_state_set_device: device addresses (ints) of float64 arrays."""
         _check(lib().swe_state_set_device(self._h, _vp(h), _vp(hu), _vp(hv), _vp(stream)),
@@ -366,6 +378,19 @@ class State:
         m = ctypes.c_double()
         args = [None if a is None else _p(a) for a in (h, hu, hv)]
         _check(lib().swe_copy_out(self._h, *args, ctypes.byref(t), ctypes.byref(m)), "swe_copy_out")
+        return t.value, m.value
+
+    def copy_out_f32(self, h=None, hu=None, hv=None):
+        """swe_copy_out_f32 into the given float32 arrays (any may be None);
+        returns (t, mass)."""
+        for a in (h, hu, hv):
+            if a is not None and (a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]):
+                raise TypeError("copy_out_f32 needs contiguous float32 arrays")
+        t = ctypes.c_double()
+        m = ctypes.c_double()
+        args = [None if a is None else _p(a) for a in (h, hu, hv)]
+        _check(lib().swe_copy_out_f32(self._h, *args, ctypes.byref(t), ctypes.byref(m)),
+               "swe_copy_out_f32")
         return t.value, m.value
 
     def fields(self):
