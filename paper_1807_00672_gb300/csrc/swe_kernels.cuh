@@ -527,8 +527,9 @@ __device__ __forceinline__ void face_flux_f32(const V4<float>& A, const V4<float
   // hydrostatic reconstruction
   const float zs = fmaxf(A.w, zB);
   const float xA = A.x + A.w - zs, xB = hB + zB - zs;
-  const float hAs = xA > eps ? xA : 0.0f;
-  const float hBs = xB > eps ? xB : 0.0f;
+  const bool wA = xA > eps, wB = xB > eps;  // wet sides: h* > 0 exactly when x > h_eps >= 0
+  const float hAs = wA ? xA : 0.0f;
+  const float hBs = wB ? xB : 0.0f;
   // HLLC wave speeds (see hllc). A dry side takes the normal velocity
   // un_B - 2 c_B (A dry) or un_A + 2 c_A (B dry): the two-rarefaction
   // estimates then reduce exactly to Toro's dry-bed speeds (c* = 0,
@@ -537,8 +538,8 @@ __device__ __forceinline__ void face_flux_f32(const V4<float>& A, const V4<float
   const float hg = 0.5f * g;
   const float ghA = g * hAs, ghB = g * hBs;
   const float cA = sqrt_approx(ghA), cB = sqrt_approx(ghB);
-  const float vnA = hAs > 0.0f ? unA : unB - 2.0f * cB;
-  const float vnB = hBs > 0.0f ? unB : unA + 2.0f * cA;
+  const float vnA = wA ? unA : unB - 2.0f * cB;
+  const float vnB = wB ? unB : unA + 2.0f * cA;
   const float us = (vnA + vnB) * 0.5f + cA - cB;
   const float cs = (cA + cB) * 0.5f + (vnA - vnB) * 0.25f;
   const float Sm = fminf(fminf(vnA - cA, us - cs), 0.0f);
