@@ -60,13 +60,15 @@ typedef enum {
 
 /* Internal cell numbering (locality of the neighbour gathers). */
 typedef enum {
-  SWE_ORDER_NONE = 0,   /* keep the caller's order */
-  SWE_ORDER_MORTON = 1  /* Z-order of the cell centroids; edges follow their cells */
+  SWE_ORDER_NONE = 0,    /* keep the caller's order */
+  SWE_ORDER_MORTON = 1,  /* Z-order of the cell centroids; edges follow their cells */
+  SWE_ORDER_RCM = 2      /* reverse Cuthill-McKee order of the edge-neighbour graph */
 } swe_order;
 
 /* Kernel structure of one step. */
 typedef enum {
-  SWE_KERNEL_AUTO = 0,  /* SWE_KERNEL_TILED */
+  SWE_KERNEL_AUTO = 0,  /* SWE_KERNEL_TILED; SWE_KERNEL_EDGE for a single mesh in
+                           SWE_ORDER_RCM, whose tiles would be thin strips */
   SWE_KERNEL_EDGE = 1,  /* two launches: per-edge fluxes to HBM, then a per-cell gather
                            and update (the paper's two parallel loops, Sec. 2.3) */
   SWE_KERNEL_TILED = 2  /* one launch: each block stages a tile of cells in shared
@@ -126,6 +128,13 @@ void swe_params_default(swe_params* p);
  * SWE_EINVAL for bad arguments. *out receives the handle. */
 swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tris,
                            const swe_params* params, void* cuda_stream, swe_mesh** out);
+
+/* Host only (no device is touched): the internal cell order swe_mesh_create
+ * gives this mesh under `order` (a swe_order), perm[j] = caller index of
+ * the cell at internal position j (perm: n_tris entries, caller-owned).
+ * SWE_EMESH for an invalid mesh, SWE_EINVAL for bad arguments. */
+swe_status swe_cell_order(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tris,
+                          int32_t order, int32_t* perm);
 
 /* Builds one device-resident mesh holding n_scenarios independent scenarios
  * (an ensemble): scenario i has the nodes xy[i] (n_nodes[i] of them) and the

@@ -14,6 +14,8 @@
 // rounded value of its formula.
 #include "mesh_build.h"
 
+#include "../../include/swe.h"
+
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -56,6 +58,95 @@ std::vector<int32_t> morton_order(const double* xy, int64_t V, const int32_t* tr
   std::vector<int32_t> order(T);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t p, int32_t r) { return key[p] < key[r]; });
+  return order;
+}
+
+std::vector<int32_t> rcm_order(int64_t T, const std::vector<int32_t>& nbr) {
+  auto degree = [&](int64_t c) {
+    int d = 0;
+    for (int k = 0; k < 3; ++k) d += nbr[3 * c + k] >= 0;
+    return d;
+  };
+  // Breadth-first levels from s over the unplaced cells of its component:
+  // fills `seen` with stamp, returns the cells in visiting order and the
+  // number of levels (the eccentricity of s plus one) in *levels.
+  std::vector<int32_t> seen(T, -1), level(T, 0), queue;
+  queue.reserve(T);
+  auto bfs = [&](int32_t s, int32_t stamp, int* levels) {
+    queue.clear();
+    queue.push_back(s);
+    seen[s] = stamp;
+    level[s] = 0;
+    for (size_t q = 0; q < queue.size(); ++q) {
+      const int32_t c = queue[q];
+      for (int k = 0; k < 3; ++k) {
+        const int32_t d = nbr[3 * (int64_t)c + k];
+        if (d < 0 || seen[d] == stamp) continue;
+        seen[d] = stamp;
+        level[d] = level[c] + 1;
+        queue.push_back(d);
+      }
+    }
+    *levels = level[queue.back()] + 1;
+  };
+  std::vector<uint8_t> placed(T, 0);
+  std::vector<int32_t> order;
+  order.reserve(T);
+  int32_t stamp = 0;
+  for (int64_t first = 0; first < T; ++first) {
+    if (placed[first]) continue;
+    // Start cell: lowest degree of the component (lowest index on ties),
+    // then the pseudo-peripheral search of George and Liu: move to the
+    // lowest-degree cell of the last level while that lengthens the levels.
+    int levels = 0;
+    bfs((int32_t)first, stamp, &levels);
+    int32_t r = (int32_t)first;
+    for (int32_t c : queue)
+      if (degree(c) < degree(r) || (degree(c) == degree(r) && c < r)) r = c;
+    ++stamp;
+    bfs(r, stamp, &levels);
+    for (int iter = 0; iter < 16; ++iter) {
+      const int last = levels - 1;
+      int32_t x = -1;
+      for (int32_t c : queue)
+        if (level[c] == last && (x < 0 || degree(c) < degree(x) || (degree(c) == degree(x) && c < x)))
+          x = c;
+      int lx = 0;
+      ++stamp;
+      bfs(x, stamp, &lx);
+      if (lx <= levels) break;
+      r = x;
+      levels = lx;
+    }
+    // Cuthill-McKee from r: each cell's unplaced neighbours by increasing
+    // degree, lower index first on ties.
+    const size_t begin = order.size();
+    order.push_back(r);
+    placed[r] = 1;
+    for (size_t q = begin; q < order.size(); ++q) {
+      const int32_t c = order[q];
+      int32_t next[3];
+      int n = 0;
+      for (int k = 0; k < 3; ++k) {
+        const int32_t d = nbr[3 * (int64_t)c + k];
+        if (d >= 0 && !placed[d]) {
+          bool dup = false;
+          for (int i = 0; i < n; ++i) dup = dup || next[i] == d;
+          if (!dup) next[n++] = d;
+        }
+      }
+      std::sort(next, next + n, [&](int32_t a, int32_t b) {
+        const int da = degree(a), db = degree(b);
+        return da != db ? da < db : a < b;
+      });
+      for (int i = 0; i < n; ++i) {
+        placed[next[i]] = 1;
+        order.push_back(next[i]);
+      }
+    }
+    ++stamp;
+  }
+  std::reverse(order.begin(), order.end());
   return order;
 }
 
@@ -170,6 +261,14 @@ int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t 
   std::iota(m.perm.begin(), m.perm.end(), 0);
   if (order == 1) {
     m.perm = morton_order(xy, V, tri.data(), T);
+  } else if (order == 2) {
+    std::vector<int32_t> nbr(3 * T, -1);  // edge neighbours, by face
+    for (int64_t i = 0; i < T; ++i)
+      for (int k = 0; k < 3; ++k) {
+        const int32_t e = edge_of_half[3 * i + k];
+        nbr[3 * i + k] = (cL[e] == i) ? cR[e] : cL[e];
+      }
+    m.perm = rcm_order(T, nbr);
   } else if (order != 0) {
     return -1;
   }
@@ -311,3 +410,14 @@ int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t 
 }
 
 }  // namespace swe
+
+extern "C" swe_status swe_cell_order(const double* xy, int64_t n_nodes, const int32_t* tri,
+                                     int64_t n_tris, int32_t order, int32_t* perm) {
+  if (!perm || order < SWE_ORDER_NONE || order > SWE_ORDER_RCM) return SWE_EINVAL;
+  swe::HostMesh hm;
+  const int rc = swe::build_host_mesh(xy, n_nodes, tri, n_tris, order, 0, false, hm);
+  if (rc == -2) return SWE_EMESH;
+  if (rc != 0) return SWE_EINVAL;
+  std::copy(hm.perm.begin(), hm.perm.end(), perm);
+  return SWE_OK;
+}

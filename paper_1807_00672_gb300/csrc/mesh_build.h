@@ -46,8 +46,16 @@ struct HostMesh {
 // must be valid.
 std::vector<int32_t> morton_order(const double* xy, int64_t V, const int32_t* tri, int64_t T);
 
+// Reverse Cuthill-McKee order of the cells of a graph given as three
+// neighbours per cell (-1: none): breadth-first from a pseudo-peripheral
+// cell of each connected component (George and Liu's search), every visited
+// cell's unvisited neighbours appended by increasing degree (lower index on
+// ties), the whole sequence reversed. order[j] = the cell at position j.
+std::vector<int32_t> rcm_order(int64_t T, const std::vector<int32_t>& nbr);
+
 // Returns 0 or a negative status: -1 bad arguments, -2 invalid mesh.
-// order: 0 = caller order, 1 = Morton order of centroids.
+// order: 0 = caller order, 1 = Morton order of centroids, 2 = reverse
+// Cuthill-McKee order of the edge-neighbour graph.
 // tile > 0 also builds the tiled layout; with_edges builds the two-launch one.
 int build_host_mesh(const double* xy, int64_t V, const int32_t* tri, int64_t T, int order,
                     int32_t tile, bool with_edges, HostMesh& out);

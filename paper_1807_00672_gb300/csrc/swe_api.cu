@@ -517,7 +517,7 @@ swe_status resolve_params(const swe_params* params, swe_params& p) {
   swe_params_default(&p);
   if (params) p = *params;
   if (p.precision != SWE_F64 && p.precision != SWE_F32) return SWE_EINVAL;
-  if (p.order != SWE_ORDER_NONE && p.order != SWE_ORDER_MORTON) return SWE_EINVAL;
+  if (p.order < SWE_ORDER_NONE || p.order > SWE_ORDER_RCM) return SWE_EINVAL;
   if (p.kernel < SWE_KERNEL_AUTO || p.kernel > SWE_KERNEL_TILED) return SWE_EINVAL;
   if (p.cells_per_thread == 0) p.cells_per_thread = 2;
   if (p.tile == 0)
@@ -552,6 +552,12 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   swe_params p;
   swe_status st = resolve_params(params, p);
   if (st != SWE_OK) return st;
+  // AUTO: the tiled kernel, except for one reverse Cuthill-McKee-ordered
+  // mesh, whose tiles are thin strips of its breadth-first levels (2.7 face
+  // records and 2 halo cells per cell at 512-cell tiles): the edge kernel
+  // runs it faster (34 against 29 G cell-updates/s at 10M triangles, FP32).
+  const bool autok = (params ? params->kernel : SWE_KERNEL_AUTO) == SWE_KERNEL_AUTO;
+  if (autok && n == 1 && p.order == SWE_ORDER_RCM) p.kernel = SWE_KERNEL_EDGE;
   const int kernel = p.kernel;
   if (kernel == SWE_KERNEL_EDGE && n > 1) return SWE_EINVAL;
   const int tile = p.tile;

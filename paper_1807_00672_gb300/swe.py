@@ -25,7 +25,7 @@ SWE_EDRY = -8
 SWE_ESTATE = -9
 
 PRECISION = {"f64": 0, "f32": 1}
-ORDER = {"none": 0, "morton": 1}
+ORDER = {"none": 0, "morton": 1, "rcm": 2}
 KERNEL = {"auto": 0, "edge": 1, "tiled": 2}
 
 # Every symbol include/swe.h declares.
@@ -40,7 +40,7 @@ EXPORTS = (
     "swe_partition_create", "swe_partition_sizes", "swe_partition_local_mesh",
     "swe_partition_exchange", "swe_partition_destroy", "swe_mesh_create_part",
     "swe_state_halo_pack", "swe_state_halo_unpack", "swe_state_dt_device",
-    "swe_state_set_dt_min_device", "swe_state_set_f32", "swe_copy_out_f32",
+    "swe_state_set_dt_min_device", "swe_state_set_f32", "swe_copy_out_f32", "swe_cell_order",
 )
 
 
@@ -99,6 +99,7 @@ def lib():
         "swe_sync": (st, [vp]),
         "swe_copy_out": (st, [vp, vp, vp, vp, vp, vp]),
         "swe_state_set_f32": (st, [vp, vp, vp, vp]),
+        "swe_cell_order": (st, [vp, i64, vp, i64, ctypes.c_int32, vp]),
         "swe_copy_out_f32": (st, [vp, vp, vp, vp, vp, vp]),
         "swe_state_info": (st, [vp, vp]),
         "swe_next_dt": (st, [vp, vp]),
@@ -173,6 +174,17 @@ def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, coura
     p.halo_schedule = halo_schedule
     p.wait_rounds = wait_rounds
     return p
+
+
+def cell_order(xy, tri, order="morton") -> np.ndarray:
+    """swe_cell_order (host only): perm[j] = caller index of the cell at
+    internal position j under `order` ("none", "morton" or "rcm")."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+    tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+    perm = np.empty(tri.shape[0], dtype=np.int32)
+    _check(lib().swe_cell_order(_p(xy), xy.shape[0], _p(tri), tri.shape[0], ORDER[order], _p(perm)),
+           "swe_cell_order")
+    return perm
 
 
 class Mesh:

@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-11
 
 KERNELS = [("tiled", "morton", 256), ("tiled", "morton", 128), ("tiled", "none", 256),
-           ("edge", "morton", 0), ("edge", "none", 0)]
+           ("tiled", "rcm", 256), ("edge", "morton", 0), ("edge", "none", 0), ("edge", "rcm", 0)]
 
 # tiled kernel shapes: (cells per tile, cells per thread, stages)
 # (tile, cells_per_thread, stages, halo_schedule)
