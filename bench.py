@@ -409,6 +409,8 @@ def main():
         out["adjoint"] = adjoint_leg(args, stream, errors)
     if rank == 0 and not args.no_extras:
         out["fp64"] = fp64_leg(case, args, stream, ws)
+        if args.precision == "f32":
+            out["compensated_depth"] = compensated_leg(case, args, stream)
         out["humps_1m"] = humps_leg(args, stream, errors)
     if rank == 0 and not args.no_extras and not args.no_ensemble:
         out["ensemble"] = ensemble_leg(args, stream, errors)
@@ -711,8 +713,10 @@ def water_drop_leg(args, stream):
     case = inputs.water_drop_case(n)
     res = {"table2_test": args.water_drop_test, "triangles": case.mesh.n_tris, "t_end": 2400.0}
     fields = {}
-    for prec in ("f32", "f64"):
-        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision=prec, stream=ctypes_stream(stream))
+    for prec in ("f32", "f64", "f32_compensated"):
+        comp = prec == "f32_compensated"
+        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f32" if comp else prec,
+                        compensated_depth=comp, stream=ctypes_stream(stream))
         st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
         m0 = st.mass
         st.run(16)  # capture the step graph
@@ -727,9 +731,11 @@ def water_drop_leg(args, stream):
                      "t": st.t, "mass_rel_drift": abs(st.mass - m0) / m0}
         st.close()
         mesh.close()
-    eta32, eta64 = fields["f32"] - 10.0, fields["f64"] - 10.0
-    res["f32_vs_f64_linf_eta"] = float(np.abs(eta32 - eta64).max() / np.abs(eta64).max())
-    res["f32_vs_f64_l1_eta"] = float(np.abs(eta32 - eta64).sum() / np.abs(eta64).sum())
+    eta64 = fields["f64"] - 10.0
+    for key in ("f32", "f32_compensated"):
+        eta32 = fields[key] - 10.0
+        res[f"{key}_vs_f64_linf_eta"] = float(np.abs(eta32 - eta64).max() / np.abs(eta64).max())
+        res[f"{key}_vs_f64_l1_eta"] = float(np.abs(eta32 - eta64).sum() / np.abs(eta64).sum())
     return res
 
 
@@ -790,6 +796,18 @@ def fp32_error(case, mesh=None, steps=None, t_end=None, stream=None):
     st.close()
     if own:
         mesh.close()
+    # the same against FP32 with a per-cell depth residual (compensated_depth)
+    cm = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f32", compensated_depth=True,
+                  stream=None if stream is None else ctypes_stream(stream))
+    cs = swe.State(cm, case.h, case.hu, case.hv, case.z, case.n)
+    m0 = cs.mass
+    kc = cs.advance(t_end)
+    comp = {"steps_fp32": int(kc)}
+    comp.update(_rel_errors(cs.fields(), (o.h, o.hu, o.hv), o.mesh.cells()["area"]))
+    comp["mass_rel_drift_fp32"] = abs(cs.mass - m0) / m0
+    res["compensated_depth"] = comp
+    cs.close()
+    cm.close()
     return res
 
 
@@ -850,6 +868,37 @@ def humps_leg(args, stream, errors):
     return res
 
 
+def compensated_leg(case, args, stream, steps=200):
+    """The FP32 step of the same workload with a per-cell depth residual
+    (compensated_depth): cell-updates/s over `steps` graph-replayed steps
+    (CUDA events) and the HBM fraction at the algorithmic bytes plus the
+    residual's read and write (8 B per cell)."""
+    import torch
+    from paper_1807_00672_gb300 import swe
+    peak, kind = measured_peaks()
+    mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f32", compensated_depth=True,
+                    stream=ctypes_stream(stream))
+    st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+    st.run(0)
+    st.run(max(3, args.warmup))
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    st.run(steps, sync=False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    st.sync()
+    ms = a.elapsed_time(b) / steps
+    balg = alg_bytes_per_cell(4, WORKLOADS[args.workload]["per_cell_n"]) + 8
+    res = {"value": mesh.T / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "alg_bytes_per_cell": balg, "hbm_frac": balg * mesh.T / (ms * 1e-3) / 1e9 / peak,
+           "peak_source": f"{kind} HBM copy bandwidth"}
+    st.close()
+    mesh.close()
+    return res
+
+
 def summary(out):
     """The headline figures again, compact, at the end of the line."""
     r = lambda x: None if x is None else float(f"{x:.4g}")
@@ -879,7 +928,18 @@ def summary(out):
             v = v.get("fp32", v)
             e[cfg] = {"l1_h": r(v.get("l1_h")), "linf_h": r(v.get("linf_h")),
                       "l1_hu": r(v.get("l1_hu")), "mass": r(v.get("mass_rel_drift_fp32"))}
+            c = v.get("compensated_depth")
+            if c:
+                e[cfg]["compensated_depth"] = {"l1_h": r(c.get("l1_h")),
+                                               "mass": r(c.get("mass_rel_drift_fp32"))}
         s["fp32_error_vs_oracle"] = e
+    if "compensated_depth" in out:
+        c = out["compensated_depth"]
+        s["f32_compensated_depth"] = {"value": r(c["value"]), "hbm_frac": r(c["hbm_frac"])}
+    if "water_drop" in out:
+        w = out["water_drop"]
+        s["water_drop_mass_drift"] = {k: r(w[k]["mass_rel_drift"])
+                                      for k in ("f32", "f32_compensated", "f64") if k in w}
     return s
 
 

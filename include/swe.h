@@ -108,6 +108,16 @@ typedef struct {
                                 testing the timeout path: copies already in flight are still
                                 waited for before a block exits, and nothing is left
                                 running). Other values: SWE_EINVAL. */
+  int32_t compensated_depth; /* 1: an SWE_F32 state also keeps, per cell, the FP32 residual of
+                                its depth (h + residual is the depth). The Euler update (Eq. 4)
+                                of h is then carried exactly up to its final rounding and the
+                                rounding error goes to the residual, so updates below half an
+                                ulp of h accumulate instead of being lost and the mass is kept
+                                over long runs. Faces use h; copy-outs and the mass integral
+                                use h + residual. 4 B per cell more in HBM, 8 B more traffic
+                                per step. Needs SWE_F32, SWE_KERNEL_TILED (or AUTO), 2 stages
+                                and halo_schedule 0; not for swe_grad_record. 0 = off
+                                (default); other values: SWE_EINVAL. */
 } swe_params;
 
 typedef struct swe_mesh swe_mesh;
@@ -294,8 +304,8 @@ void swe_state_destroy(swe_state* state);
  * state and to the gauge depths, the gradient of L with respect to the
  * initial state, the bed z and Manning's n. swe_grad can be called any
  * number of times on one tape (different seeds). Requires a single-scenario
- * mesh built with SWE_KERNEL_TILED and without ghost cells (SWE_ESTATE
- * otherwise). Results are in
+ * mesh built with SWE_KERNEL_TILED, without ghost cells and without
+ * compensated_depth (SWE_ESTATE otherwise). Results are in
  * the mesh precision; FP64 is the reference for accuracy. The adjoint runs
  * on the mesh's tiles: 256-cell tiles (swe_params.tile = 256) give the faster
  * adjoint, since at 512 cells its shared memory fits half as many blocks per

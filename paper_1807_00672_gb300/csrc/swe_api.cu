@@ -73,15 +73,17 @@ __global__ void k_put_fields(const Host* __restrict__ f0, const Host* __restrict
 }
 
 // The reverse over caller cells [c0, c1): f_k[c] = Host(d_k[iperm[c] stride])
-// (any f_k may be null), written in caller order.
+// (any f_k may be null), written in caller order. lo (FP32 states with a
+// depth residual, else null): the depth is h + lo, summed in FP64 (exactly:
+// |lo| is at most half an ulp of h) and rounded once to Host.
 template <typename Real, typename Host>
-__global__ void k_take_fields(const Real* s0, const Real* s1, const Real* s2,
+__global__ void k_take_fields(const Real* s0, const Real* s1, const Real* s2, const Real* lo,
                               const int32_t* __restrict__ iperm, int64_t c0, int64_t c1, Host* f0,
                               Host* f1, Host* f2, int stride) {
   for (int64_t c = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < c1;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = (int64_t)iperm[c] * stride;
-    if (f0) f0[c] = Host(s0[j]);
+    const int64_t i = iperm[c], j = i * stride;
+    if (f0) f0[c] = lo ? Host((double)s0[j] + (double)lo[i]) : Host(s0[j]);
     if (f1) f1[c] = Host(s1[j]);
     if (f2) f2[c] = Host(s2[j]);
   }
@@ -148,10 +150,10 @@ int grid_for(int64_t n, int threads, int cap) {
 
 // Opts the tiled kernel into its dynamic shared memory and returns its
 // resident blocks per SM (0 if it cannot run with this layout).
-template <typename Real, int NT, int NS, int TC, bool Early = false>
+template <typename Real, int NT, int NS, int TC, bool Early = false, bool CH = false>
 int prepare_tiled(const swe::TileLayout& L) {
   constexpr bool comp = sizeof(Real) == 4;
-  auto k = swe::k_tiled_step<Real, comp, NT, NS, TC, Early>;
+  auto k = swe::k_tiled_step<Real, comp, NT, NS, TC, Early, CH>;
   // The limit is a property of the kernel, shared by every mesh that
   // launches it: set it to the device's largest opt-in size (not this
   // layout's), so that a later mesh with a smaller layout cannot lower it
@@ -207,6 +209,7 @@ int blocks_per_sm_tiled_nt(const swe_mesh* m) {
   if constexpr (sizeof(Real) == 4) {
     if (m->layout.pipe) return prepare_pipe<NT, TC>(m->layout);
     if (m->layout.early) return prepare_tiled<Real, NT, 2, TC, true>(m->layout);
+    if (m->prm.compensated_depth) return prepare_tiled<Real, NT, 2, TC, false, true>(m->layout);
   }
   return m->stages == 3 ? prepare_tiled<Real, NT, 3, TC>(m->layout)
                         : prepare_tiled<Real, NT, 2, TC>(m->layout);
@@ -257,6 +260,10 @@ void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe:
   }
   if constexpr (NT <= 256) {  // 512 threads exist only for the pipelined kernel
     if constexpr (sizeof(Real) == 4) {
+      if (ds.hlo) {  // compensated depth (2 stages, halo schedule 0)
+        cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, false, true>, dm, ds, num, L);
+        return;
+      }
       if (L.early) {
         cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, true>, dm, ds, num, L);
         return;
@@ -472,6 +479,7 @@ swe_status upload_state_fields(swe_state* s, const Host* h, const Host* hu, cons
                                bool on_device = false) {
   const Host* src[3] = {h, hu, hv};
   void* dst[3] = {s->h[0], s->hu[0], s->hv[0]};
+  if (s->hlo) CK(cudaMemsetAsync(s->hlo, 0, 4 * (size_t)s->mesh->Tp, s->mesh->stream));
   return put_fields<Host>(s, src, dst, s->stride, on_device);
 }
 
@@ -533,6 +541,10 @@ swe_status resolve_params(const swe_params* params, swe_params& p) {
   if (p.stages != 2 && p.stages != 3) return SWE_EINVAL;
   if (p.halo_schedule < 0 || p.halo_schedule > 2) return SWE_EINVAL;
   if (p.wait_rounds < -1) return SWE_EINVAL;
+  if (p.compensated_depth != 0 && p.compensated_depth != 1) return SWE_EINVAL;
+  if (p.compensated_depth &&
+      (p.precision != SWE_F32 || p.kernel == SWE_KERNEL_EDGE || p.stages != 2 || p.halo_schedule != 0))
+    return SWE_EINVAL;
   if (!(p.g > 0.0) || !(p.courant > 0.0) || !(p.h_eps >= 0.0)) return SWE_EINVAL;
   if (p.kernel == SWE_KERNEL_AUTO) p.kernel = SWE_KERNEL_TILED;
   return SWE_OK;
@@ -557,7 +569,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
   // records and 2 halo cells per cell at 512-cell tiles): the edge kernel
   // runs it faster (34 against 29 G cell-updates/s at 10M triangles, FP32).
   const bool autok = (params ? params->kernel : SWE_KERNEL_AUTO) == SWE_KERNEL_AUTO;
-  if (autok && n == 1 && p.order == SWE_ORDER_RCM) p.kernel = SWE_KERNEL_EDGE;
+  if (autok && n == 1 && p.order == SWE_ORDER_RCM && !p.compensated_depth) p.kernel = SWE_KERNEL_EDGE;
   const int kernel = p.kernel;
   if (kernel == SWE_KERNEL_EDGE && n > 1) return SWE_EINVAL;
   const int tile = p.tile;
@@ -981,6 +993,7 @@ void swe_params_default(swe_params* p) {
   p->cells_per_thread = 0;
   p->halo_schedule = 0;
   p->wait_rounds = 0;
+  p->compensated_depth = 0;
 }
 
 const char* swe_strerror(swe_status s) {
@@ -1085,6 +1098,8 @@ swe_status state_init(swe_mesh* m, const double* h, const double* hu, const doub
   if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) L.add(w * E);
   L.add(8 * (size_t)m->max_grid);
   L.add(8 * T);                                 // staging
+  const bool with_hlo = m->prm.compensated_depth != 0;
+  if (with_hlo) L.add(4 * Tp);                  // depth residual (FP32)
   L.add(sizeof(swe::Ctl) * n);
   if (cudaMalloc((void**)&s->arena.base, L.total) != cudaSuccess) {
     cudaGetLastError();
@@ -1117,6 +1132,7 @@ swe_status state_init(swe_mesh* m, const double* h, const double* hu, const doub
   if (m->kernel == SWE_KERNEL_EDGE) for (int k = 0; k < 5; ++k) s->fx[k] = s->arena.take(w * E);
   s->partial = (double*)s->arena.take(8 * (size_t)m->max_grid);
   s->stage = (double*)s->arena.take(8 * T);
+  if (with_hlo) s->hlo = s->arena.take(4 * Tp);
   s->ctl = (swe::Ctl*)s->arena.take(sizeof(swe::Ctl) * n);
   swe_status st = SWE_OK;
   if (s->arena.overflow) {
@@ -1265,12 +1281,12 @@ void launch_take(const swe_state* s, int b, int64_t c0, int64_t c1, Host* const 
   const int grid = grid_for(c1 - c0, 256, m->sms * 16);
   if (m->prm.precision == SWE_F64)
     swe::k_take_fields<double, Host><<<grid, 256, 0, m->stream>>>(
-        (const double*)s->h[b], (const double*)s->hu[b], (const double*)s->hv[b], m->iperm, c0, c1,
-        f[0], f[1], f[2], s->stride);
+        (const double*)s->h[b], (const double*)s->hu[b], (const double*)s->hv[b], nullptr,
+        m->iperm, c0, c1, f[0], f[1], f[2], s->stride);
   else
     swe::k_take_fields<float, Host><<<grid, 256, 0, m->stream>>>(
-        (const float*)s->h[b], (const float*)s->hu[b], (const float*)s->hv[b], m->iperm, c0, c1,
-        f[0], f[1], f[2], s->stride);
+        (const float*)s->h[b], (const float*)s->hu[b], (const float*)s->hv[b],
+        (const float*)s->hlo, m->iperm, c0, c1, f[0], f[1], f[2], s->stride);
 }
 
 // swe_copy_out[_f32] and swe_copy_out_device (to_device: h, hu, hv are

@@ -363,7 +363,8 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   if (!s || n_steps <= 0 || checkpoint_every <= 0 || n_gauges < 0 || (n_gauges > 0 && !gauge_cells))
     return SWE_EINVAL;
   swe_mesh* m = s->mesh;
-  if (m->kernel != SWE_KERNEL_TILED || nscen(m) != 1 || m->ghosts || m->tile / m->cpt > 256)
+  if (m->kernel != SWE_KERNEL_TILED || nscen(m) != 1 || m->ghosts || m->tile / m->cpt > 256 ||
+      m->prm.compensated_depth)
     return SWE_ESTATE;
   for (int j = 0; j < n_gauges; ++j)
     if (gauge_cells[j] < 0 || gauge_cells[j] >= m->T) return SWE_EINVAL;

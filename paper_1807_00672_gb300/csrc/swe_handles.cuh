@@ -97,6 +97,7 @@ struct swe_state {
   swe_host::Arena arena;
   void *h[2] = {nullptr, nullptr}, *hu[2] = {nullptr, nullptr}, *hv[2] = {nullptr, nullptr};
   void *z = nullptr, *gn2 = nullptr;
+  void* hlo = nullptr;  // FP32 depth residual per cell (compensated_depth), else null
   int stride = 1;  // 4: interleaved cells (h, hu, hv, z) for the tiled kernel
   void* fx[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double* partial = nullptr;
@@ -158,6 +159,7 @@ swe::DevState<Real> dev_state(const swe_state* s) {
   d.stride = s->stride;
   d.z = (const Real*)s->z;
   d.gn2 = (const Real*)s->gn2;
+  d.hlo = (Real*)s->hlo;
   for (int k = 0; k < 5; ++k) d.fx[k] = (Real*)s->fx[k];
   d.partial = s->partial;
   d.ctl = s->ctl;
@@ -168,8 +170,8 @@ swe::DevState<Real> dev_state(const swe_state* s) {
 // (0 if the query fails).
 int smem_optin_bytes();
 
-// One forward step of the mesh's kernel on explicitly given state buffers.
-// One step; back: walk every chunk's tiles last to first (same results).
+// One forward step of the mesh's kernel on explicitly given state buffers;
+// back: walk every chunk's tiles last to first (same results).
 void launch_forward(const swe_mesh* m, const swe::DevState<float>& ds, cudaStream_t st,
                     bool back = false);
 void launch_forward(const swe_mesh* m, const swe::DevState<double>& ds, cudaStream_t st,

@@ -148,6 +148,9 @@ struct DevState {
   int stride;
   const Real* z;
   const Real* gn2;  // g * n^2 per cell
+  // FP32 states with a depth residual (tiled kernel): per cell the part of
+  // h its FP32 value does not hold (h + hlo is the depth); else null
+  Real* hlo;
   // scratch
   Real* fx[5];      // two-launch face outputs: c0, cA1, cA2, cB1, cB2
   double* partial;  // per-block mass partial sums
@@ -647,18 +650,31 @@ __device__ __forceinline__ void face_flux_f64(const V4<double>& A, const V4<doub
 // next-step CFL rate. R: the residual (for Comp, the compensated face sum
 // rounded once, and U - a R is then one FMA). Writes the new state and
 // accumulates mass/rate. Recip: `area` holds 1 / area (a = dt / area is then
-// one product; no mass is accumulated).
-template <typename Real, bool Comp, typename Acc, bool Recip = false>
+// one product; no mass is accumulated). CH (FP32 with Comp): *lo is the
+// depth's residual, h + *lo the depth; the update h + *lo - a R[0] is
+// carried exactly up to the final rounding (the product's error from an
+// FMA, the sum's from TwoSum), and *lo receives what that rounding left, so
+// updates below half an ulp of h accumulate instead of being lost.
+template <typename Real, bool Comp, typename Acc, bool Recip = false, bool CH = false>
 __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area, Real irP, Real gn2,
                                             Real dt, const Real R[3], const Num& num, Real& h1,
                                             Real& hu1, Real& hv1, Acc& mass, Real& rate, Real& chk,
-                                            int& neg) {
+                                            int& neg, Real* lo = nullptr) {
   using O = Ops<Real>;
   const Real zero = Real(0);
   const Real a = Recip ? dt * area : O::div(dt, area);
   Real out[3];
   if constexpr (Comp && sizeof(Real) == 4) {
-    out[0] = fma_rn(-a, R[0], h);
+    if constexpr (CH) {
+      const float t = mul_rn(-a, R[0]);
+      const float e1 = fma_rn(-a, R[0], -t);  // -a R[0] = t + e1 exactly
+      float s0, e2;
+      two_sum(h, t, s0, e2);                   // h + t = s0 + e2 exactly
+      const float r = add_rn(*lo, add_rn(e1, e2));
+      two_sum(s0, r, out[0], *lo);             // new depth and residual
+    } else {
+      out[0] = fma_rn(-a, R[0], h);
+    }
     const float2 o = fma2(make_float2(-a, -a), make_float2(R[1], R[2]), make_float2(hu, hv));
     out[1] = o.x;
     out[2] = o.y;
@@ -668,7 +684,11 @@ __device__ __forceinline__ void cell_finish(Real h, Real hu, Real hv, Real area,
     for (int c = 0; c < 3; ++c) out[c] = Comp ? fma_rn(-a, R[c], U[c]) : U[c] - a * R[c];
   }
   Real hs = out[0], qx = out[1], qy = out[2];
-  if (hs < zero) { hs = zero; neg += 1; }
+  if (hs < zero) {
+    hs = zero;
+    neg += 1;
+    if constexpr (CH) *lo = zero;
+  }
   if (O::wet(hs, num)) {
     const Real q = O::sqrt_(qx * qx + qy * qy);
     const Real d = Real(1) + O::friction(dt, gn2, q, hs);
@@ -1038,8 +1058,9 @@ constexpr int tiled_min_blocks() { return (sizeof(Real) == 4 ? 768 : 512) / NT; 
 // NT threads per block, tiles of TC cells (a power of two, NT <= TC); a
 // thread updates the tile cells tid, tid + NT, ... (CPT = ceil(TC / NT)).
 // Early: a tile's halo gather is issued at the start of the previous tile's
-// iteration (launched only on layouts with hreg).
-template <typename Real, bool Comp, int NT, int NS, int TC, bool Early = false>
+// iteration (launched only on layouts with hreg). CH: FP32 with a depth
+// residual per cell (s.hlo, read and written by the cell's own thread).
+template <typename Real, bool Comp, int NT, int NS, int TC, bool Early = false, bool CH = false>
 __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     k_tiled_step(DevMesh<Real> m, DevState<Real> s, Num num, TileLayout L) {
   constexpr int CPT = (TC + NT - 1) / NT;
@@ -1291,7 +1312,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     const int nrec = s_nrec[st];
     // this thread's cells' area, perimeter/area and g n^2 (cell arrays are
     // padded to whole tiles, so the loads are always in bounds)
-    Real c_area[CPT], c_irP[CPT], c_gn2[CPT];
+    Real c_area[CPT], c_irP[CPT], c_gn2[CPT], c_lo[CPT];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) {
       const int j = tid + cc * NT;
@@ -1299,6 +1320,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       c_area[cc] = kVel ? m.rarea[base + j] : m.area[base + j];  // FP64: 1 / area
       c_irP[cc] = m.irP[base + j];
       c_gn2[cc] = s.gn2[base + j];
+      if constexpr (CH) c_lo[cc] = s.hlo[base + j];
     }
 
     // face records, the highest threads first: a partial last round falls
@@ -1404,9 +1426,11 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       // FP64: the staged cell holds (h, u, v, z); its (hu, hv) are in registers
       const Real qx = kVel ? own_q[cc][0] : c.y, qy = kVel ? own_q[cc][1] : c.z;
       Real a1, b1, c1;
-      cell_finish<Real, Comp, NoMass<Real>, kVel>(c.x, qx, qy, c_area[cc], c_irP[cc], c_gn2[cc], dt,
-                                                  R, num, a1, b1, c1, mass, rate, chk, neg);
+      cell_finish<Real, Comp, NoMass<Real>, kVel, CH>(c.x, qx, qy, c_area[cc], c_irP[cc],
+                                                      c_gn2[cc], dt, R, num, a1, b1, c1, mass,
+                                                      rate, chk, neg, &c_lo[cc]);
       st4(U1 + 4 * (int64_t)(base + j), a1, b1, c1, c.w);
+      if constexpr (CH) s.hlo[base + j] = c_lo[cc];
     }
     if constexpr (kVel) {
 #pragma unroll
@@ -1739,7 +1763,10 @@ __global__ void __launch_bounds__(256) k_cfl_tiled(DevMesh<Real> m, DevState<Rea
         rate = fmax(rate, lam * m.irP[i]);
       }
       if (!isfinite(hh + qx + qy)) bad = 1;
-      if (m.irP[i] != Real(0)) mass.add(m.area[i], hh);  // 0: a ghost (or padding) cell
+      if (m.irP[i] != Real(0)) {  // 0: a ghost (or padding) cell
+        mass.add(m.area[i], hh);
+        if (s.hlo) mass.add(m.area[i], s.hlo[i]);  // the depth's residual
+      }
     }
   }
   finish_launch<256>(ctl, s.partial, ch.part, ctl->part0, (int)ctl->nparts, mass.value(),

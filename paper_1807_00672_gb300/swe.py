@@ -57,6 +57,7 @@ class Params(ctypes.Structure):
         ("cells_per_thread", ctypes.c_int32),
         ("halo_schedule", ctypes.c_int32),
         ("wait_rounds", ctypes.c_int32),
+        ("compensated_depth", ctypes.c_int32),
     ]
 
 
@@ -161,7 +162,8 @@ def _check(status: int, what: str):
 
 
 def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, courant=0.7,
-           h_eps=1e-6, stages=0, cells_per_thread=0, halo_schedule=0, wait_rounds=0) -> Params:
+           h_eps=1e-6, stages=0, cells_per_thread=0, halo_schedule=0, wait_rounds=0,
+           compensated_depth=False) -> Params:
     p = Params()
     lib().swe_params_default(ctypes.byref(p))
     p.g, p.courant, p.h_eps = g, courant, h_eps
@@ -173,6 +175,7 @@ def params(precision="f64", order="morton", kernel="auto", tile=0, g=9.81, coura
     p.cells_per_thread = cells_per_thread
     p.halo_schedule = halo_schedule
     p.wait_rounds = wait_rounds
+    p.compensated_depth = int(compensated_depth)
     return p
 
 
@@ -193,28 +196,29 @@ class Mesh:
 
     def __init__(self, xy, tri, *, precision="f64", order="morton", kernel="auto", tile=0,
                  stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6,
-                 halo_schedule=0, wait_rounds=0):
+                 halo_schedule=0, wait_rounds=0, compensated_depth=False):
         self._build([(xy, tri)], precision, order, kernel, tile, stages, cells_per_thread,
                     stream, g, courant, h_eps, batch=False, halo_schedule=halo_schedule,
-                    wait_rounds=wait_rounds)
+                    wait_rounds=wait_rounds, compensated_depth=compensated_depth)
 
     @classmethod
     def ensemble(cls, meshes, *, precision="f64", order="morton", kernel="auto", tile=0,
                  stages=0, cells_per_thread=0, stream=None, g=9.81, courant=0.7, h_eps=1e-6,
-                 halo_schedule=0):
+                 halo_schedule=0, compensated_depth=False):
         """One mesh holding the scenarios ``meshes`` = [(xy, tri), ...]; cell
         arrays are the scenarios' cells concatenated in this order."""
         self = cls.__new__(cls)
         self._build(list(meshes), precision, order, kernel, tile, stages, cells_per_thread,
-                    stream, g, courant, h_eps, batch=True, halo_schedule=halo_schedule)
+                    stream, g, courant, h_eps, batch=True, halo_schedule=halo_schedule,
+                    compensated_depth=compensated_depth)
         return self
 
     def _build(self, meshes, precision, order, kernel, tile, stages, cpt, stream, g, courant,
-               h_eps, batch, halo_schedule=0, wait_rounds=0):
+               h_eps, batch, halo_schedule=0, wait_rounds=0, compensated_depth=False):
         xys = [_f64(xy).reshape(-1, 2) for xy, _ in meshes]
         tris = [np.ascontiguousarray(t, dtype=np.int32).reshape(-1, 3) for _, t in meshes]
         self.prm = params(precision, order, kernel, tile, g, courant, h_eps, stages, cpt,
-                          halo_schedule, wait_rounds)
+                          halo_schedule, wait_rounds, compensated_depth)
         self.precision = precision
         h = ctypes.c_void_p()
         if batch:

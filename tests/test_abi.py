@@ -89,7 +89,8 @@ def test_invalid_meshes_rejected_on_the_host(L, bad):
 
 @pytest.mark.parametrize("field,val", [("precision", 7), ("order", 5), ("kernel", 9), ("tile", 100),
                                        ("stages", 5), ("cells_per_thread", 3),
-                                       ("halo_schedule", 3), ("wait_rounds", -2)])
+                                       ("halo_schedule", 3), ("wait_rounds", -2),
+                                       ("compensated_depth", 2), ("compensated_depth", 1)])
 def test_bad_params_rejected(L, field, val):
     m = inputs.jittered_grid(3, 3, 3.0, 3.0)
     p = swe.params()
