@@ -18,7 +18,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <numeric>
+#include <thread>
 
 namespace swe {
 
@@ -150,8 +152,158 @@ std::vector<int32_t> rcm_order(int64_t T, const std::vector<int32_t>& nbr) {
   return order;
 }
 
+namespace {
+
+// Shared-memory accesses of one face record in the FP32 tiled step, in
+// 16-byte units: the loads of its two cells (A, B) and the stores of its
+// face slots on the sides that are tile cells. Wall and padding records
+// (side B a wall) run another branch of the loop and are left out.
+struct RecAccess {
+  int32_t addr[4];
+  bool on[4];
+};
+
+RecAccess rec_access(int32_t a, int32_t b, int tile) {
+  RecAccess r{};
+  const bool body = b != kWall;
+  auto cell = [&](int32_t c) { return c < 0 ? ((-1 - c) & (tile - 1)) : c; };
+  auto slot = [&](int32_t c) {
+    const int s = -1 - c;
+    return s + (s / tile) * kRecordSlotPad;
+  };
+  r.on[0] = r.on[1] = body;
+  r.addr[0] = body ? cell(a) : 0;
+  r.addr[1] = body ? cell(b) : 0;
+  r.on[2] = body && a < 0;
+  r.addr[2] = r.on[2] ? slot(a) : 0;
+  r.on[3] = body && b < 0;
+  r.addr[3] = r.on[3] ? slot(b) : 0;
+  return r;
+}
+
+// The accesses of the records placed in one block of eight so far: per
+// access and bank group (16-byte address mod 8) the distinct addresses. An
+// access of the block takes as many shared-memory wavefronts as its fullest
+// group holds addresses (one when all differ in group or coincide).
+struct BlockBanks {
+  int32_t seen[4][8][8];
+  int8_t n[4][8];
+  int8_t mx[4];
+  void clear() {
+    std::memset(n, 0, sizeof(n));
+    std::memset(mx, 0, sizeof(mx));
+  }
+  bool has(int k, int g, int32_t addr) const {
+    for (int i = 0; i < n[k][g]; ++i)
+      if (seen[k][g][i] == addr) return true;
+    return false;
+  }
+  // wavefronts the record would add to the block
+  int cost(const RecAccess& r) const {
+    int c = 0;
+    for (int k = 0; k < 4; ++k) {
+      if (!r.on[k]) continue;
+      const int g = r.addr[k] & 7;
+      if (!has(k, g, r.addr[k]) && n[k][g] + 1 > mx[k]) c += 1;
+    }
+    return c;
+  }
+  void add(const RecAccess& r) {
+    for (int k = 0; k < 4; ++k) {
+      if (!r.on[k]) continue;
+      const int g = r.addr[k] & 7;
+      if (has(k, g, r.addr[k])) continue;
+      seen[k][g][n[k][g]++] = r.addr[k];
+      if (n[k][g] > mx[k]) mx[k] = n[k][g];
+    }
+  }
+};
+
+// Record classes of the stored order: 0 both cells in the tile, 1 a halo
+// side, 2 wall or padding.
+int rec_class(int32_t a, int32_t b) { return b == kWall ? 2 : (a >= 0 || b >= 0) ? 1 : 0; }
+
+// New order of records [r0, r1) of one tile: the kernel deals record r to
+// the thread whose quarter warp takes the aligned block of eight r / 8, so
+// each block is filled greedily, in order, with the first of the next
+// kWindow unplaced records of the current class that adds no wavefront (or,
+// if none, the one that adds the fewest). Classes stay contiguous and in
+// their order; within a class the records stay close to their cell order.
+void bank_order(const std::vector<int32_t>& tA, const std::vector<int32_t>& tB, int64_t r0,
+                int64_t r1, int tile, std::vector<int32_t>& order) {
+  constexpr size_t kWindow = 128;
+  order.clear();
+  BlockBanks bb;
+  bb.clear();
+  std::vector<char> used;
+  int64_t i = r0;
+  while (i < r1) {
+    int64_t j = i;
+    while (j < r1 && rec_class(tA[j], tB[j]) == rec_class(tA[i], tB[i])) ++j;
+    used.assign((size_t)(j - i), 0);
+    size_t head = 0;
+    for (int64_t placed = 0; placed < j - i; ++placed) {
+      if (order.size() % 8 == 0) bb.clear();
+      while (used[head]) ++head;
+      size_t best = head, seen = 0;
+      int best_cost = 1 << 30;
+      for (size_t k = head; k < used.size() && seen < kWindow; ++k) {
+        if (used[k]) continue;
+        ++seen;
+        const int c = bb.cost(rec_access(tA[i + k], tB[i + k], tile));
+        if (c < best_cost) {
+          best_cost = c;
+          best = k;
+          if (c == 0) break;
+        }
+      }
+      used[best] = 1;
+      bb.add(rec_access(tA[i + best], tB[i + best], tile));
+      order.push_back((int32_t)(i + best));
+    }
+    i = j;
+  }
+}
+
+// Applies bank_order to every tile of m (host threads over tiles).
+void order_records_for_banks(HostMesh& m) {
+  const int64_t nt = m.ntiles;
+  unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (m.T < 200000) nth = 1;
+  auto work = [&](int64_t t0, int64_t t1) {
+    std::vector<int32_t> order;
+    std::vector<int32_t> a, b;
+    std::vector<double> x, y, l;
+    for (int64_t t = t0; t < t1; ++t) {
+      const int64_t r0 = m.toff[t], r1 = m.toff[t + 1];
+      bank_order(m.tA, m.tB, r0, r1, m.tile, order);
+      a.resize(order.size()); b.resize(order.size());
+      x.resize(order.size()); y.resize(order.size()); l.resize(order.size());
+      for (size_t q = 0; q < order.size(); ++q) {
+        const int32_t r = order[q];
+        a[q] = m.tA[r]; b[q] = m.tB[r]; x[q] = m.tnx[r]; y[q] = m.tny[r]; l[q] = m.tlen[r];
+      }
+      std::copy(a.begin(), a.end(), m.tA.begin() + r0);
+      std::copy(b.begin(), b.end(), m.tB.begin() + r0);
+      std::copy(x.begin(), x.end(), m.tnx.begin() + r0);
+      std::copy(y.begin(), y.end(), m.tny.begin() + r0);
+      std::copy(l.begin(), l.end(), m.tlen.begin() + r0);
+    }
+  };
+  if (nth == 1) {
+    work(0, nt);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (unsigned k = 0; k < nth; ++k)
+    pool.emplace_back(work, nt * k / nth, nt * (k + 1) / nth);
+  for (std::thread& th : pool) th.join();
+}
+
+}  // namespace
+
 int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t T, int order,
-                    int32_t tile, bool with_edges, HostMesh& m) {
+                    int32_t tile, bool with_edges, HostMesh& m, bool bank) {
   if (!xy || !tri_in || V <= 0 || T <= 0) return T == 0 ? -2 : -1;
   if (T >= (int64_t)INT32_MAX / 3 || V >= (int64_t)INT32_MAX) return -1;
   m = HostMesh();
@@ -405,6 +557,7 @@ int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t 
       m.halo_cap = std::max<int64_t>(m.halo_cap, (int64_t)nh);
     }
     if (m.halo_cap == 0) m.halo_cap = 4;
+    if (bank) order_records_for_banks(m);
   }
   return 0;
 }

@@ -53,11 +53,20 @@ std::vector<int32_t> morton_order(const double* xy, int64_t V, const int32_t* tr
 // ties), the whole sequence reversed. order[j] = the cell at position j.
 std::vector<int32_t> rcm_order(int64_t T, const std::vector<int32_t>& nbr);
 
+// Offset, in slots, between the face slots of consecutive faces k of the
+// FP32 tiled step (face k of tile cell j at k (tile + pad) + j); the same
+// value as the kernels' kSlotPad, which the record order below models.
+constexpr int kRecordSlotPad = 3;
+
 // Returns 0 or a negative status: -1 bad arguments, -2 invalid mesh.
 // order: 0 = caller order, 1 = Morton order of centroids, 2 = reverse
 // Cuthill-McKee order of the edge-neighbour graph.
 // tile > 0 also builds the tiled layout; with_edges builds the two-launch one.
+// bank_order (FP32 tiled step): within each class of a tile's records, the
+// records are reordered so that the eight records one quarter warp handles
+// at a time spread their shared-memory accesses over the banks (see
+// order_records_for_banks); results do not depend on the order.
 int build_host_mesh(const double* xy, int64_t V, const int32_t* tri, int64_t T, int order,
-                    int32_t tile, bool with_edges, HostMesh& out);
+                    int32_t tile, bool with_edges, HostMesh& out, bool bank_order = false);
 
 }  // namespace swe

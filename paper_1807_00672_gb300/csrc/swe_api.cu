@@ -26,6 +26,8 @@
 
 namespace swe {
 
+static_assert(kRecordSlotPad == kSlotPad, "the host record order models the kernels' face slots");
+
 // Sets the end time of every scenario and re-clamps its next dt.
 __global__ void k_set_end(Ctl* ctls, int n, double t_end) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -586,7 +588,8 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
       for (int i = next++; i < n; i = next++)
         rc[i] = swe::build_host_mesh(xy[i], n_nodes[i], tri[i], n_tris[i], p.order,
                                      kernel == SWE_KERNEL_TILED ? tile : 0,
-                                     kernel == SWE_KERNEL_EDGE, hm[i]);
+                                     kernel == SWE_KERNEL_EDGE, hm[i],
+                                     kernel == SWE_KERNEL_TILED && p.precision == SWE_F32);
     };
     std::vector<std::thread> pool;
     for (int k = 1; k < nthr; ++k) pool.emplace_back(work);
