@@ -294,9 +294,15 @@ void order_records_for_banks(HostMesh& m) {
     work(0, nt);
     return;
   }
+  // Ranges whose thread cannot be started are done on this thread.
   std::vector<std::thread> pool;
-  for (unsigned k = 0; k < nth; ++k)
-    pool.emplace_back(work, nt * k / nth, nt * (k + 1) / nth);
+  unsigned started = 0;
+  try {
+    for (; started < nth; ++started)
+      pool.emplace_back(work, nt * started / nth, nt * (started + 1) / nth);
+  } catch (...) {
+  }
+  for (unsigned k = started; k < nth; ++k) work(nt * k / nth, nt * (k + 1) / nth);
   for (std::thread& th : pool) th.join();
 }
 
