@@ -592,7 +592,10 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
                                      kernel == SWE_KERNEL_TILED && p.precision == SWE_F32);
     };
     std::vector<std::thread> pool;
-    for (int k = 1; k < nthr; ++k) pool.emplace_back(work);
+    try {  // the calling thread takes every scenario no worker takes
+      for (int k = 1; k < nthr; ++k) pool.emplace_back(work);
+    } catch (...) {
+    }
     work();
     for (auto& t : pool) t.join();
   }
