@@ -573,10 +573,12 @@ int build_host_mesh(const double* xy, int64_t V, const int32_t* tri_in, int64_t 
 extern "C" swe_status swe_cell_order(const double* xy, int64_t n_nodes, const int32_t* tri,
                                      int64_t n_tris, int32_t order, int32_t* perm) {
   if (!perm || order < SWE_ORDER_NONE || order > SWE_ORDER_RCM) return SWE_EINVAL;
-  swe::HostMesh hm;
-  const int rc = swe::build_host_mesh(xy, n_nodes, tri, n_tris, order, 0, false, hm);
-  if (rc == -2) return SWE_EMESH;
-  if (rc != 0) return SWE_EINVAL;
-  std::copy(hm.perm.begin(), hm.perm.end(), perm);
-  return SWE_OK;
+  return swe::guarded([&] {
+    swe::HostMesh hm;
+    const int rc = swe::build_host_mesh(xy, n_nodes, tri, n_tris, order, 0, false, hm);
+    if (rc == -2) return SWE_EMESH;
+    if (rc != 0) return SWE_EINVAL;
+    std::copy(hm.perm.begin(), hm.perm.end(), perm);
+    return SWE_OK;
+  });
 }

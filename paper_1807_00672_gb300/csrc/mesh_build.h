@@ -3,9 +3,24 @@
 #pragma once
 
 #include <cstdint>
+#include <new>
 #include <vector>
 
 namespace swe {
+
+// Runs a C-ABI call's body so that no C++ exception crosses the boundary:
+// std::bad_alloc becomes status -3 (SWE_ENOMEM), any other exception -1
+// (SWE_EINVAL).
+template <typename F>
+int guarded(F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return -3;
+  } catch (...) {
+    return -1;
+  }
+}
 
 // Encoding of one side of a tile face record:
 //   >= 0             tile + q for the cell of another tile at index q of the

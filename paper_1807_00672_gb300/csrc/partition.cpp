@@ -50,8 +50,8 @@ int64_t local_index(const swe_partition::Part& p, int32_t c) {
 
 extern "C" {
 
-swe_status swe_partition_create(const double* xy, int64_t n_nodes, const int32_t* tri,
-                                int64_t n_tris, int32_t n_parts, swe_partition** out) {
+static swe_status partition_create(const double* xy, int64_t n_nodes, const int32_t* tri,
+                                   int64_t n_tris, int32_t n_parts, swe_partition** out) {
   if (!out) return SWE_EINVAL;
   *out = nullptr;
   if (!xy || !tri || n_nodes <= 0 || n_tris < 0 || n_parts < 1) return SWE_EINVAL;
@@ -138,6 +138,12 @@ swe_status swe_partition_create(const double* xy, int64_t n_nodes, const int32_t
   }
   *out = P;
   return SWE_OK;
+}
+
+swe_status swe_partition_create(const double* xy, int64_t n_nodes, const int32_t* tri,
+                                int64_t n_tris, int32_t n_parts, swe_partition** out) {
+  if (out) *out = nullptr;
+  return swe::guarded([&] { return partition_create(xy, n_nodes, tri, n_tris, n_parts, out); });
 }
 
 swe_status swe_partition_sizes(const swe_partition* P, int32_t part, int64_t* sizes) {

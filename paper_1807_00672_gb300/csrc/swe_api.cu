@@ -1021,7 +1021,7 @@ const char* swe_last_cuda_error(void) { return g_cuda_msg.c_str(); }
 
 swe_status swe_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tris,
                            const swe_params* params, void* cuda_stream, swe_mesh** out) {
-  return create_batch(1, &xy, &n_nodes, &tri, &n_tris, params, cuda_stream, out);
+  return swe::guarded([&] { return create_batch(1, &xy, &n_nodes, &tri, &n_tris, params, cuda_stream, out); });
 }
 
 swe_status swe_mesh_create_part(const double* xy, int64_t n_nodes, const int32_t* tri,
@@ -1034,7 +1034,7 @@ swe_status swe_mesh_create_part(const double* xy, int64_t n_nodes, const int32_t
   swe_status st = resolve_params(params, p);
   if (st != SWE_OK) return st;
   if (p.kernel != SWE_KERNEL_TILED) return SWE_EINVAL;
-  st = create_batch(1, &xy, &n_nodes, &tri, &n_tris, &p, cuda_stream, out, ghost);
+  st = swe::guarded([&] { return create_batch(1, &xy, &n_nodes, &tri, &n_tris, &p, cuda_stream, out, ghost); });
   if (st == SWE_OK) (*out)->ghosts = true;
   return st;
 }
@@ -1043,7 +1043,8 @@ swe_status swe_mesh_create_batch(int32_t n_scenarios, const double* const* xy,
                                  const int64_t* n_nodes, const int32_t* const* tri,
                                  const int64_t* n_tris, const swe_params* params,
                                  void* cuda_stream, swe_mesh** out) {
-  return create_batch(n_scenarios, xy, n_nodes, tri, n_tris, params, cuda_stream, out);
+  return swe::guarded(
+      [&] { return create_batch(n_scenarios, xy, n_nodes, tri, n_tris, params, cuda_stream, out); });
 }
 
 swe_status swe_mesh_counts(const swe_mesh* m, int64_t* counts) {
@@ -1197,13 +1198,15 @@ extern "C" {
 swe_status swe_state_init(swe_mesh* m, const double* h, const double* hu, const double* hv,
                           const double* z, const double* manning, double manning_const,
                           swe_state** out) {
-  return state_init(m, h, hu, hv, z, manning, manning_const, false, nullptr, out);
+  return swe::guarded(
+      [&] { return state_init(m, h, hu, hv, z, manning, manning_const, false, nullptr, out); });
 }
 
 swe_status swe_state_init_device(swe_mesh* m, const double* h, const double* hu, const double* hv,
                                  const double* z, const double* manning, double manning_const,
                                  void* cuda_stream, swe_state** out) {
-  return state_init(m, h, hu, hv, z, manning, manning_const, true, cuda_stream, out);
+  return swe::guarded(
+      [&] { return state_init(m, h, hu, hv, z, manning, manning_const, true, cuda_stream, out); });
 }
 
 swe_status swe_state_set(swe_state* s, const double* h, const double* hu, const double* hv) {

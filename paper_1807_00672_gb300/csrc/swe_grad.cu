@@ -22,6 +22,7 @@
 
 #include "../../include/swe.h"
 #include "swe_adjoint.cuh"
+#include "mesh_build.h"
 #include "swe_handles.cuh"
 #include "swe_kernels.cuh"
 
@@ -351,13 +352,9 @@ swe_status grad_t(swe_tape* t, bool seeds_gauge, int* lam_cur) {
   return SWE_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_every,
-                           const int32_t* gauge_cells, int32_t n_gauges, double* gauge_h,
-                           swe_tape** out) {
+swe_status grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_every,
+                       const int32_t* gauge_cells, int32_t n_gauges, double* gauge_h,
+                       swe_tape** out) {
   if (!out) return SWE_EINVAL;
   *out = nullptr;
   if (!s || n_steps <= 0 || checkpoint_every <= 0 || n_gauges < 0 || (n_gauges > 0 && !gauge_cells))
@@ -511,9 +508,6 @@ swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_eve
   return SWE_OK;
 }
 
-}  // extern "C"
-
-namespace {
 
 // swe_grad and swe_grad_device: seeds and outputs in host memory, or
 // (on_device) in device memory ordered on caller_stream.
@@ -597,6 +591,14 @@ swe_status grad(swe_tape* t, const double* g_h, const double* g_hu, const double
 }  // namespace
 
 extern "C" {
+
+swe_status swe_grad_record(swe_state* s, int64_t n_steps, int64_t checkpoint_every,
+                           const int32_t* gauge_cells, int32_t n_gauges, double* gauge_h,
+                           swe_tape** out) {
+  if (out) *out = nullptr;
+  return swe::guarded(
+      [&] { return grad_record(s, n_steps, checkpoint_every, gauge_cells, n_gauges, gauge_h, out); });
+}
 
 swe_status swe_grad(swe_tape* t, const double* g_h, const double* g_hu, const double* g_hv,
                     const double* g_gauge, double* d_h0, double* d_hu0, double* d_hv0, double* d_z,
