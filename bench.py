@@ -920,6 +920,8 @@ def summary(out):
         a = out["adjoint"]
         s["adjoint_backward_over_forward"] = {p: r(a[p]["backward_over_forward"])
                                               for p in ("f32", "f64") if p in a}
+        s["adjoint_hbm_frac_est"] = {p: r(a[p].get("adjoint_hbm_frac_est"))
+                                     for p in ("f32", "f64") if p in a}
         s["adjoint_f32_vs_f64_rel_n"] = {"own_seeds": r(a.get("f32_vs_f64_rel_n")),
                                          "f64_seeds": r(a.get("f32_adjoint_f64_seeds_rel_n"))}
     if "error" in out:
