@@ -737,6 +737,8 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     L.add(4 * H);
     L.add(sizeof(swe::Chunk) * C);
     L.add(sizeof(swe::Chunk) * C);  // the same chunks walked backwards
+    L.add(sizeof(swe::Chunk) * C);  // the step's chunks with tile pools, forwards
+    L.add(sizeof(swe::Chunk) * C);  // and backwards
     if (m->layout.hreg) L.add(4 * tiles * (int64_t)m->layout.halo_cap);
   }
   if (cudaMalloc((void**)&m->arena.base, L.total) != cudaSuccess) {
@@ -774,6 +776,8 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     m->hidx = (int32_t*)m->arena.take(4 * H);
     m->chunks = (swe::Chunk*)m->arena.take(sizeof(swe::Chunk) * C);
     m->chunks_back = (swe::Chunk*)m->arena.take(sizeof(swe::Chunk) * C);
+    m->chunks_pool = (swe::Chunk*)m->arena.take(sizeof(swe::Chunk) * C);
+    m->chunks_pool_back = (swe::Chunk*)m->arena.take(sizeof(swe::Chunk) * C);
     if (m->layout.hreg)
       m->hpad = (int32_t*)m->arena.take(4 * tiles * (int64_t)m->layout.halo_cap);
   }
@@ -882,6 +886,35 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
       c.stride = -c.stride;
     }
     chk(upload(m, back, m->chunks_back));
+    // The step's tables: the blocks of one SM progress at different speeds
+    // (the warp scheduler favours the oldest; on the 10M mesh the three
+    // blocks of an SM end their equal shares about 109, 114 and 127 us into
+    // a step), so a chunk keeps the tiles of all but the last kPoolWaves
+    // waves of its scenario's walk and those last waves form the scenario's
+    // pool, from which the faster blocks take more tiles. Each pool entry
+    // costs an atomic on one address; measured best at 3 waves (a pool of
+    // every tile was 1.6 % slower than none).
+    constexpr int64_t kPoolWaves = 3;
+    std::vector<swe::Chunk> pooled(chunks), pooled_back(back);
+    for (size_t q = 0; q < chunks.size(); ++q) {
+      const Scenario& sc = m->scen[chunks[q].scen];
+      const int64_t S = sc.nchunks, N = sc.ntiles, ns = m->stages;
+      const int64_t W = std::max<int64_t>(ns, N / S - kPoolWaves);  // static tiles per chunk
+      if (N < (ns + 2) * S || W * S >= N) continue;
+      const int64_t r = chunks[q].tile0 - sc.tile0;
+      swe::Chunk& f = pooled[q];
+      f.ntiles = (int32_t)W;
+      f.pool_first = (int32_t)(sc.tile0 + W * S);
+      f.pool_count = (int32_t)(N - W * S);
+      swe::Chunk& b = pooled_back[q];
+      b.tile0 = (int32_t)(sc.tile0 + N - 1 - r);
+      b.ntiles = (int32_t)W;
+      b.stride = -(int32_t)S;
+      b.pool_first = (int32_t)(sc.tile0 + N - 1 - W * S);
+      b.pool_count = (int32_t)(N - W * S);
+    }
+    chk(upload(m, pooled, m->chunks_pool));
+    chk(upload(m, pooled_back, m->chunks_pool_back));
     if (m->layout.hreg) {
       // tile t's halo list at t * halo_cap, padded with the tile's first cell
       const int64_t hc = m->layout.halo_cap;
@@ -947,7 +980,10 @@ static void launch_forward_t(const swe_mesh* m, const swe::DevState<Real>& ds, c
                              bool back) {
   constexpr bool comp = sizeof(Real) == 4;
   swe::DevMesh<Real> dm = dev_mesh<Real>(m);
-  if (back && m->chunks_back) dm.chunks = m->chunks_back;
+  if (m->kernel == SWE_KERNEL_TILED && !m->layout.pipe)  // k_tiled_step: the pooled tables
+    dm.chunks = back ? m->chunks_pool_back : m->chunks_pool;
+  else if (back && m->chunks_back)
+    dm.chunks = m->chunks_back;
   const swe::Num num = num_of(m);
   if (m->kernel == SWE_KERNEL_EDGE) {
     swe::k_edge_flux<Real><<<m->grid_edge, 256, 0, st>>>(dm, ds, num);

@@ -46,6 +46,7 @@ struct Ctl {
   int clamped;       // dt == t_end - t
   int err;           // latched error bits
   unsigned int ticket;  // blocks of this scenario finished in the current launch
+  unsigned int pool_next;  // next free entry of the step's tile pool (see Chunk)
   int subdomain;     // 1: a sub-domain of a decomposed mesh (its CFL step may be
                      // +inf when none of its own cells is wet; not an error here)
 };
@@ -91,12 +92,19 @@ inline Num make_num(double g, double courant, double h_eps, int32_t wait = 0) {
 // at any moment sweep neighbouring tiles together and a tile's halo cells
 // are mostly still in L2 from the neighbours' copies. The same chunks walked
 // backwards (tile0 the last tile, stride negative) serve every other step.
-// part: the chunk's
+// The step's own tables add a pool: a block works its ntiles tiles, then
+// takes further tiles one at a time from its scenario's pool, the
+// pool_count tiles pool_first, pool_first + 1, ... (in the walk's direction,
+// pool_first - 1, ... for a negative stride) in the order blocks ask for
+// them (Ctl::pool_next), so that the blocks of an SM, which the warp
+// scheduler does not serve equally, finish closer together. A pooled
+// chunk keeps at least NS static tiles (those fetched before the
+// dependency wait). part: the chunk's
 // mass partial slot (the scenario's slots are contiguous from its
 // control word's part0).
 struct Chunk {
   int32_t scen, tile0, ntiles, stride;
-  int32_t part, cell_end, pad0, pad1;
+  int32_t part, cell_end, pool_first, pool_count;
 };
 
 template <typename Real>
@@ -782,6 +790,7 @@ __device__ void finish_launch(Ctl* ctl, double* partial, long long part, long lo
     ctl->nparts = nblocks;
     const unsigned long long bits = atomicExch(&ctl->rate_bits, 0ull);
     ctl->ticket = 0u;
+    ctl->pool_next = 0u;  // every block has taken its last tile
     if (kind == kMassOnly) return;  // errors this launch saw are latched above
     double t = ctl->t;
     if (stepped) {
@@ -1075,16 +1084,43 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   constexpr int CPT = (TC + NT - 1) / NT;
   static_assert((TC & (TC - 1)) == 0 && NT <= TC && NT % 32 == 0, "tile shape");
   __shared__ int s_nrec[NS], s_nh[NS];  // record and halo counts of each stage's tile
+  __shared__ int s_tile[8];  // tile of iteration j in slot j & 7 (-1: none), written by thread 0
   extern __shared__ __align__(128) unsigned char smem[];
   Real* slots = reinterpret_cast<Real*>(smem + L.off_slots);  // [3 (TC + kSlotPad)][4]
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bars);
 
-  // This block's work: tiles t_first + k t_step (k < n_tiles) of one scenario.
+  // This block's work: tiles t_first + k t_step (k < n_tiles) of one scenario,
+  // then tiles from the scenario's pool (see Chunk).
   const Chunk ch = m.chunks[blockIdx.x];
   const int t_first = ch.tile0, n_tiles = ch.ntiles, t_step = ch.stride;
+  const int pool_first = ch.pool_first, pool_count = ch.pool_count;
   const int cell_end = ch.cell_end;
   Ctl* ctl = s.ctl + ch.scen;
   const int tid = threadIdx.x;
+  // Thread 0 takes pool entries in iteration order, only after pdl_wait (the
+  // previous step's last block resets the pool): entries for iterations
+  // 0..3 in one atomic before the first tile, then the entry of iteration
+  // k + 4 with an atomic issued at the start of iteration k whose result is
+  // first used at its end, so that its latency is hidden. Once the pool is
+  // empty every later iteration gets -1.
+  bool exhausted = pool_count <= 0;
+  unsigned int q_next = 0u;
+  auto pool_tile = [&](unsigned int q) -> int {
+    return t_step > 0 ? pool_first + (int)q : pool_first - (int)q;
+  };
+  // Thread 0: the tile of iteration j >= 4 at the end of iteration j - 4
+  // (its pool entry, if any, taken with the atomic issued at its start).
+  auto publish = [&](int j) {
+    int t = -1;
+    if (j < n_tiles) {
+      t = t_first + j * t_step;
+    } else if (!exhausted && q_next < (unsigned int)pool_count) {
+      t = pool_tile(q_next);
+    } else {
+      exhausted = true;
+    }
+    s_tile[j & 7] = t;
+  };
   // The state and the control word are read only after pdl_wait (they are
   // the previous step's output); mesh data may be fetched before it.
   const Real* __restrict__ U = nullptr;  // interleaved cells (h, hu, hv, z)
@@ -1263,6 +1299,22 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
 #pragma unroll
     for (int i = 0; i < NS - 1; ++i)
       if (i < n_tiles) issue_cells(i, t_first + i * t_step);
+    // the tiles of iterations 0..3: static ones, then pool entries taken
+    // with one atomic
+    const int ndyn = n_tiles >= 4 ? 0 : 4 - n_tiles;
+    const unsigned int q0 = (!exhausted && ndyn > 0) ? atomicAdd(&ctl->pool_next, (unsigned int)ndyn) : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int t = -1;
+      if (j < n_tiles) {
+        t = t_first + j * t_step;
+      } else if (!exhausted && q0 + (unsigned int)(j - n_tiles) < (unsigned int)pool_count) {
+        t = pool_tile(q0 + (unsigned int)(j - n_tiles));
+      } else {
+        exhausted = true;
+      }
+      s_tile[j] = t;
+    }
     if (NS - 1 < n_tiles) load_offsets(t_first + (NS - 1) * t_step);
   }
   if (n_tiles > 0) {
@@ -1288,15 +1340,25 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   // Each iteration: the face records of tile k, then the cell updates of
   // tile k while tile k+1's halo gather is in flight (with `early`, issued
   // before the face records). Two block barriers.
-  for (int k = 0; !timeout && k < n_tiles; ++k) {
+  // Every thread keeps the tiles of iterations k, k + 1 and k + 2 (from the
+  // ring, published at least one barrier earlier).
+  int tile_c = s_tile[0], tile_n = s_tile[1], tile_n2 = s_tile[2];
+  for (int k = 0; !timeout; ++k) {
+    const int tile = tile_c;
+    if (tile < 0) break;
     const int st = k % NS;
-    const int tile = t_first + k * t_step;
-    const bool has_next = k + 1 < n_tiles;
+    const bool has_next = tile_n >= 0;
+    // the pool entry of iteration k + 4 (published at the end of this one)
+    if (tid == 0 && !exhausted && k + 4 >= n_tiles) q_next = atomicAdd(&ctl->pool_next, 1u);
     // The stage that receives tile k+NS-1 was released by the barrier that
     // ended iteration k-1.
-    if (tid == 0 && k + NS - 1 < n_tiles) {
-      issue((k + NS - 1) % NS, tile + (NS - 1) * t_step);
-      if (k + NS < n_tiles) load_offsets(tile + NS * t_step);
+    if (tid == 0) {
+      const int t_issue = NS == 2 ? tile_n : tile_n2;
+      const int t_offs = NS == 2 ? tile_n2 : s_tile[(k + 3) & 7];
+      if (t_issue >= 0) {
+        issue((k + NS - 1) % NS, t_issue);
+        if (t_offs >= 0) load_offsets(t_offs);
+      }
     }
     if (early) {
       // Tile k+1's gather starts now, from indices loaded an iteration ago:
@@ -1305,10 +1367,10 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       // indices of tile k+2.
       if (has_next) {
         gather_halo((k + 1) % NS);
-        if (k + 2 < n_tiles) load_halo(tile + 2 * t_step);
+        if (tile_n2 >= 0) load_halo(tile_n2);
       }
     } else if (hreg && has_next) {
-      load_halo(tile + t_step);  // used by tile k+1's gather after the face loop
+      load_halo(tile_n);  // used by tile k+1's gather after the face loop
     }
     const unsigned char* p = smem + st * L.stage;
     const Real* xc = reinterpret_cast<const Real*>(p + L.off_cells);  // [ext][4]
@@ -1448,6 +1510,8 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
         own_q[cc][1] = next_q[cc][1];
       }
     }
+    // Slot (k + 4) & 7 held iteration k - 4's tile, which nobody reads now.
+    if (tid == 0) publish(k + 4);
     if (early) {
       const bool ok_end = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
       cp_async_wait_all();
@@ -1462,6 +1526,9 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       }
       __syncthreads();
     }
+    tile_c = tile_n;
+    tile_n = tile_n2;
+    tile_n2 = s_tile[(k + 3) & 7];
   }
   // After a timed-out wait, let every copy still in flight land before the
   // block's shared memory is released (bounded as well).
