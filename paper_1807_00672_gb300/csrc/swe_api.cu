@@ -893,14 +893,18 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     // waves of its scenario's walk and those last waves form the scenario's
     // pool, from which the faster blocks take more tiles. Each pool entry
     // costs an atomic on one address; measured best at 3 waves (a pool of
-    // every tile was 1.6 % slower than none).
+    // every tile was 1.6 % slower than none). Only for a single FP32
+    // scenario with at least 5 kPoolWaves tiles per chunk: where the pool
+    // would be a larger share of the tiles (the 1M-cell meshes, ensembles)
+    // and on the FP64 step it measured 0.5-5 % slower.
     constexpr int64_t kPoolWaves = 3;
+    const bool use_pool = n == 1 && p.precision == SWE_F32;
     std::vector<swe::Chunk> pooled(chunks), pooled_back(back);
-    for (size_t q = 0; q < chunks.size(); ++q) {
+    for (size_t q = 0; q < chunks.size() && use_pool; ++q) {
       const Scenario& sc = m->scen[chunks[q].scen];
       const int64_t S = sc.nchunks, N = sc.ntiles, ns = m->stages;
       const int64_t W = std::max<int64_t>(ns, N / S - kPoolWaves);  // static tiles per chunk
-      if (N < (ns + 2) * S || W * S >= N) continue;
+      if (N < 5 * kPoolWaves * S || W * S >= N) continue;
       const int64_t r = chunks[q].tile0 - sc.tile0;
       swe::Chunk& f = pooled[q];
       f.ntiles = (int32_t)W;

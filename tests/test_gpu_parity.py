@@ -141,11 +141,12 @@ def test_a_step_is_independent_of_the_tile_walk_direction():
     blocks that finish first take more). The order and the assignment of the
     tiles change no bit: the first step of a fresh state (walked forwards)
     equals the second step of a state restarted from the same fields by
-    swe_state_set (walked backwards), on a mesh of several tiles per block
-    (974,000 cells, pooled tiles in both walks) with a ragged last tile, and
-    repeated runs are identical."""
-    case = inputs.humps_case(nx=1000, ny=487, lx=20_000.0, ly=10_000.0, seed=19)
-    for prec in ("f32", "f64"):
+    swe_state_set (walked backwards), with a ragged last tile, and repeated
+    runs are identical. FP32 on 4,000,000 cells (about 17 tiles per block,
+    the last three waves pooled in both walks), FP64 on 974,000 cells (no
+    pool)."""
+    for prec, (nx, ny) in (("f32", (2000, 1000)), ("f64", (1000, 487))):
+        case = inputs.humps_case(nx=nx, ny=ny, lx=20_000.0, ly=10_000.0, seed=19)
         _, a = gpu_state(case, prec)
         a.step()
         _, b = gpu_state(case, prec)
