@@ -152,10 +152,11 @@ int grid_for(int64_t n, int threads, int cap) {
 
 // Opts the tiled kernel into its dynamic shared memory and returns its
 // resident blocks per SM (0 if it cannot run with this layout).
-template <typename Real, int NT, int NS, int TC, bool Early = false, bool CH = false>
+template <typename Real, int NT, int NS, int TC, bool Early = false, bool CH = false,
+          bool Pool = false>
 int prepare_tiled(const swe::TileLayout& L) {
   constexpr bool comp = sizeof(Real) == 4;
-  auto k = swe::k_tiled_step<Real, comp, NT, NS, TC, Early, CH>;
+  auto k = swe::k_tiled_step<Real, comp, NT, NS, TC, Early, CH, Pool>;
   // The limit is a property of the kernel, shared by every mesh that
   // launches it: set it to the device's largest opt-in size (not this
   // layout's), so that a later mesh with a smaller layout cannot lower it
@@ -212,6 +213,9 @@ int blocks_per_sm_tiled_nt(const swe_mesh* m) {
     if (m->layout.pipe) return prepare_pipe<NT, TC>(m->layout);
     if (m->layout.early) return prepare_tiled<Real, NT, 2, TC, true>(m->layout);
     if (m->prm.compensated_depth) return prepare_tiled<Real, NT, 2, TC, false, true>(m->layout);
+    // the pooled variant (FP32, halo schedule 0) shares the layout
+    if (m->stages == 2) prepare_tiled<Real, NT, 2, TC, false, false, true>(m->layout);
+    else prepare_tiled<Real, NT, 3, TC, false, false, true>(m->layout);
   }
   return m->stages == 3 ? prepare_tiled<Real, NT, 3, TC>(m->layout)
                         : prepare_tiled<Real, NT, 2, TC>(m->layout);
@@ -264,6 +268,13 @@ void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe:
     if constexpr (sizeof(Real) == 4) {
       if (ds.hlo) {  // compensated depth (2 stages, halo schedule 0)
         cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, false, true>, dm, ds, num, L);
+        return;
+      }
+      if (m->pooled && !L.early) {  // chunk tables with tile pools
+        if (m->stages == 3)
+          cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 3, TC, false, false, true>, dm, ds, num, L);
+        else
+          cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, false, false, true>, dm, ds, num, L);
         return;
       }
       if (L.early) {
@@ -898,7 +909,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     // would be a larger share of the tiles (the 1M-cell meshes, ensembles)
     // and on the FP64 step it measured 0.5-5 % slower.
     constexpr int64_t kPoolWaves = 3;
-    const bool use_pool = n == 1 && p.precision == SWE_F32;
+    const bool use_pool = n == 1 && p.precision == SWE_F32 && !m->layout.early && !p.compensated_depth;
     std::vector<swe::Chunk> pooled(chunks), pooled_back(back);
     for (size_t q = 0; q < chunks.size() && use_pool; ++q) {
       const Scenario& sc = m->scen[chunks[q].scen];
@@ -917,6 +928,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
       b.pool_first = (int32_t)(sc.tile0 + N - 1 - W * S);
       b.pool_count = (int32_t)(N - W * S);
     }
+    for (const swe::Chunk& c : pooled) m->pooled = m->pooled || c.pool_count > 0;
     chk(upload(m, pooled, m->chunks_pool));
     chk(upload(m, pooled_back, m->chunks_pool_back));
     if (m->layout.hreg) {
@@ -984,7 +996,7 @@ static void launch_forward_t(const swe_mesh* m, const swe::DevState<Real>& ds, c
                              bool back) {
   constexpr bool comp = sizeof(Real) == 4;
   swe::DevMesh<Real> dm = dev_mesh<Real>(m);
-  if (m->kernel == SWE_KERNEL_TILED && !m->layout.pipe)  // k_tiled_step: the pooled tables
+  if (m->pooled)  // the pooled k_tiled_step
     dm.chunks = back ? m->chunks_pool_back : m->chunks_pool;
   else if (back && m->chunks_back)
     dm.chunks = m->chunks_back;

@@ -87,6 +87,7 @@ struct swe_mesh {
   swe::Chunk* chunks_back = nullptr;  // the same chunks, tiles last to first
   swe::Chunk* chunks_pool = nullptr;  // k_tiled_step's chunks with tile pools
   swe::Chunk* chunks_pool_back = nullptr;  // the same, walked backwards
+  bool pooled = false;  // the step launches the pooled k_tiled_step on chunks_pool*
   int grid_edge = 1, grid_cell = 1, grid_cfl = 1, max_grid = 1;
   // Handles that use this mesh (states). swe_mesh_destroy while some are
   // alive only marks the mesh; the last of them to go frees it.

@@ -1078,7 +1078,10 @@ constexpr int tiled_min_blocks() { return (sizeof(Real) == 4 ? 768 : 512) / NT; 
 // Early: a tile's halo gather is issued at the start of the previous tile's
 // iteration (launched only on layouts with hreg). CH: FP32 with a depth
 // residual per cell (s.hlo, read and written by the cell's own thread).
-template <typename Real, bool Comp, int NT, int NS, int TC, bool Early = false, bool CH = false>
+// Pool: the chunk table has tile pools (see Chunk); without it a block works
+// its static tiles only and no tile bookkeeping goes through shared memory.
+template <typename Real, bool Comp, int NT, int NS, int TC, bool Early = false, bool CH = false,
+          bool Pool = false>
 __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
     k_tiled_step(DevMesh<Real> m, DevState<Real> s, Num num, TileLayout L) {
   constexpr int CPT = (TC + NT - 1) / NT;
@@ -1103,7 +1106,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   // k + 4 with an atomic issued at the start of iteration k whose result is
   // first used at its end, so that its latency is hidden. Once the pool is
   // empty every later iteration gets -1.
-  bool exhausted = pool_count <= 0;
+  bool exhausted = !Pool || pool_count <= 0;
   unsigned int q_next = 0u;
   auto pool_tile = [&](unsigned int q) -> int {
     return t_step > 0 ? pool_first + (int)q : pool_first - (int)q;
@@ -1299,21 +1302,24 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
 #pragma unroll
     for (int i = 0; i < NS - 1; ++i)
       if (i < n_tiles) issue_cells(i, t_first + i * t_step);
-    // the tiles of iterations 0..3: static ones, then pool entries taken
-    // with one atomic
-    const int ndyn = n_tiles >= 4 ? 0 : 4 - n_tiles;
-    const unsigned int q0 = (!exhausted && ndyn > 0) ? atomicAdd(&ctl->pool_next, (unsigned int)ndyn) : 0u;
+    if constexpr (Pool) {
+      // the tiles of iterations 0..3: static ones, then pool entries taken
+      // with one atomic
+      const int ndyn = n_tiles >= 4 ? 0 : 4 - n_tiles;
+      const unsigned int q0 =
+          (!exhausted && ndyn > 0) ? atomicAdd(&ctl->pool_next, (unsigned int)ndyn) : 0u;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int t = -1;
-      if (j < n_tiles) {
-        t = t_first + j * t_step;
-      } else if (!exhausted && q0 + (unsigned int)(j - n_tiles) < (unsigned int)pool_count) {
-        t = pool_tile(q0 + (unsigned int)(j - n_tiles));
-      } else {
-        exhausted = true;
+      for (int j = 0; j < 4; ++j) {
+        int t = -1;
+        if (j < n_tiles) {
+          t = t_first + j * t_step;
+        } else if (!exhausted && q0 + (unsigned int)(j - n_tiles) < (unsigned int)pool_count) {
+          t = pool_tile(q0 + (unsigned int)(j - n_tiles));
+        } else {
+          exhausted = true;
+        }
+        s_tile[j] = t;
       }
-      s_tile[j] = t;
     }
     if (NS - 1 < n_tiles) load_offsets(t_first + (NS - 1) * t_step);
   }
@@ -1340,25 +1346,36 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
   // Each iteration: the face records of tile k, then the cell updates of
   // tile k while tile k+1's halo gather is in flight (with `early`, issued
   // before the face records). Two block barriers.
-  // Every thread keeps the tiles of iterations k, k + 1 and k + 2 (from the
-  // ring, published at least one barrier earlier).
-  int tile_c = s_tile[0], tile_n = s_tile[1], tile_n2 = s_tile[2];
-  for (int k = 0; !timeout; ++k) {
-    const int tile = tile_c;
-    if (tile < 0) break;
+  // Pool: every thread keeps the tiles of iterations k, k + 1 and k + 2
+  // (from the ring, published at least one barrier earlier). Otherwise the
+  // tiles follow from k.
+  int tile_c = 0, tile_n = -1, tile_n2 = -1;
+  if constexpr (Pool) {
+    tile_c = s_tile[0];
+    tile_n = s_tile[1];
+    tile_n2 = s_tile[2];
+  }
+  for (int k = 0; !timeout && (Pool || k < n_tiles); ++k) {
+    const int tile = Pool ? tile_c : t_first + k * t_step;
+    if (Pool && tile < 0) break;
     const int st = k % NS;
-    const bool has_next = tile_n >= 0;
+    const bool has_next = Pool ? tile_n >= 0 : k + 1 < n_tiles;
     // the pool entry of iteration k + 4 (published at the end of this one)
-    if (tid == 0 && !exhausted && k + 4 >= n_tiles) q_next = atomicAdd(&ctl->pool_next, 1u);
+    if (Pool && tid == 0 && !exhausted && k + 4 >= n_tiles) q_next = atomicAdd(&ctl->pool_next, 1u);
     // The stage that receives tile k+NS-1 was released by the barrier that
     // ended iteration k-1.
-    if (tid == 0) {
-      const int t_issue = NS == 2 ? tile_n : tile_n2;
-      const int t_offs = NS == 2 ? tile_n2 : s_tile[(k + 3) & 7];
-      if (t_issue >= 0) {
-        issue((k + NS - 1) % NS, t_issue);
-        if (t_offs >= 0) load_offsets(t_offs);
+    if constexpr (Pool) {
+      if (tid == 0) {
+        const int t_issue = NS == 2 ? tile_n : tile_n2;
+        const int t_offs = NS == 2 ? tile_n2 : s_tile[(k + 3) & 7];
+        if (t_issue >= 0) {
+          issue((k + NS - 1) % NS, t_issue);
+          if (t_offs >= 0) load_offsets(t_offs);
+        }
       }
+    } else if (tid == 0 && k + NS - 1 < n_tiles) {
+      issue((k + NS - 1) % NS, tile + (NS - 1) * t_step);
+      if (k + NS < n_tiles) load_offsets(tile + NS * t_step);
     }
     if (early) {
       // Tile k+1's gather starts now, from indices loaded an iteration ago:
@@ -1367,10 +1384,10 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       // indices of tile k+2.
       if (has_next) {
         gather_halo((k + 1) % NS);
-        if (tile_n2 >= 0) load_halo(tile_n2);
+        if (Pool ? tile_n2 >= 0 : k + 2 < n_tiles) load_halo(Pool ? tile_n2 : tile + 2 * t_step);
       }
     } else if (hreg && has_next) {
-      load_halo(tile_n);  // used by tile k+1's gather after the face loop
+      load_halo(Pool ? tile_n : tile + t_step);  // used by tile k+1's gather after the face loop
     }
     const unsigned char* p = smem + st * L.stage;
     const Real* xc = reinterpret_cast<const Real*>(p + L.off_cells);  // [ext][4]
@@ -1511,7 +1528,7 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       }
     }
     // Slot (k + 4) & 7 held iteration k - 4's tile, which nobody reads now.
-    if (tid == 0) publish(k + 4);
+    if (Pool && tid == 0) publish(k + 4);
     if (early) {
       const bool ok_end = (tid == 0 && has_next) ? wait_stage((k + 1) % NS) : true;
       cp_async_wait_all();
@@ -1526,9 +1543,11 @@ __global__ void __launch_bounds__(NT, tiled_min_blocks<Real, NT>())
       }
       __syncthreads();
     }
-    tile_c = tile_n;
-    tile_n = tile_n2;
-    tile_n2 = s_tile[(k + 3) & 7];
+    if constexpr (Pool) {
+      tile_c = tile_n;
+      tile_n = tile_n2;
+      tile_n2 = s_tile[(k + 3) & 7];
+    }
   }
   // After a timed-out wait, let every copy still in flight land before the
   // block's shared memory is released (bounded as well).
