@@ -1049,7 +1049,8 @@ inline TileLayout make_tile_layout(uint32_t w, uint32_t geo_arrays, uint32_t tc,
 // ---------------------------------------------------------------------------
 // Tiled one-launch step on interleaved cells (h, hu, hv, z). A block of NT
 // threads walks the tiles of its work chunk (TC = NT * CPT consecutive cells
-// each; see Chunk) through NS shared-memory stages:
+// each; see Chunk), then, in the Pool variant, tiles of its scenario's pool,
+// through NS shared-memory stages:
 //   - thread 0 queues bulk async copies (TMA) of tile k+NS-1's cell arrays
 //     and face records (and its halo list, unless the layout's hreg has each
 //     thread load its halo index into a register) while the block works on
