@@ -212,7 +212,10 @@ int blocks_per_sm_tiled_nt(const swe_mesh* m) {
   if constexpr (sizeof(Real) == 4) {
     if (m->layout.pipe) return prepare_pipe<NT, TC>(m->layout);
     if (m->layout.early) return prepare_tiled<Real, NT, 2, TC, true>(m->layout);
-    if (m->prm.compensated_depth) return prepare_tiled<Real, NT, 2, TC, false, true>(m->layout);
+    if (m->prm.compensated_depth) {
+      prepare_tiled<Real, NT, 2, TC, false, true, true>(m->layout);  // its pooled variant
+      return prepare_tiled<Real, NT, 2, TC, false, true>(m->layout);
+    }
     // the pooled variant (FP32, halo schedule 0) shares the layout
     if (m->stages == 2) prepare_tiled<Real, NT, 2, TC, false, false, true>(m->layout);
     else prepare_tiled<Real, NT, 3, TC, false, false, true>(m->layout);
@@ -267,7 +270,10 @@ void launch_tiled_nt(const swe_mesh* m, const swe::DevMesh<Real>& dm, const swe:
   if constexpr (NT <= 256) {  // 512 threads exist only for the pipelined kernel
     if constexpr (sizeof(Real) == 4) {
       if (ds.hlo) {  // compensated depth (2 stages, halo schedule 0)
-        cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, false, true>, dm, ds, num, L);
+        if (m->pooled)
+          cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, false, true, true>, dm, ds, num, L);
+        else
+          cudaLaunchKernelEx(&cfg, swe::k_tiled_step<Real, Comp, NT, 2, TC, false, true>, dm, ds, num, L);
         return;
       }
       if (m->pooled && !L.early) {  // chunk tables with tile pools
@@ -909,7 +915,7 @@ swe_status create_batch(int32_t n, const double* const* xy, const int64_t* n_nod
     // would be a larger share of the tiles (the 1M-cell meshes, ensembles)
     // and on the FP64 step it measured 0.5-5 % slower.
     constexpr int64_t kPoolWaves = 3;
-    const bool use_pool = n == 1 && p.precision == SWE_F32 && !m->layout.early && !p.compensated_depth;
+    const bool use_pool = n == 1 && p.precision == SWE_F32 && !m->layout.early;
     std::vector<swe::Chunk> pooled(chunks), pooled_back(back);
     for (size_t q = 0; q < chunks.size() && use_pool; ++q) {
       const Scenario& sc = m->scen[chunks[q].scen];
