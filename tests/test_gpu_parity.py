@@ -163,6 +163,23 @@ def test_a_step_is_independent_of_the_tile_walk_direction():
             assert np.array_equal(x, y)
 
 
+def test_pooled_tiles_with_three_stages_give_the_same_bits():
+    """A mesh large enough for the tile pool (4,000,000 cells), stepped with
+    three shared-memory stages and with two: the same bits (the stages only
+    change how far ahead tiles are fetched)."""
+    case = inputs.humps_case(nx=2000, ny=1000, lx=20_000.0, ly=10_000.0, seed=23)
+    out = []
+    for stages in (2, 3):
+        ensure_built()
+        mesh = swe.Mesh(case.mesh.xy, case.mesh.tri, precision="f32", stages=stages)
+        st = swe.State(mesh, case.h, case.hu, case.hv, case.z, case.n)
+        st.run(12)
+        assert st.info()["err"] == 0
+        out.append(st.fields())
+    for x, y in zip(*out):
+        assert np.array_equal(x, y)
+
+
 def test_runs_are_deterministic_bitwise():
     case = inputs.humps_case(nx=80, ny=40, lx=2_000.0, ly=1_000.0, seed=13)
     for prec in ("f64", "f32"):
